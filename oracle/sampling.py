@@ -1,0 +1,83 @@
+"""McEwen-Wiaux (MW) sampling and quadrature for the oracle (test infrastructure only).
+
+Sec. 4.2.2 of the paper:
+* MW positions: theta_t = (2t+1) pi / (2L-1), t = 0..L-1;  phi_p = 2 pi p / (2L-1), p = 0..2L-2.
+* MW weights: the function equal to sin(theta) on [0, pi] and 0 on (pi, 2pi) is replaced by its
+  bandlimited Fourier series w, with coefficients w_hat(m') = int_0^pi sin(theta) e^{i m' theta}
+  dtheta (the paper's table: +-i pi/2 at m' = +-1, 0 at other odd m', 2/(1-m'^2) at even m'), and
+  contributions on (pi, 2pi) are folded back onto (0, pi).
+* For the spherical-harmonic transform the signal is upsampled to bandlimit 2L first, and the
+  weights at bandlimit L' = 2L are used.
+
+Readings (the printed formula is ambiguous or inconsistent here):
+* The sum over m' runs over |m'| <= L'-1 and T = 2L'-1.
+* The Fourier synthesis carries e^{-i m' theta}: with the coefficient definition printed
+  (e^{+i m' theta} inside the integral) this is the series that sums back to sin(theta) on [0, pi].
+  Only the m' = +-1 terms depend on this sign, and they cancel in the fold below.
+* The fold factor is +1.  The integrand of the forward transform, F_m(theta) d^l_{m,-s}(theta),
+  is the product of two functions that both change sign by (-1)^{m+s} under theta -> 2pi - theta
+  after the torus extension, so it is even; the printed zeta_t (-1)^s would be right only for an
+  integrand of parity (-1)^s.  With fold +1 the quadrature is exact for every even integrand.
+* theta_{L'-1} = pi is the one unreflected ring (zeta = 0 there), as printed.
+* The constant is 1/T per ring for the theta integral; the phi integral contributes 2 pi / (2L-1)
+  separately (the printed 2 pi / T^2 is the product of both when phi is sampled like theta).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from .wigner import PI_LD
+
+
+def mw_thetas(L: int, dtype=np.longdouble) -> np.ndarray:
+    """MW colatitudes theta_t = (2t+1) pi / (2L-1), t < L (the last one is exactly pi)."""
+    t = np.arange(L)
+    th = (2 * t + 1).astype(np.longdouble) * PI_LD / np.longdouble(2 * L - 1)
+    th[-1] = PI_LD
+    return th.astype(dtype)
+
+
+def mw_torus_thetas(L: int, dtype=np.longdouble) -> np.ndarray:
+    """The same formula for t = 0..2L-2: the MW grid extended to the theta torus [0, 2 pi)."""
+    t = np.arange(2 * L - 1)
+    th = (2 * t + 1).astype(np.longdouble) * PI_LD / np.longdouble(2 * L - 1)
+    th[L - 1] = PI_LD
+    return th.astype(dtype)
+
+
+def mw_phis(L: int) -> np.ndarray:
+    """MW longitudes phi_p = 2 pi p / (2L-1), p < 2L-1 (extended precision)."""
+    p = np.arange(2 * L - 1)
+    return (2 * p).astype(np.longdouble) * PI_LD / np.longdouble(2 * L - 1)
+
+
+def w_hat(mp: np.ndarray) -> np.ndarray:
+    """w_hat(m') = int_0^pi sin(theta) e^{i m' theta} dtheta (the paper's closed form), complex."""
+    mp = np.asarray(mp)
+    out = np.zeros(mp.shape, dtype=np.complex128)
+    even = (mp % 2) == 0
+    out[even] = 2.0 / (1.0 - mp[even].astype(np.float64) ** 2)
+    out[mp == 1] = 1j * np.pi / 2
+    out[mp == -1] = -1j * np.pi / 2
+    return out
+
+
+def mw_theta_weights(Lp: int) -> np.ndarray:
+    """Theta quadrature weights q_t, t < Lp, of the MW sampling theorem at bandlimit Lp.
+
+    sum_t q_t g(theta_t) = int_0^pi g(theta) sin(theta) dtheta for every g whose torus extension
+    is even about pi and has frequencies |k| <= Lp-1 (module readings: fold +1, constant 1/T).
+    """
+    T = 2 * Lp - 1
+    th = mw_torus_thetas(Lp, dtype=np.float64)           # theta_t on the torus, t < T
+    k = np.arange(-(Lp - 1), Lp)
+    wk = w_hat(k)
+    # w(theta_t) = sum_k w_hat(k) e^{-i k theta_t}   (reading: sign of the synthesis)
+    E = np.exp(-1j * np.outer(th, k))
+    w = E @ wk
+    q = np.empty(Lp, dtype=np.complex128)
+    for t in range(Lp):
+        zeta = 0.0 if t == Lp - 1 else 1.0
+        q[t] = (w[t] + zeta * w[2 * Lp - 2 - t]) / T      # reflect: theta_{2L'-2-t} = 2 pi - theta_t
+    assert np.max(np.abs(q.imag)) < 1e-12 * np.max(np.abs(q.real))
+    return q.real.copy()

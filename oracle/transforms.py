@@ -1,0 +1,216 @@
+"""Spin-s spherical-harmonic and Wigner transforms on MW sampling -- the oracle (test infrastructure).
+
+Everything is a direct sum in float64 (no FFT); exponentials are built from exactly reduced
+integer phases.  Array conventions (shared with the GPU library's boundary, written out here
+independently):
+
+* sphere signal   f[..., t, p]           t < L rings (theta_t), p < 2L-1 (phi_p)
+* coefficients    flm[..., l, m+L-1]     l < L, |m| <= l; other entries ignored / returned as 0
+* SO(3) signal    f[..., k, t, p]        k < 2N-1 (gamma_k = 2 pi k/(2N-1)), t (beta), p (alpha)
+* Wigner coeffs   flmn[..., n+N-1, l, m+L-1]
+
+Definitions followed (Sec. 4.1): with c_l = (-1)^s sqrt((2l+1)/(4 pi)),
+  inverse  (Eqs. disc_ish_expanded, disc_ish_fft):
+      f~_m(theta) = sum_l c_l flm_lm d^l_{m,-s}(theta),   f(theta, phi_p) = sum_m f~_m(theta) e^{i m phi_p}
+  forward  (Eqs. disc_sh_fft, disc_sh_expanded; Sec. 4.2.2 for MW):
+      F_m(theta_t) = sum_p f(theta_t, phi_p) e^{-i m phi_p}
+      extend to the theta torus: G_m(theta_{2L-2-t}) = (-1)^{m+s} F_m(theta_t), and at the
+      self-reflected ring theta = pi, G_m(pi) = (1 + (-1)^{m+s})/2 F_m(pi) (reading, see _extend)
+      upsample to the MW grid of bandlimit 2L by zero padding the theta-Fourier series
+      flm_lm = c_l sum_u q_u d^l_{m,-s}(theta'_u) q_Phi G_m(theta'_u),   q_Phi = 2 pi/(2L-1)
+The Wigner transform (Sec. 2.3, 4.5) is a gamma-DFT plus spin-(-n) transforms whose per-l factor
+is (2l+1)/(8 pi^2) (inverse) or 1 (forward) instead of c_l.  Adjoints (Sec. 5.2) are the
+conjugate transposes of these linear maps, written stage by stage in reverse order.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from .sampling import mw_theta_weights, mw_thetas
+from .wigner import PI_LD, wigner_d_table
+
+_CHUNK_BYTES = 256 << 20
+
+
+def _expi_pi(num, den: int) -> np.ndarray:
+    """exp(i pi num/den) for integer arrays num, reduced exactly modulo 2 den."""
+    r = np.mod(np.asarray(num, dtype=np.int64), 2 * den)
+    ang = r.astype(np.longdouble) * PI_LD / np.longdouble(den)
+    return (np.cos(ang) + 1j * np.sin(ang)).astype(np.complex128)
+
+
+def phi_dft_matrix(L: int, sign: int) -> np.ndarray:
+    """E[p, j] = exp(sign * i m_j phi_p), m_j = j - (L-1), phi_p = 2 pi p/(2L-1)."""
+    T = 2 * L - 1
+    p = np.arange(T)[:, None]
+    m = np.arange(-(L - 1), L)[None, :]
+    return _expi_pi(sign * 2 * p * m, T)
+
+
+def ell_factor(L: int, spin: int) -> np.ndarray:
+    """c_l = (-1)^s sqrt((2l+1)/(4 pi)), l < L (Eq. disc_sh_expanded)."""
+    ell = np.arange(L)
+    return (-1.0) ** spin * np.sqrt((2 * ell + 1) / (4 * np.pi))
+
+
+def coeff_mask(L: int, n: int) -> np.ndarray:
+    """True where max(|m|, |n|) <= l < L, shape (L, 2L-1)."""
+    ell = np.arange(L)[:, None]
+    m = np.arange(-(L - 1), L)[None, :]
+    return (np.abs(m) <= ell) & (abs(n) <= ell)
+
+
+# ----------------------------------------------------------------------------- inverse
+def _theta_inverse(flm: np.ndarray, L: int, n: int, scale: np.ndarray, thetas) -> np.ndarray:
+    """f~[..., t, m] = sum_l scale_l flm[..., l, m] d^l_{m,n}(theta_t) (Eq. disc_ish_expanded)."""
+    flm = np.where(coeff_mask(L, n), flm, 0) * scale[:, None]
+    out = np.zeros(flm.shape[:-2] + (len(thetas), 2 * L - 1), dtype=np.complex128)
+    per_ring = L * (2 * L - 1) * 8
+    step = max(1, _CHUNK_BYTES // per_ring)
+    for a in range(0, len(thetas), step):
+        D = wigner_d_table(np.arange(L), n, thetas[a:a + step])          # [l, m, t]
+        out[..., a:a + step, :] = np.einsum("...lm,lmt->...tm", flm, D)
+    return out
+
+
+def inverse(flm: np.ndarray, L: int, spin: int, rings=None) -> np.ndarray:
+    """Inverse spin-s SHT on the MW grid; ``rings`` selects theta indices (default: all L)."""
+    th = mw_thetas(L)
+    if rings is not None:
+        th = th[np.asarray(rings)]
+    ft = _theta_inverse(np.asarray(flm, dtype=np.complex128), L, -spin, ell_factor(L, spin), th)
+    return ft @ phi_dft_matrix(L, +1).T                                   # Eq. disc_ish_fft
+
+
+# ----------------------------------------------------------------------------- forward
+def _upsample_matrices(L: int):
+    """Matrices of the theta torus extension / Fourier coefficients / upsampled evaluation."""
+    T = 2 * L - 1
+    Tu = 4 * L - 1                       # torus length of the MW grid at bandlimit 2L
+    k = np.arange(-(L - 1), L)
+    tt = np.arange(T)
+    uu = np.arange(2 * L)
+    coef = _expi_pi(-np.outer(k, 2 * tt + 1), T) / T                      # [k, t'] e^{-ik theta_t'}/T
+    up = _expi_pi(np.outer(2 * uu + 1, k), Tu)                              # [u, k]  e^{+ik theta'_u}
+    return coef, up
+
+
+def _phi_forward(f: np.ndarray, L: int) -> np.ndarray:
+    """F[..., t, m] = sum_p f[..., t, p] e^{-i m phi_p} (Eq. disc_sh_fft without q_Phi)."""
+    return np.asarray(f, dtype=np.complex128) @ phi_dft_matrix(L, -1)
+
+
+def _extend(F: np.ndarray, L: int, n: int) -> np.ndarray:
+    """Torus extension in theta, G[..., t', m] for t' < 2L-1 (Sec. 4.2.2); n is the d-index (-s).
+
+    Reading: the ring theta = pi is its own reflection, so the extension there is the average of
+    the ring and its reflection, G_m(pi) = (1 + (-1)^{m+s})/2 F_m(pi).  Bandlimited signals already
+    have F_m(pi) = 0 for odd m+s; for arbitrary samples this makes the torus function exactly of
+    parity (-1)^{m+s}, so that every exact theta quadrature gives the same result."""
+    m = np.arange(-(L - 1), L)
+    sigma = (-1.0) ** ((m - n) % 2)                                         # (-1)^{m+s}
+    G = np.zeros(F.shape[:-2] + (2 * L - 1, 2 * L - 1), dtype=np.complex128)
+    G[..., :L, :] = F
+    G[..., L - 1, :] = F[..., L - 1, :] * (1 + sigma) / 2
+    G[..., L:, :] = (F[..., :L - 1, :] * sigma)[..., ::-1, :]               # G[2L-2-t] = sigma F[t]
+    return G
+
+
+def _theta_forward_upsampled(Gu: np.ndarray, L: int, n: int, scale: np.ndarray, ells) -> np.ndarray:
+    """flm[..., i, m] = scale_l sum_u q_u d^l_{m,n}(theta'_u) q_Phi Gu[..., u, m], l = ells[i]."""
+    ells = np.asarray(ells)
+    q = mw_theta_weights(2 * L)
+    qphi = 2 * np.pi / (2 * L - 1)
+    thu = mw_thetas(2 * L)
+    W = Gu * (q * qphi)[:, None]
+    out = np.zeros(Gu.shape[:-2] + (len(ells), 2 * L - 1), dtype=np.complex128)
+    per_l = (2 * L - 1) * 2 * L * 8 * 2
+    step = max(1, _CHUNK_BYTES // per_l)
+    for a in range(0, len(ells), step):
+        sel = ells[a:a + step]
+        D = wigner_d_table(sel, n, thu)                                      # [i, m', u], m' width max(sel)
+        M = int(sel.max())
+        D = D[:, M - (L - 1):M + L, :] if M >= L - 1 else np.pad(D, ((0, 0), (L - 1 - M, L - 1 - M), (0, 0)))
+        out[..., a:a + step, :] = np.einsum("...um,imu->...im", W, D) * scale[sel][:, None]
+    mask = coeff_mask(L, n)[ells]
+    return np.where(mask, out, 0)
+
+
+def forward(f: np.ndarray, L: int, spin: int, ells=None) -> np.ndarray:
+    """Forward spin-s SHT on the MW grid; ``ells`` selects output rows (default: all l < L)."""
+    if ells is None:
+        ells = np.arange(L)
+    coef, up = _upsample_matrices(L)
+    G = _extend(_phi_forward(f, L), L, -spin)
+    Gu = up @ (coef @ G)
+    return _theta_forward_upsampled(Gu, L, -spin, ell_factor(L, spin), ells)
+
+
+# ----------------------------------------------------------------------------- adjoints (Sec. 5.2)
+def adjoint_inverse(fbar: np.ndarray, L: int, spin: int) -> np.ndarray:
+    """Conjugate transpose of ``inverse``: flm_bar[l, m] = c_l sum_t d^l_{m,-s}(theta_t) sum_p fbar e^{-i m phi_p}."""
+    v = _phi_forward(fbar, L)                                                # phi-DFT^H of the synthesis
+    th = mw_thetas(L)
+    n = -spin
+    out = np.zeros(v.shape[:-2] + (L, 2 * L - 1), dtype=np.complex128)
+    D = wigner_d_table(np.arange(L), n, th)                                  # [l, m, t]
+    out = np.einsum("...tm,lmt->...lm", v, D) * ell_factor(L, spin)[:, None]
+    return np.where(coeff_mask(L, n), out, 0)
+
+
+def adjoint_forward(flm_bar: np.ndarray, L: int, spin: int) -> np.ndarray:
+    """Conjugate transpose of ``forward``: every stage of ``forward`` transposed, in reverse order."""
+    n = -spin
+    flm_bar = np.where(coeff_mask(L, n), np.asarray(flm_bar, dtype=np.complex128), 0)
+    q = mw_theta_weights(2 * L)
+    qphi = 2 * np.pi / (2 * L - 1)
+    thu = mw_thetas(2 * L)
+    D = wigner_d_table(np.arange(L), n, thu)                                 # [l, m, u]
+    X = np.einsum("...lm,lmu->...um", flm_bar * ell_factor(L, spin)[:, None], D)
+    X = X * (q * qphi)[:, None]
+    coef, up = _upsample_matrices(L)
+    Gbar = coef.conj().T @ (up.conj().T @ X)                                 # [t', m]
+    m = np.arange(-(L - 1), L)
+    sigma = (-1.0) ** ((m - n) % 2)
+    Fbar = Gbar[..., :L, :].copy()
+    Fbar[..., L - 1, :] *= (1 + sigma) / 2
+    Fbar[..., :L - 1, :] += sigma * Gbar[..., L:, :][..., ::-1, :]
+    return Fbar @ phi_dft_matrix(L, -1).conj().T                            # phi-DFT^H
+
+
+# ----------------------------------------------------------------------------- Wigner (Sec. 2.3, 4.5)
+def _gamma_matrix(N: int, sign: int) -> np.ndarray:
+    """E[k, j] = exp(sign i n_j gamma_k), n_j = j-(N-1), gamma_k = 2 pi k/(2N-1)."""
+    K = 2 * N - 1
+    k = np.arange(K)[:, None]
+    nn = np.arange(-(N - 1), N)[None, :]
+    return _expi_pi(sign * 2 * k * nn, K)
+
+
+def wigner_inverse(flmn: np.ndarray, L: int, N: int, rings=None) -> np.ndarray:
+    """Inverse Wigner transform: f(alpha, beta, gamma) = sum (2l+1)/(8 pi^2) flmn D^{l*}_{mn}."""
+    flmn = np.asarray(flmn, dtype=np.complex128)
+    th = mw_thetas(L) if rings is None else mw_thetas(L)[np.asarray(rings)]
+    scale = (2 * np.arange(L) + 1) / (8 * np.pi ** 2)
+    fn = []
+    for j, n in enumerate(range(-(N - 1), N)):
+        ft = _theta_inverse(flmn[..., j, :, :], L, n, scale, th)
+        fn.append(ft @ phi_dft_matrix(L, +1).T)                              # sum_m e^{i m alpha}
+    fn = np.stack(fn, axis=-3)                                               # [..., n, t, p]
+    return np.einsum("kn,...ntp->...ktp", _gamma_matrix(N, +1), fn)         # sum_n e^{i n gamma}
+
+
+def wigner_forward(f: np.ndarray, L: int, N: int, ells=None) -> np.ndarray:
+    """Forward Wigner transform: flmn = int f D^l_{mn}, as gamma-DFT plus spin-(-n) theta stages."""
+    f = np.asarray(f, dtype=np.complex128)
+    if ells is None:
+        ells = np.arange(L)
+    qgam = 2 * np.pi / (2 * N - 1)
+    fn = np.einsum("kn,...ktp->...ntp", _gamma_matrix(N, -1), f) * qgam     # f_n(alpha, beta)
+    coef, up = _upsample_matrices(L)
+    ones = np.ones(L)
+    out = []
+    for j, n in enumerate(range(-(N - 1), N)):
+        G = _extend(_phi_forward(fn[..., j, :, :], L), L, n)
+        out.append(_theta_forward_upsampled(up @ (coef @ G), L, n, ones, ells))
+    return np.stack(out, axis=-3)

@@ -1,0 +1,140 @@
+/*
+ * s2gb -- spin spherical-harmonic and Wigner transforms on McEwen-Wiaux sampling for NVIDIA
+ * GB300 (sm_103a).  C ABI of libs2gb.so.
+ *
+ * The operations are those of Price & McEwen, "Differentiable and accelerated spherical harmonic
+ * and Wigner transforms" (arXiv:2311.14670):
+ *   - forward / inverse spin-s spherical-harmonic transform, separated into a phi-DFT and a theta
+ *     stage (Sec. 4.1, Eqs. disc_sh_expanded, disc_sh_fft, disc_ish_fft, disc_ish_expanded),
+ *     on MW sampling (Sec. 4.2.2);
+ *   - forward / inverse Wigner transform as a gamma-DFT plus spin-(-n) transforms (Sec. 2.3, 4.5);
+ *   - the adjoints of both directions (Sec. 5.2).
+ * The Wigner d-functions of the theta stage are generated on the fly by a three-term recursion
+ * in the degree l, interleaved with the theta contraction (Sec. 4.4), and never stored.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *   L      bandlimit (l < L), L >= 1.
+ *   T      2L - 1 (number of phi samples; number of orders m).
+ *   theta_t = (2t+1) pi / (2L-1), t < L;  phi_p = 2 pi p / (2L-1), p < T.
+ *   sY_lm(theta, phi) = (-1)^s sqrt((2l+1)/(4 pi)) d^l_{m,-s}(theta) e^{i m phi}.
+ *   Sphere signal      f  [batch][L][T]              (ring t, sample p), row-major.
+ *   Sphere coefficients flm[batch][L][T]             (degree l, index m+L-1).
+ *   SO(3) signal       f  [batch][2N-1][L][T]        (gamma_k = 2 pi k/(2N-1), beta_t, alpha_p).
+ *   Wigner coefficients flmn[batch][2N-1][L][T]      (index n+N-1, degree l, index m+L-1).
+ *   Coefficient entries with |m| > l, or l < |s| (sphere) / l < |n| (Wigner), are ignored on
+ *   input and written as 0 on output.
+ *   Element type: interleaved complex, double (complex128) for S2GB_FP64 plans and float
+ *   (complex64) for S2GB_FP32 plans.  All data pointers are DEVICE pointers on the plan's device,
+ *   16-byte aligned (8-byte for complex64).  The caller owns them.
+ *   Adjoints are taken with respect to the Euclidean inner product sum conj(x) y (so that
+ *   adjoint_inverse(grad_f) is the gradient of a real loss with respect to flm, PyTorch's
+ *   convention for complex tensors).
+ *
+ * Execution model: every transform call only enqueues work on `stream` (a cudaStream_t passed as
+ * void*, NULL = legacy default stream) and returns.  It launches kernels and cuFFT executions and
+ * allocates nothing.  Scratch memory is the caller's `ws` buffer of at least
+ * s2gb_workspace_bytes(plan, batch) bytes; calls that may run concurrently need distinct
+ * workspaces.  A plan is immutable after creation; its cuFFT handles are shared, and calls on the
+ * same plan from several host threads are serialised internally around the cuFFT executions.
+ * Errors are returned as negative codes; no exception crosses the ABI.  Asynchronous kernel
+ * faults surface, as in any CUDA program, at the next synchronising call.
+ */
+#ifndef S2GB_H
+#define S2GB_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct s2gb_plan_s* s2gb_plan;
+
+/* Return codes. */
+enum {
+  S2GB_OK = 0,
+  S2GB_EINVAL = -1,        /* bad argument: null pointer, size out of range, in == out, ... */
+  S2GB_EUNSUPPORTED = -2,  /* valid request that this build does not implement */
+  S2GB_ENOMEM = -3,        /* device allocation failed (plan creation only) */
+  S2GB_ECUDA = -4,         /* a CUDA runtime call or kernel launch failed */
+  S2GB_ECUFFT = -5,        /* a cuFFT call failed */
+  S2GB_EWORKSPACE = -6     /* ws is NULL or smaller than s2gb_workspace_bytes() */
+};
+
+/* Sampling schemes.  Only McEwen-Wiaux (Sec. 4.2.2) is implemented. */
+enum { S2GB_MW = 0 };
+
+/* Arithmetic of the theta stage. */
+enum {
+  S2GB_FP64 = 0,  /* float64 recursion and contraction, complex128 data */
+  S2GB_FP32 = 1   /* float32 recursion and contraction with float64 seeds, complex64 data */
+};
+
+/*
+ * Create a plan on `device` for bandlimit L.
+ *   N == 0 : spin-`spin` sphere transforms, |spin| < L.
+ *   N >= 1 : Wigner transforms on SO(3) with azimuthal bandlimit N (|n| < N), N <= L; `spin` is
+ *            ignored.
+ * max_batch >= 1 bounds the `batch` argument of later calls.  The plan holds on the device the
+ * recursion coefficient tables (Sec. 3.3 readings, O(L^2) per spin), the per-ring and per-order
+ * log-space seed data (Eq. "initial_values") and the FFT weights; it creates cuFFT plans.
+ * Returns S2GB_EINVAL for L < 1, |spin| >= L (sphere), N < 0 or N > L, max_batch < 1, an unknown
+ * sampling or precision; S2GB_ENOMEM / S2GB_ECUDA / S2GB_ECUFFT on device failures.  On failure
+ * *out is set to NULL.  The calling thread's current device is restored on return.
+ */
+int s2gb_plan_create(s2gb_plan* out, int L, int spin, int N, int sampling, int precision,
+                     int max_batch, int device);
+
+/* Free a plan and everything it holds (NULL is ignored).  No call on it may be in flight. */
+void s2gb_plan_destroy(s2gb_plan plan);
+
+/* Bytes of scratch a transform call on `batch` signals needs (0 if batch is out of range). */
+size_t s2gb_workspace_bytes(s2gb_plan plan, int batch);
+
+/* Bytes of device memory the plan itself holds (tables, weights, cuFFT plans excluded). */
+size_t s2gb_plan_device_bytes(s2gb_plan plan);
+
+/*
+ * Forward transform (Sec. 4.1, Eqs. disc_sh_fft + disc_sh_expanded; Wigner: Eq. wigner_sht_forward
+ * with the gamma-DFT).  f -> flm.  The theta quadrature is exact for bandlimited signals (MW
+ * sampling theorem).  f and flm must not overlap (else S2GB_EINVAL).
+ */
+int s2gb_forward(s2gb_plan plan, const void* f, void* flm, int batch, void* ws, size_t ws_bytes,
+                 void* stream);
+
+/* Inverse transform (Eqs. disc_ish_expanded + disc_ish_fft; Wigner: Eq. wigner_sht_inverse). */
+int s2gb_inverse(s2gb_plan plan, const void* flm, void* f, int batch, void* ws, size_t ws_bytes,
+                 void* stream);
+
+/* Adjoint of s2gb_forward: flm_bar -> f_bar (Sec. 5.2.1, F^H; exact transpose of the pipeline). */
+int s2gb_adjoint_forward(s2gb_plan plan, const void* flm_bar, void* f_bar, int batch, void* ws,
+                         size_t ws_bytes, void* stream);
+
+/* Adjoint of s2gb_inverse: f_bar -> flm_bar (Sec. 5.2.2, F^{-H}). */
+int s2gb_adjoint_inverse(s2gb_plan plan, const void* f_bar, void* flm_bar, int batch, void* ws,
+                         size_t ws_bytes, void* stream);
+
+/*
+ * Theta stages alone (the recursion + contraction kernels, Sec. 4.4), for sphere plans.
+ *
+ * s2gb_inverse_theta: Eq. disc_ish_expanded,
+ *     ftilde[b][t][k] = sum_l (-1)^s sqrt((2l+1)/(4 pi)) flm[b][l][m+L-1] d^l_{m,-s}(theta_t),
+ *   k = m mod T (the layout a length-T inverse DFT along the last axis turns into f).
+ * s2gb_forward_theta: Eq. disc_sh_expanded on the L MW rings with ring weights already applied,
+ *     flm[b][l][m+L-1] = (-1)^s sqrt((2l+1)/(4 pi)) sum_t d^l_{m,-s}(theta_t) g[b][m+L-1][t],
+ *   g of shape [batch][T][L] (order-major).
+ * Same pointer, batch and stream rules as the transforms; no workspace is needed.  For N >= 1
+ * plans these return S2GB_EUNSUPPORTED.
+ */
+int s2gb_inverse_theta(s2gb_plan plan, const void* flm, void* ftilde, int batch, void* stream);
+int s2gb_forward_theta(s2gb_plan plan, const void* g, void* flm, int batch, void* stream);
+
+/* Static description of a return code (never NULL). */
+const char* s2gb_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* S2GB_H */

@@ -1,0 +1,132 @@
+"""ctypes binding of libs2gb.so: argument marshalling only.
+
+Every function here has the name of the C entry point in ``include/s2gb.h`` without the
+``s2gb_`` prefix and passes its arguments straight through.  Data arguments are CUDA tensors
+(their ``data_ptr()`` is passed), ``stream`` defaults to PyTorch's current stream on the plan's
+device.  A negative return code raises ``S2GBError``.  There is no fallback: if the library is
+missing, importing any transform raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libs2gb.so")
+
+S2GB_OK = 0
+S2GB_EINVAL = -1
+S2GB_EUNSUPPORTED = -2
+S2GB_ENOMEM = -3
+S2GB_ECUDA = -4
+S2GB_ECUFFT = -5
+S2GB_EWORKSPACE = -6
+S2GB_MW = 0
+S2GB_FP64 = 0
+S2GB_FP32 = 1
+
+_lib = None
+
+
+class S2GBError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        super().__init__(f"{where}: {strerror(code)} ({code})")
+        self.code = code
+
+
+def lib() -> ctypes.CDLL:
+    """Load libs2gb.so (built in-tree by ``paper_2311_14670_gb300.build``)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
+        L.s2gb_plan_create.argtypes = [ctypes.POINTER(vp), i, i, i, i, i, i, i]
+        L.s2gb_plan_create.restype = i
+        L.s2gb_plan_destroy.argtypes = [vp]
+        L.s2gb_plan_destroy.restype = None
+        L.s2gb_workspace_bytes.argtypes = [vp, i]
+        L.s2gb_workspace_bytes.restype = sz
+        L.s2gb_plan_device_bytes.argtypes = [vp]
+        L.s2gb_plan_device_bytes.restype = sz
+        for name in ("s2gb_forward", "s2gb_inverse", "s2gb_adjoint_forward", "s2gb_adjoint_inverse"):
+            fn = getattr(L, name)
+            fn.argtypes = [vp, vp, vp, i, vp, sz, vp]
+            fn.restype = i
+        for name in ("s2gb_inverse_theta", "s2gb_forward_theta"):
+            fn = getattr(L, name)
+            fn.argtypes = [vp, vp, vp, i, vp]
+            fn.restype = i
+        L.s2gb_strerror.argtypes = [i]
+        L.s2gb_strerror.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def strerror(code: int) -> str:
+    return lib().s2gb_strerror(int(code)).decode()
+
+
+def _check(rc: int, where: str) -> None:
+    if rc != S2GB_OK:
+        raise S2GBError(rc, where)
+
+
+def plan_create(L: int, spin: int, N: int, sampling: int, precision: int, max_batch: int, device: int) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().s2gb_plan_create(ctypes.byref(h), L, spin, N, sampling, precision, max_batch, device),
+           "s2gb_plan_create")
+    return h.value
+
+
+def plan_destroy(plan: int) -> None:
+    lib().s2gb_plan_destroy(ctypes.c_void_p(plan))
+
+
+def workspace_bytes(plan: int, batch: int) -> int:
+    return int(lib().s2gb_workspace_bytes(ctypes.c_void_p(plan), batch))
+
+
+def plan_device_bytes(plan: int) -> int:
+    return int(lib().s2gb_plan_device_bytes(ctypes.c_void_p(plan)))
+
+
+def _ptr(x) -> int:
+    return x if isinstance(x, int) else x.data_ptr()
+
+
+def _call(name: str, plan: int, src, dst, batch: int, ws, ws_bytes: int, stream: int) -> None:
+    fn = getattr(lib(), "s2gb_" + name)
+    _check(fn(ctypes.c_void_p(plan), ctypes.c_void_p(_ptr(src)), ctypes.c_void_p(_ptr(dst)), batch,
+              ctypes.c_void_p(_ptr(ws) if ws is not None else 0), ws_bytes, ctypes.c_void_p(stream)),
+           "s2gb_" + name)
+
+
+def forward(plan, f, flm, batch, ws, ws_bytes, stream):
+    _call("forward", plan, f, flm, batch, ws, ws_bytes, stream)
+
+
+def inverse(plan, flm, f, batch, ws, ws_bytes, stream):
+    _call("inverse", plan, flm, f, batch, ws, ws_bytes, stream)
+
+
+def adjoint_forward(plan, flm_bar, f_bar, batch, ws, ws_bytes, stream):
+    _call("adjoint_forward", plan, flm_bar, f_bar, batch, ws, ws_bytes, stream)
+
+
+def adjoint_inverse(plan, f_bar, flm_bar, batch, ws, ws_bytes, stream):
+    _call("adjoint_inverse", plan, f_bar, flm_bar, batch, ws, ws_bytes, stream)
+
+
+def inverse_theta(plan, flm, ftilde, batch, stream):
+    _check(lib().s2gb_inverse_theta(ctypes.c_void_p(plan), ctypes.c_void_p(_ptr(flm)),
+                                    ctypes.c_void_p(_ptr(ftilde)), batch, ctypes.c_void_p(stream)),
+           "s2gb_inverse_theta")
+
+
+def forward_theta(plan, g, flm, batch, stream):
+    _check(lib().s2gb_forward_theta(ctypes.c_void_p(plan), ctypes.c_void_p(_ptr(g)),
+                                    ctypes.c_void_p(_ptr(flm)), batch, ctypes.c_void_p(stream)),
+           "s2gb_forward_theta")

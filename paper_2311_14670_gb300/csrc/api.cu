@@ -1,0 +1,373 @@
+// C ABI of libs2gb.so (declared in include/s2gb.h): argument checks and the stage sequences of
+// the transforms.  Every stage runs on the caller's stream; nothing here allocates after plan
+// creation.
+//
+// Forward, per signal (Sec. 4.1 and 4.2.2), with T = 2L-1 and NF >= 4L-3:
+//   F   = DFT_T along phi                                  (Eq. disc_sh_fft, without q_Phi)
+//   G   = torus extension of F in theta (order-major rows of length T)
+//   H   = (1/(T NF)) IDFT_T . trunc . DFT_N . W . IDFT_N . pad . DFT_T (G)
+//   flm = c_l sum_{t<L} d^l_{m,-s}(theta_t) nu_t H_m(theta_t)   (theta kernel, Eq. disc_sh_expanded)
+// H is the degree-(L-1) projection of G(theta) |sin theta|/2 on the theta torus, evaluated on the L
+// MW rings: W holds that weight's Fourier series (|k| <= 2L-2) sampled on the fine grid
+// x_j = pi/T + 2 pi j/NF (the half-sample shift cancels the phases of the MW grid), together with
+// the constants (2 pi/T)^2/(T NF).  Because the d-functions are trigonometric polynomials of degree
+// <= L-1 in theta, int_0^pi G d sin = int_torus H d |sin|/2... = (2pi/T) sum over the torus of H d,
+// folded onto the L rings with nu_t = 2 (t < L-1) and nu_{L-1} = 1.  This integrates exactly what
+// the upsample-to-2L route of Sec. 4.2.2 integrates, on L rings instead of 2L.
+// Inverse (Eqs. disc_ish_expanded, disc_ish_fft): theta kernel into [t][m mod T], then IDFT_T.
+// Wigner (Sec. 2.3, 4.5): a gamma DFT (forward, scaled by 2 pi/(2N-1)) or IDFT (inverse) around
+// 2N-1 spin-(-n) stages, with per-degree factors 1 (forward) and (2l+1)/(8 pi^2) (inverse).
+// Adjoints (Sec. 5.2): every stage transposed in reverse order; the operator between the two
+// DFT_T calls above is self-adjoint, the theta kernels swap roles.
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "s2gb_internal.h"
+
+struct s2gb_plan_s {
+  s2gb::Plan p;
+};
+
+namespace s2gb {
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Workspace {
+  char* A;
+  char* B;
+  char* C;
+  void* fft;
+};
+
+Workspace carve(const Plan& p, void* ws, int batch) {
+  const size_t es = p.precision == S2GB_FP64 ? 16 : 8;
+  const size_t S = (size_t)batch * p.nN;
+  const size_t a = align256(S * p.T * (size_t)(p.Nfft > p.L ? p.Nfft : p.L) * es);
+  const size_t b = align256(S * p.T * (size_t)p.T * es);
+  const size_t c = align256(p.wigner ? S * p.L * (size_t)p.T * es : 0);
+  char* base = reinterpret_cast<char*>(((uintptr_t)ws + 255) & ~(uintptr_t)255);
+  return {base, base + a, base + a + b, base + a + b + c};
+}
+
+int cuda_rc(cudaError_t e) { return e == cudaSuccess ? S2GB_OK : S2GB_ECUDA; }
+
+// Run one cuFFT plan over the whole batch (q = 1) or item by item (q = 0).
+struct FftRunner {
+  Plan& p;
+  cudaStream_t st;
+  void* work;
+  int batch;
+  int run(cufftHandle* hs, const void* in, void* out, size_t item_elems, int dir) {
+    const bool whole = (batch == p.max_batch);
+    const int q = whole ? 1 : 0;
+    cufftHandle h = hs[q];
+    if (cufftSetStream(h, st) != CUFFT_SUCCESS) return S2GB_ECUFFT;
+    if (cufftSetWorkArea(h, work) != CUFFT_SUCCESS) return S2GB_ECUFFT;
+    const int reps = whole ? 1 : batch;
+    const size_t es = p.precision == S2GB_FP64 ? 16 : 8;
+    for (int r = 0; r < reps; ++r) {
+      const char* i = reinterpret_cast<const char*>(in) + r * item_elems * es;
+      char* o = reinterpret_cast<char*>(out) + r * item_elems * es;
+      cufftResult res;
+      if (p.precision == S2GB_FP64)
+        res = cufftExecZ2Z(h, (cufftDoubleComplex*)i, (cufftDoubleComplex*)o, dir);
+      else
+        res = cufftExecC2C(h, (cufftComplex*)i, (cufftComplex*)o, dir);
+      if (res != CUFFT_SUCCESS) return S2GB_ECUFFT;
+    }
+    return S2GB_OK;
+  }
+};
+
+#define S2GB_TRY(expr)            \
+  do {                            \
+    int _rc = (expr);             \
+    if (_rc != S2GB_OK) return _rc; \
+  } while (0)
+
+InvArgs inv_args(const Plan& p, const void* flm, void* out, int batch, const double* scale,
+                 long long s_sig, long long s_t, long long s_m, int m_mod) {
+  InvArgs a;
+  a.flm = flm; a.out = out; a.s_sig = s_sig; a.s_t = s_t; a.s_m = s_m; a.m_mod = m_mod;
+  a.nsig = batch; a.nN = p.nN; a.L = p.L; a.coef = p.coef; a.ring = p.ring; a.seed = p.seed;
+  a.scale = scale;
+  return a;
+}
+
+FwdArgs fwd_args(const Plan& p, const void* g, void* flm, int batch, const double* scale,
+                 long long s_sig, long long s_t, long long s_m, int m_mod, int use_nu) {
+  FwdArgs a;
+  a.g = g; a.flm = flm; a.s_sig = s_sig; a.s_t = s_t; a.s_m = s_m; a.m_mod = m_mod; a.use_nu = use_nu;
+  a.nsig = batch; a.nN = p.nN; a.L = p.L; a.coef = p.coef; a.ring = p.ring; a.seed = p.seed;
+  a.scale = scale; a.nu = p.nu;
+  return a;
+}
+
+// G (rows of length T, S*T rows, in B) -> H in B, using A as the fine-grid buffer.
+int theta_weight_operator(Plan& p, FftRunner& fr, char* A, char* B, int S) {
+  const size_t rows_item = (size_t)p.nN * p.T;
+  const int rows = S * p.T;
+  cudaStream_t st = fr.st;
+  S2GB_TRY(fr.run(p.fft_T, B, B, rows_item * p.T, CUFFT_FORWARD));
+  S2GB_TRY(cuda_rc(launch_pad(p, B, A, rows, st)));
+  S2GB_TRY(fr.run(p.fft_N, A, A, rows_item * p.Nfft, CUFFT_INVERSE));
+  S2GB_TRY(cuda_rc(launch_weight_fine(p, A, rows, st)));
+  S2GB_TRY(fr.run(p.fft_N, A, A, rows_item * p.Nfft, CUFFT_FORWARD));
+  S2GB_TRY(cuda_rc(launch_truncate(p, A, B, rows, st)));
+  S2GB_TRY(fr.run(p.fft_T, B, B, rows_item * p.T, CUFFT_INVERSE));
+  return S2GB_OK;
+}
+
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+
+int do_forward(Plan& p, const void* f, void* flm, int batch, const Workspace& w, cudaStream_t st) {
+  FftRunner fr{p, st, w.fft, batch};
+  const int S = batch * p.nN;
+  const size_t plane = (size_t)p.L * p.T;
+  const void* sig_in = f;
+  if (p.wigner) {
+    if (cufftSetStream(p.fft_gam[0], st) != CUFFT_SUCCESS) return S2GB_ECUFFT;
+    if (cufftSetWorkArea(p.fft_gam[0], w.fft) != CUFFT_SUCCESS) return S2GB_ECUFFT;
+    const size_t es = p.precision == S2GB_FP64 ? 16 : 8;
+    for (int b = 0; b < batch; ++b) {
+      const char* i = reinterpret_cast<const char*>(f) + (size_t)b * p.nN * plane * es;
+      char* o = w.C + (size_t)b * p.nN * plane * es;
+      cufftResult r = p.precision == S2GB_FP64
+          ? cufftExecZ2Z(p.fft_gam[0], (cufftDoubleComplex*)i, (cufftDoubleComplex*)o, CUFFT_FORWARD)
+          : cufftExecC2C(p.fft_gam[0], (cufftComplex*)i, (cufftComplex*)o, CUFFT_FORWARD);
+      if (r != CUFFT_SUCCESS) return S2GB_ECUFFT;
+    }
+    S2GB_TRY(cuda_rc(launch_gamma_reorder(p, w.C, w.B, batch, 1, kTwoPi / (2 * p.N - 1), st)));
+    sig_in = w.B;
+  }
+  S2GB_TRY(fr.run(p.fft_phi, sig_in, w.A, (size_t)p.nN * plane, CUFFT_FORWARD));
+  S2GB_TRY(cuda_rc(launch_extend(p, w.A, w.B, S, st)));
+  S2GB_TRY(theta_weight_operator(p, fr, w.A, w.B, S));
+  FwdArgs a = fwd_args(p, w.B, flm, batch, p.scale_fwd, (long long)p.T * p.T, 1, p.T, 0, 1);
+  return cuda_rc(launch_theta_forward(p, a, st));
+}
+
+int do_inverse(Plan& p, const void* flm, void* f, int batch, const Workspace& w, cudaStream_t st) {
+  FftRunner fr{p, st, w.fft, batch};
+  const size_t plane = (size_t)p.L * p.T;
+  InvArgs a = inv_args(p, flm, w.A, batch, p.scale_inv, (long long)plane, p.T, 1, 1);
+  S2GB_TRY(cuda_rc(launch_theta_inverse(p, a, st)));
+  if (!p.wigner) return fr.run(p.fft_phi, w.A, f, plane, CUFFT_INVERSE);
+  S2GB_TRY(fr.run(p.fft_phi, w.A, w.B, (size_t)p.nN * plane, CUFFT_INVERSE));
+  S2GB_TRY(cuda_rc(launch_gamma_reorder(p, w.B, w.C, batch, 0, 1.0, st)));
+  if (cufftSetStream(p.fft_gam[0], st) != CUFFT_SUCCESS) return S2GB_ECUFFT;
+  if (cufftSetWorkArea(p.fft_gam[0], w.fft) != CUFFT_SUCCESS) return S2GB_ECUFFT;
+  const size_t es = p.precision == S2GB_FP64 ? 16 : 8;
+  for (int b = 0; b < batch; ++b) {
+    const char* i = w.C + (size_t)b * p.nN * plane * es;
+    char* o = reinterpret_cast<char*>(f) + (size_t)b * p.nN * plane * es;
+    cufftResult r = p.precision == S2GB_FP64
+        ? cufftExecZ2Z(p.fft_gam[0], (cufftDoubleComplex*)i, (cufftDoubleComplex*)o, CUFFT_INVERSE)
+        : cufftExecC2C(p.fft_gam[0], (cufftComplex*)i, (cufftComplex*)o, CUFFT_INVERSE);
+    if (r != CUFFT_SUCCESS) return S2GB_ECUFFT;
+  }
+  return S2GB_OK;
+}
+
+int do_adjoint_inverse(Plan& p, const void* fbar, void* flmbar, int batch, const Workspace& w,
+                       cudaStream_t st) {
+  FftRunner fr{p, st, w.fft, batch};
+  const size_t plane = (size_t)p.L * p.T;
+  const void* sig_in = fbar;
+  if (p.wigner) {
+    if (cufftSetStream(p.fft_gam[0], st) != CUFFT_SUCCESS) return S2GB_ECUFFT;
+    if (cufftSetWorkArea(p.fft_gam[0], w.fft) != CUFFT_SUCCESS) return S2GB_ECUFFT;
+    const size_t es = p.precision == S2GB_FP64 ? 16 : 8;
+    for (int b = 0; b < batch; ++b) {
+      const char* i = reinterpret_cast<const char*>(fbar) + (size_t)b * p.nN * plane * es;
+      char* o = w.C + (size_t)b * p.nN * plane * es;
+      cufftResult r = p.precision == S2GB_FP64
+          ? cufftExecZ2Z(p.fft_gam[0], (cufftDoubleComplex*)i, (cufftDoubleComplex*)o, CUFFT_FORWARD)
+          : cufftExecC2C(p.fft_gam[0], (cufftComplex*)i, (cufftComplex*)o, CUFFT_FORWARD);
+      if (r != CUFFT_SUCCESS) return S2GB_ECUFFT;
+    }
+    S2GB_TRY(cuda_rc(launch_gamma_reorder(p, w.C, w.B, batch, 1, 1.0, st)));
+    sig_in = w.B;
+  }
+  S2GB_TRY(fr.run(p.fft_phi, sig_in, w.A, (size_t)p.nN * plane, CUFFT_FORWARD));
+  FwdArgs a = fwd_args(p, w.A, flmbar, batch, p.scale_inv, (long long)plane, p.T, 1, 1, 0);
+  return cuda_rc(launch_theta_forward(p, a, st));
+}
+
+int do_adjoint_forward(Plan& p, const void* flmbar, void* fbar, int batch, const Workspace& w,
+                       cudaStream_t st) {
+  FftRunner fr{p, st, w.fft, batch};
+  const int S = batch * p.nN;
+  const size_t plane = (size_t)p.L * p.T;
+  InvArgs a = inv_args(p, flmbar, w.B, batch, p.scale_fwd, (long long)p.T * p.T, 1, p.T, 0);
+  S2GB_TRY(cuda_rc(launch_theta_inverse(p, a, st)));
+  S2GB_TRY(cuda_rc(launch_nu_extend(p, w.B, S * p.T, st)));
+  S2GB_TRY(theta_weight_operator(p, fr, w.A, w.B, S));
+  S2GB_TRY(cuda_rc(launch_extend_adjoint(p, w.B, w.A, S, st)));
+  if (!p.wigner) return fr.run(p.fft_phi, w.A, fbar, plane, CUFFT_INVERSE);
+  S2GB_TRY(fr.run(p.fft_phi, w.A, w.B, (size_t)p.nN * plane, CUFFT_INVERSE));
+  S2GB_TRY(cuda_rc(launch_gamma_reorder(p, w.B, w.C, batch, 0, kTwoPi / (2 * p.N - 1), st)));
+  if (cufftSetStream(p.fft_gam[0], st) != CUFFT_SUCCESS) return S2GB_ECUFFT;
+  if (cufftSetWorkArea(p.fft_gam[0], w.fft) != CUFFT_SUCCESS) return S2GB_ECUFFT;
+  const size_t es = p.precision == S2GB_FP64 ? 16 : 8;
+  for (int b = 0; b < batch; ++b) {
+    const char* i = w.C + (size_t)b * p.nN * plane * es;
+    char* o = reinterpret_cast<char*>(fbar) + (size_t)b * p.nN * plane * es;
+    cufftResult r = p.precision == S2GB_FP64
+        ? cufftExecZ2Z(p.fft_gam[0], (cufftDoubleComplex*)i, (cufftDoubleComplex*)o, CUFFT_INVERSE)
+        : cufftExecC2C(p.fft_gam[0], (cufftComplex*)i, (cufftComplex*)o, CUFFT_INVERSE);
+    if (r != CUFFT_SUCCESS) return S2GB_ECUFFT;
+  }
+  return S2GB_OK;
+}
+
+bool overlaps(const void* a, const void* b, size_t bytes) {
+  const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+  return x < y + bytes && y < x + bytes;
+}
+
+enum class Op { Forward, Inverse, AdjForward, AdjInverse };
+
+int run(s2gb_plan plan, Op op, const void* in, void* out, int batch, void* ws, size_t ws_bytes,
+        void* stream) {
+  if (!plan || !in || !out) return S2GB_EINVAL;
+  Plan& p = plan->p;
+  if (batch < 1 || batch > p.max_batch) return S2GB_EINVAL;
+  const size_t es = p.precision == S2GB_FP64 ? 16 : 8;
+  const size_t bytes = (size_t)batch * p.nN * p.L * p.T * es;
+  if (overlaps(in, out, bytes)) return S2GB_EINVAL;
+  if (!ws || ws_bytes < workspace_bytes(p, batch)) return S2GB_EWORKSPACE;
+  DeviceGuard g(p.device);
+  std::lock_guard<std::mutex> lock(p.fft_mutex);
+  const Workspace w = carve(p, ws, batch);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  switch (op) {
+    case Op::Forward: return do_forward(p, in, out, batch, w, st);
+    case Op::Inverse: return do_inverse(p, in, out, batch, w, st);
+    case Op::AdjForward: return do_adjoint_forward(p, in, out, batch, w, st);
+    case Op::AdjInverse: return do_adjoint_inverse(p, in, out, batch, w, st);
+  }
+  return S2GB_EINVAL;
+}
+
+}  // namespace
+}  // namespace s2gb
+
+using s2gb::Op;
+
+extern "C" {
+
+int s2gb_plan_create(s2gb_plan* out, int L, int spin, int N, int sampling, int precision,
+                     int max_batch, int device) {
+  if (!out) return S2GB_EINVAL;
+  *out = nullptr;
+  if (L < 1 || L > 4096 || N < 0 || N > L || max_batch < 1 || sampling != S2GB_MW) return S2GB_EINVAL;
+  if (precision != S2GB_FP64 && precision != S2GB_FP32) return S2GB_EINVAL;
+  if (N == 0 && (spin <= -L || spin >= L)) return S2GB_EINVAL;
+  if (precision == S2GB_FP32) return S2GB_EUNSUPPORTED;
+  if (L > 2048) return S2GB_EUNSUPPORTED;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return S2GB_EINVAL;
+  s2gb_plan h = new (std::nothrow) s2gb_plan_s;
+  if (!h) return S2GB_ENOMEM;
+  s2gb::Plan& p = h->p;
+  p.L = L; p.spin = N == 0 ? spin : 0; p.N = N; p.precision = precision; p.max_batch = max_batch;
+  p.device = device;
+  int rc;
+  {
+    s2gb::DeviceGuard g(device);
+    rc = s2gb::make_plan(&p);
+    if (rc != S2GB_OK) s2gb::free_plan(&p);
+  }
+  if (rc != S2GB_OK) {
+    delete h;
+    return rc;
+  }
+  *out = h;
+  return S2GB_OK;
+}
+
+void s2gb_plan_destroy(s2gb_plan plan) {
+  if (!plan) return;
+  {
+    s2gb::DeviceGuard g(plan->p.device);
+    s2gb::free_plan(&plan->p);
+  }
+  delete plan;
+}
+
+size_t s2gb_workspace_bytes(s2gb_plan plan, int batch) {
+  if (!plan) return 0;
+  return s2gb::workspace_bytes(plan->p, batch);
+}
+
+size_t s2gb_plan_device_bytes(s2gb_plan plan) { return plan ? plan->p.device_bytes : 0; }
+
+int s2gb_forward(s2gb_plan plan, const void* f, void* flm, int batch, void* ws, size_t ws_bytes, void* stream) {
+  return s2gb::run(plan, Op::Forward, f, flm, batch, ws, ws_bytes, stream);
+}
+int s2gb_inverse(s2gb_plan plan, const void* flm, void* f, int batch, void* ws, size_t ws_bytes, void* stream) {
+  return s2gb::run(plan, Op::Inverse, flm, f, batch, ws, ws_bytes, stream);
+}
+int s2gb_adjoint_forward(s2gb_plan plan, const void* flm_bar, void* f_bar, int batch, void* ws,
+                         size_t ws_bytes, void* stream) {
+  return s2gb::run(plan, Op::AdjForward, flm_bar, f_bar, batch, ws, ws_bytes, stream);
+}
+int s2gb_adjoint_inverse(s2gb_plan plan, const void* f_bar, void* flm_bar, int batch, void* ws,
+                         size_t ws_bytes, void* stream) {
+  return s2gb::run(plan, Op::AdjInverse, f_bar, flm_bar, batch, ws, ws_bytes, stream);
+}
+
+int s2gb_inverse_theta(s2gb_plan plan, const void* flm, void* ftilde, int batch, void* stream) {
+  if (!plan || !flm || !ftilde) return S2GB_EINVAL;
+  s2gb::Plan& p = plan->p;
+  if (p.wigner) return S2GB_EUNSUPPORTED;
+  if (batch < 1 || batch > p.max_batch) return S2GB_EINVAL;
+  const size_t es = p.precision == S2GB_FP64 ? 16 : 8;
+  if (s2gb::overlaps(flm, ftilde, (size_t)batch * p.L * p.T * es)) return S2GB_EINVAL;
+  s2gb::DeviceGuard g(p.device);
+  s2gb::InvArgs a = s2gb::inv_args(p, flm, ftilde, batch, p.scale_inv, (long long)p.L * p.T, p.T, 1, 1);
+  return s2gb::cuda_rc(s2gb::launch_theta_inverse(p, a, reinterpret_cast<cudaStream_t>(stream)));
+}
+
+int s2gb_forward_theta(s2gb_plan plan, const void* gin, void* flm, int batch, void* stream) {
+  if (!plan || !gin || !flm) return S2GB_EINVAL;
+  s2gb::Plan& p = plan->p;
+  if (p.wigner) return S2GB_EUNSUPPORTED;
+  if (batch < 1 || batch > p.max_batch) return S2GB_EINVAL;
+  const size_t es = p.precision == S2GB_FP64 ? 16 : 8;
+  if (s2gb::overlaps(gin, flm, (size_t)batch * p.L * p.T * es)) return S2GB_EINVAL;
+  s2gb::DeviceGuard g(p.device);
+  s2gb::FwdArgs a = s2gb::fwd_args(p, gin, flm, batch, p.scale_fwd, (long long)p.T * p.L, 1, p.L, 0, 0);
+  return s2gb::cuda_rc(s2gb::launch_theta_forward(p, a, reinterpret_cast<cudaStream_t>(stream)));
+}
+
+const char* s2gb_strerror(int code) {
+  switch (code) {
+    case S2GB_OK: return "success";
+    case S2GB_EINVAL: return "invalid argument";
+    case S2GB_EUNSUPPORTED: return "unsupported configuration";
+    case S2GB_ENOMEM: return "device allocation failed";
+    case S2GB_ECUDA: return "CUDA runtime error";
+    case S2GB_ECUFFT: return "cuFFT error";
+    case S2GB_EWORKSPACE: return "workspace missing or too small";
+    default: return "unknown error code";
+  }
+}
+
+}  // extern "C"

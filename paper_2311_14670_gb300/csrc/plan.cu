@@ -1,0 +1,290 @@
+// Plan creation: host-side tables in extended precision, the recursion-coefficient kernel in
+// double-double arithmetic, FFT weights and cuFFT plans.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <limits>
+#include <vector>
+
+#include "dd.cuh"
+#include "s2gb_internal.h"
+
+namespace s2gb {
+
+namespace {
+
+constexpr long double kPiL = 3.141592653589793238462643383279502884197169399375105820974944L;
+constexpr double kPi = 3.14159265358979323846;
+
+// log2(k!) for k = 0..kmax, compensated running sum in long double.
+std::vector<long double> log2_factorials(int kmax) {
+  std::vector<long double> out(kmax + 1, 0.0L);
+  long double s = 0.0L, c = 0.0L;
+  for (int k = 1; k <= kmax; ++k) {
+    long double x = std::log2((long double)k);
+    long double t = s + x;
+    if (std::fabs(s) >= std::fabs(x)) c += (s - t) + x; else c += (x - t) + s;
+    s = t;
+    out[k] = s + c;
+  }
+  return out;
+}
+
+void split(long double v, double* hi, double* lo) {
+  double h = (double)v;
+  *hi = h;
+  *lo = std::isfinite(h) ? (double)(v - (long double)h) : 0.0;
+}
+
+// Recursion coefficients of the step j -> j+1 for every (n, m, j), in double-double, then rounded.
+//   d^{j+1} = A_j (cos t - B_j) d^j - C_j d^{j-1}
+//   A_j = (2j+1)(j+1) / sqrt(((j+1)^2-m^2)((j+1)^2-n^2)),  B_j = m n / (j (j+1)),
+//   C_j = (j+1) sqrt((j^2-m^2)(j^2-n^2)) / (j sqrt(((j+1)^2-m^2)((j+1)^2-n^2)))
+// (the three-term recurrence of the Wigner d-functions in the degree, obtained from the Jacobi
+// representation of Sec. 3.1 through the Jacobi polynomials' own three-term recurrence).
+// Stored per step: A, C, K_n = A(1-B), K_s = -A(1+B), Kd_n = K_n - 1 - C, Kd_s = K_s + 1 + C.
+// The Kd are differences of O(1) terms that nearly cancel for j >> |m|,|n|; evaluating them in
+// double-double keeps them accurate to a few ulps of their own size.
+__global__ void coef_kernel(double* coef, const int* n_of, int nN, int L) {
+  const int T = 2 * L - 1;
+  long long total = (long long)nN * T * L;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(idx % L);
+    const int mi = (int)((idx / L) % T);
+    const int ni = (int)(idx / ((long long)L * T));
+    const long long m = mi - (L - 1);
+    const long long n = n_of[ni];
+    double* out = coef + idx * kCoefPerStep;
+    const long long l0 = (m < 0 ? -m : m) > (n < 0 ? -n : n) ? (m < 0 ? -m : m) : (n < 0 ? -n : n);
+    if (j < l0 || j >= L - 1) {
+      for (int q = 0; q < kCoefPerStep; ++q) out[q] = 0.0;
+      continue;
+    }
+    const long long j1 = j + 1;
+    const long long X1 = (j1 * j1 - m * m) * (j1 * j1 - n * n);
+    const long long X0 = ((long long)j * j - m * m) * ((long long)j * j - n * n);
+    dd R1 = dd_sqrt(dd_from_ll(X1));
+    dd R0 = dd_sqrt(dd_from_ll(X0));
+    dd A = dd_div(dd_from_ll((2LL * j + 1) * j1), R1);
+    dd B = {0.0, 0.0}, C = {0.0, 0.0};
+    if (j > 0) {
+      B = dd_div(dd_from_ll(m * n), dd_from_ll((long long)j * j1));
+      C = dd_div(dd_mul(dd_from_ll(j1), R0), dd_mul(dd_from_ll(j), R1));
+    }
+    dd one = {1.0, 0.0};
+    dd Kn = dd_mul(A, dd_sub(one, B));
+    dd Ks = dd_neg(dd_mul(A, dd_add(one, B)));
+    dd Kdn = dd_sub(dd_sub(Kn, one), C);
+    dd Kds = dd_add(dd_add(Ks, one), C);
+    out[0] = A.hi + A.lo;
+    out[1] = C.hi + C.lo;
+    out[2] = Kn.hi + Kn.lo;
+    out[3] = Ks.hi + Ks.lo;
+    out[4] = Kdn.hi + Kdn.lo;
+    out[5] = Kds.hi + Kds.lo;
+  }
+}
+
+int good_fft_size(int n) {
+  // smallest m >= n whose prime factors are in {2, 3, 5, 7}
+  for (int m = n > 1 ? n : 1;; ++m) {
+    int r = m;
+    for (int p : {2, 3, 5, 7})
+      while (r % p == 0) r /= p;
+    if (r == 1) return m;
+  }
+}
+
+template <typename T>
+int upload(T** dst, const std::vector<T>& src, size_t* counter) {
+  size_t bytes = src.size() * sizeof(T);
+  if (cudaMalloc((void**)dst, bytes > 0 ? bytes : sizeof(T)) != cudaSuccess) return S2GB_ENOMEM;
+  *counter += bytes;
+  if (bytes && cudaMemcpy(*dst, src.data(), bytes, cudaMemcpyHostToDevice) != cudaSuccess) return S2GB_ECUDA;
+  return S2GB_OK;
+}
+
+int make_fft(cufftHandle* h, int n, int batch, int istride, int idist, cufftType type, size_t* work) {
+  if (cufftCreate(h) != CUFFT_SUCCESS) return S2GB_ECUFFT;
+  if (cufftSetAutoAllocation(*h, 0) != CUFFT_SUCCESS) return S2GB_ECUFFT;
+  int nn[1] = {n};
+  int emb[1] = {n};
+  size_t ws = 0;
+  cufftResult r = cufftMakePlanMany(*h, 1, nn, emb, istride, idist, emb, istride, idist, type, batch, &ws);
+  if (r != CUFFT_SUCCESS) return S2GB_ECUFFT;
+  if (ws > *work) *work = ws;
+  return S2GB_OK;
+}
+
+}  // namespace
+
+int make_plan(Plan* p) {
+  const int L = p->L;
+  const int T = 2 * L - 1;
+  p->T = T;
+  p->wigner = p->N >= 1;
+  p->nN = p->wigner ? 2 * p->N - 1 : 1;
+  p->Nfft = good_fft_size(4 * L - 3 > 2 * L - 1 ? 4 * L - 3 : 2 * L - 1);
+  const int nN = p->nN;
+
+  std::vector<int> n_of(nN);
+  for (int i = 0; i < nN; ++i) n_of[i] = p->wigner ? i - (p->N - 1) : -p->spin;
+
+  // ---- rings (MW, Sec. 4.2.2) ----
+  std::vector<RingData> ring(L);
+  for (int t = 0; t < L; ++t) {
+    RingData r{};
+    const bool pole = (t == L - 1);
+    long double th = pole ? kPiL : (long double)(2 * t + 1) * kPiL / (long double)T;
+    long double sh = std::sin(th / 2), ch = pole ? 0.0L : std::cos(th / 2);
+    r.north = th < kPiL / 2;
+    r.pole = pole;
+    r.v = (double)(r.north ? 2 * sh * sh : 2 * ch * ch);
+    split(std::log2(sh), &r.ls_hi, &r.ls_lo);
+    if (pole) {
+      r.lc_hi = -std::numeric_limits<double>::infinity();
+      r.lc_lo = 0.0;
+    } else {
+      split(std::log2(ch), &r.lc_hi, &r.lc_lo);
+    }
+    r.diff = std::sin(th) < (long double)kPoleSin;
+    ring[t] = r;
+  }
+
+  // ---- starting values d^{l0}_{m,n} (Eq. "initial_values" and Sec. 3.3 symmetries) ----
+  std::vector<long double> lf2 = log2_factorials(2 * L + 2);
+  std::vector<SeedData> seed((size_t)nN * T);
+  for (int ni = 0; ni < nN; ++ni) {
+    const int n = n_of[ni];
+    const int an = n < 0 ? -n : n;
+    for (int mi = 0; mi < T; ++mi) {
+      const int m = mi - (L - 1);
+      const int am = m < 0 ? -m : m;
+      SeedData s{};
+      int l0, a, b, sign;
+      if (m >= an) {            // d^m_{m,n} = sqrt((2m)!/((m+n)!(m-n)!)) (-sin)^{m-n} cos^{m+n}
+        l0 = m; a = m - n; b = m + n; sign = ((m - n) & 1) ? -1 : 1;
+      } else if (-m >= an) {    // d^l_{-l,n} = (-1)^{l+n} d^l_{l,-n}
+        l0 = -m; a = l0 + n; b = l0 - n; sign = 1;
+      } else if (n > am) {      // d^n_{m,n} = (-1)^{m-n} d^n_{n,m}
+        l0 = n; a = n - m; b = n + m; sign = 1;
+      } else {                  // n < -|m|: d^{|n|}_{m,n} = d^{|n|}_{|n|,-m}
+        l0 = -n; a = l0 + m; b = l0 - m; sign = ((l0 + m) & 1) ? -1 : 1;
+      }
+      long double pl = 0.5L * (lf2[2 * l0] - lf2[a] - lf2[b]);
+      split(pl, &s.p_hi, &s.p_lo);
+      s.l0 = l0; s.a = a; s.b = b; s.sign = sign;
+      seed[(size_t)ni * T + mi] = s;
+    }
+  }
+
+  // ---- per-degree factors ----
+  std::vector<double> sinv((size_t)nN * L), sfwd((size_t)nN * L);
+  for (int ni = 0; ni < nN; ++ni)
+    for (int l = 0; l < L; ++l) {
+      long double c;
+      if (p->wigner) {
+        sinv[(size_t)ni * L + l] = (double)((2.0L * l + 1.0L) / (8.0L * kPiL * kPiL));
+        sfwd[(size_t)ni * L + l] = 1.0;
+      } else {
+        c = std::sqrt((2.0L * l + 1.0L) / (4.0L * kPiL));
+        if (p->spin & 1) c = -c;
+        sinv[(size_t)ni * L + l] = (double)c;
+        sfwd[(size_t)ni * L + l] = (double)c;
+      }
+    }
+
+  // ---- ring fold factors and fine-grid weights of the forward quadrature ----
+  std::vector<double> nu(L, 2.0);
+  nu[L - 1] = 1.0;
+  const int NF = p->Nfft;
+  std::vector<double> wf(NF);
+  {
+    // W_B(x) = sum_{|k| <= 2L-2} What(k) e^{ikx},  What(0) = 1/pi, What(k) = 1/(pi (1-k^2)) for
+    // even k != 0 and 0 for odd k: the Fourier series of |sin x|/2, truncated.  Sampled at
+    // x_j = pi/T + 2 pi j/NF; all constants of the pipeline folded in (see api.cu).
+    const long double cst = (2.0L * kPiL / T) * (2.0L * kPiL / T) / ((long double)T * NF);
+    const long long TN2 = 2LL * T * NF;
+    for (int j = 0; j < NF; ++j) {
+      long double acc = 0.0L;
+      for (int k = 2; k <= 2 * L - 2; k += 2) {
+        long long num = ((long long)k * ((long long)NF + 2LL * j * T)) % TN2;   // k x_j = pi num/(T NF)
+        double ang = (double)num * (kPi / ((double)T * NF));
+        acc += (long double)(std::cos(ang) / (1.0 - (double)k * k));
+      }
+      wf[j] = (double)((1.0L / kPiL + (2.0L / kPiL) * acc) * cst);
+    }
+  }
+
+  size_t bytes = 0;
+  int rc;
+  if ((rc = upload(&p->ring, ring, &bytes))) return rc;
+  if ((rc = upload(&p->seed, seed, &bytes))) return rc;
+  if ((rc = upload(&p->scale_inv, sinv, &bytes))) return rc;
+  if ((rc = upload(&p->scale_fwd, sfwd, &bytes))) return rc;
+  if ((rc = upload(&p->nu, nu, &bytes))) return rc;
+  if ((rc = upload(&p->wfine, wf, &bytes))) return rc;
+  if ((rc = upload(&p->n_of, n_of, &bytes))) return rc;
+  const size_t coef_bytes = (size_t)nN * T * L * kCoefPerStep * sizeof(double);
+  if (cudaMalloc((void**)&p->coef, coef_bytes) != cudaSuccess) return S2GB_ENOMEM;
+  bytes += coef_bytes;
+  p->device_bytes = bytes;
+  coef_kernel<<<1024, 256>>>(p->coef, p->n_of, nN, L);
+  if (cudaGetLastError() != cudaSuccess) return S2GB_ECUDA;
+  if (cudaDeviceSynchronize() != cudaSuccess) return S2GB_ECUDA;
+
+  // ---- cuFFT plans ----
+  const cufftType ty = p->precision == S2GB_FP64 ? CUFFT_Z2Z : CUFFT_C2C;
+  const int S[2] = {nN, p->max_batch * nN};
+  for (int q = 0; q < 2; ++q) {
+    if (q == 1 && S[1] == S[0]) {
+      p->fft_phi[1] = p->fft_phi[0];
+      p->fft_T[1] = p->fft_T[0];
+      p->fft_N[1] = p->fft_N[0];
+      continue;
+    }
+    if ((rc = make_fft(&p->fft_phi[q], T, S[q] * L, 1, T, ty, &p->fft_work))) return rc;
+    if ((rc = make_fft(&p->fft_T[q], T, S[q] * T, 1, T, ty, &p->fft_work))) return rc;
+    if ((rc = make_fft(&p->fft_N[q], NF, S[q] * T, 1, NF, ty, &p->fft_work))) return rc;
+    p->fft_made[q] = true;
+  }
+  if (p->wigner) {
+    const int K = 2 * p->N - 1;
+    if ((rc = make_fft(&p->fft_gam[0], K, L * T, L * T, 1, ty, &p->fft_work))) return rc;
+    p->fft_gam_made = true;
+  }
+  return S2GB_OK;
+}
+
+void free_plan(Plan* p) {
+  cudaFree(p->coef);
+  cudaFree(p->ring);
+  cudaFree(p->seed);
+  cudaFree(p->scale_inv);
+  cudaFree(p->scale_fwd);
+  cudaFree(p->nu);
+  cudaFree(p->wfine);
+  cudaFree(p->n_of);
+  for (int q = 0; q < 2; ++q)
+    if (p->fft_made[q]) {
+      cufftDestroy(p->fft_phi[q]);
+      cufftDestroy(p->fft_T[q]);
+      cufftDestroy(p->fft_N[q]);
+    }
+  if (p->fft_gam_made) cufftDestroy(p->fft_gam[0]);
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+size_t workspace_bytes(const Plan& p, int batch) {
+  if (batch < 1 || batch > p.max_batch) return 0;
+  const size_t es = p.precision == S2GB_FP64 ? 16 : 8;
+  const size_t S = (size_t)batch * p.nN;
+  const size_t bufA = S * p.T * (size_t)(p.Nfft > p.L ? p.Nfft : p.L) * es;
+  const size_t bufB = S * p.T * (size_t)p.T * es;
+  const size_t bufC = p.wigner ? S * p.L * (size_t)p.T * es : 0;
+  return align256(bufA) + align256(bufB) + align256(bufC) + align256(p.fft_work) + 256;
+}
+
+}  // namespace s2gb

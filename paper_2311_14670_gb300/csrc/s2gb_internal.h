@@ -1,0 +1,128 @@
+// Internal declarations shared by the translation units of libs2gb.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cufft.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <mutex>
+#include <vector>
+
+#include "../../include/s2gb.h"
+
+namespace s2gb {
+
+// Rings whose sin(theta) is below this use the difference form of the l-recursion (see
+// theta_kernels.cu): there the plain three-term recurrence amplifies rounding by ~1/sin(theta).
+constexpr double kPoleSin = 0.15;
+
+// Per-ring data, host-computed in extended precision and rounded once.
+struct RingData {
+  double v;        // 2 sin^2(theta/2) for north rings (theta < pi/2), 2 cos^2(theta/2) for south
+  double ls_hi;    // log2 sin(theta/2) as an unevaluated double-double (hi + lo)
+  double ls_lo;
+  double lc_hi;    // log2 cos(theta/2) (lc_hi = -inf at theta = pi)
+  double lc_lo;
+  int north;       // theta < pi/2
+  int pole;        // theta == pi (last MW ring)
+  int diff;        // sin(theta) < kPoleSin: difference form of the recursion
+  int pad;
+};
+
+// Per (n, m) data of the starting value d^{l0}_{m,n}, l0 = max(|m|,|n|) (Eq. "initial_values"
+// plus the symmetries of Sec. 3.3): d = sign * 2^{p} * sin(theta/2)^a * cos(theta/2)^b with
+// p = log2 sqrt((2 l0)! / (a! b!)), a + b = 2 l0.
+struct SeedData {
+  double p_hi;
+  double p_lo;
+  int l0;
+  int a;
+  int b;
+  int sign;
+};
+
+// Recursion step j -> j+1 coefficients for one (n, m), see theta_kernels.cu.
+constexpr int kCoefPerStep = 6;  // A, C, K_north, K_south, Kd_north, Kd_south
+
+struct Plan {
+  int L = 0, spin = 0, N = 0, precision = 0, max_batch = 0, device = 0;
+  int T = 0;        // 2L - 1
+  int nN = 1;       // number of n values (1 for the sphere, 2N-1 for Wigner)
+  int Nfft = 0;     // length of the fine theta grid of the forward quadrature (>= 4L-3)
+  bool wigner = false;
+
+  // device tables
+  double* coef = nullptr;      // [nN][T][L][kCoefPerStep]  (m index = m + L - 1, step j)
+  RingData* ring = nullptr;    // [L]
+  SeedData* seed = nullptr;    // [nN][T]
+  double* scale_inv = nullptr; // [nN][L] per-degree factor of the inverse theta stage
+  double* scale_fwd = nullptr; // [nN][L] per-degree factor of the forward theta stage
+  double* wfine = nullptr;     // [Nfft] weights on the fine grid (constants folded in)
+  double* nu = nullptr;        // [L] ring fold factors of the forward quadrature (2, ..., 2, 1)
+  int* n_of = nullptr;         // [nN] n for each n index
+  size_t device_bytes = 0;
+
+  // cuFFT plans: index 0 = one signal, 1 = max_batch signals (rows of the whole batch)
+  cufftHandle fft_phi[2] = {0, 0};   // length T along rows of length T, S*L rows
+  cufftHandle fft_T[2] = {0, 0};     // length T, S*T rows
+  cufftHandle fft_N[2] = {0, 0};     // length Nfft, S*T rows
+  cufftHandle fft_gam[1] = {0};      // length 2N-1, stride L*T, L*T rows (one signal)
+  bool fft_made[2] = {false, false};
+  bool fft_gam_made = false;
+  size_t fft_work = 0;               // max cuFFT work area over all plans
+  std::mutex fft_mutex;
+};
+
+// ---- kernels (theta_kernels.cu) ----
+struct InvArgs {
+  const void* flm;      // [S][L][T] coefficients (S = batch * nN signals)
+  void* out;            // output with strides below
+  long long s_sig;      // stride between signals in out (elements)
+  long long s_t;        // stride between rings
+  long long s_m;        // stride between orders
+  int m_mod;            // 1: column = m mod T, 0: column = m + L - 1
+  int nsig;             // number of signals per n (batch)
+  int nN;
+  int L;
+  const double* coef;
+  const RingData* ring;
+  const SeedData* seed;
+  const double* scale;  // [nN][L]
+};
+
+struct FwdArgs {
+  const void* g;        // input with strides below
+  void* flm;            // [S][L][T]
+  long long s_sig, s_t, s_m;
+  int m_mod;
+  int use_nu;           // multiply g by the fold factors nu_t
+  int nsig;
+  int nN;
+  int L;
+  const double* coef;
+  const RingData* ring;
+  const SeedData* seed;
+  const double* scale;
+  const double* nu;
+};
+
+cudaError_t launch_theta_inverse(const Plan& p, const InvArgs& a, cudaStream_t st);
+cudaError_t launch_theta_forward(const Plan& p, const FwdArgs& a, cudaStream_t st);
+
+// ---- glue kernels (glue.cu) ----
+cudaError_t launch_extend(const Plan& p, const void* F, void* G, int nsig, cudaStream_t st);
+cudaError_t launch_extend_adjoint(const Plan& p, const void* G, void* F, int nsig, cudaStream_t st);
+cudaError_t launch_pad(const Plan& p, const void* X, void* Y, int rows, cudaStream_t st);
+cudaError_t launch_truncate(const Plan& p, const void* Y, void* X, int rows, cudaStream_t st);
+cudaError_t launch_weight_fine(const Plan& p, void* Y, int rows, cudaStream_t st);
+cudaError_t launch_nu_extend(const Plan& p, void* X, int rows, cudaStream_t st);
+cudaError_t launch_gamma_reorder(const Plan& p, const void* in, void* out, int batch, int to_signal,
+                                 double scale, cudaStream_t st);
+
+// ---- plan helpers (plan.cu) ----
+int make_plan(Plan* p);
+void free_plan(Plan* p);
+size_t workspace_bytes(const Plan& p, int batch);
+
+}  // namespace s2gb

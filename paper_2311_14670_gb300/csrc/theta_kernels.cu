@@ -1,0 +1,468 @@
+// Theta stages of the spin-s SHT (Sec. 4.1, Eqs. disc_ish_expanded and disc_sh_expanded) with the
+// Wigner d-functions generated on the fly and interleaved with the contraction (Sec. 4.4).
+//
+// Recursion.  For fixed (m, n, theta) the functions d^j_{mn}(theta) obey, for j >= l0 =
+// max(|m|,|n|) and with d^{l0-1} = 0, the three-term recurrence in the degree
+//     d^{j+1} = A_j (cos theta - B_j) d^j - C_j d^{j-1}
+// (coefficients in plan.cu).  Each thread owns KT (m, theta) chains; the state lives in registers.
+// Ascending j the wanted solution dominates, so the recurrence is stable.  It is run in the
+// half-angle variable v = 2 sin^2(theta/2) (north rings) or v = 2 cos^2(theta/2) (south rings),
+//     P_j = A_j (cos theta - B_j) = K_n - A_j v   or   K_s + A_j v,
+// because cos theta itself cannot resolve theta near the poles (an error of one ulp in cos theta
+// shifts d^l by ~l^2 ulp there).  On rings with sin(theta) < kPoleSin the recurrence is nearly
+// degenerate (its characteristic roots approach +-1) and amplifies rounding of the state by
+// ~1/sin(theta); there the "difference form" carries e^j = d^j - sigma d^{j-1} (sigma = +1 north,
+// -1 south):
+//     e^{j+1} = (P_j - sigma (1 + C_j)) d^j + sigma C_j e^j,    d^{j+1} = sigma d^j + e^{j+1},
+// whose coefficient P_j - sigma(1+C_j) = Kd - (+-A_j v) is small and precomputed accurately.
+//
+// Range.  Starting values d^{l0} (Eq. "initial_values" via the symmetries of Sec. 3.3) can be as
+// small as 2^-20000.  A chain keeps its value as x * 2^-E with an integer E >= 0.  While E > 0 the
+// chain is "dead": its true magnitude is below 2^-kLiveThr and it contributes nothing (exactly as
+// in float64, where such products vanish against the O(1) sum).  Every few steps the exponent of x
+// is inspected on the integer pipe: a chain whose true magnitude has grown past 2^-kLiveThr is
+// converted to unscaled form (E = 0) and contributes from then on; a dead chain whose x grew past
+// 2^kRescale is rescaled by an exact power of two.  Once unscaled, |d| <= 1 and never underflows
+// (ascending l leaves the forbidden region for good), so no further checks are needed.  This is
+// the running renormalisation of Sec. 3.4 in exact power-of-two form.
+#include <cuda_runtime.h>
+
+#include "dd.cuh"
+#include "s2gb_internal.h"
+
+namespace s2gb {
+
+namespace {
+
+constexpr int kLiveThr = 400;   // dead while |d| < 2^-400
+constexpr int kRescale = 256;   // rescale dead chains when x exceeds 2^256
+
+__device__ __forceinline__ double pow2i(int e) {          // 2^e, -1022 <= e <= 1023
+  return __hiloint2double((1023 + e) << 20, 0);
+}
+__device__ __forceinline__ int exp_of(double x) {         // unbiased exponent field of x
+  return ((__double2hiint(x) >> 20) & 0x7ff) - 1023;
+}
+__device__ __forceinline__ double flip_sign(double x, unsigned mask) {
+  return __hiloint2double(__double2hiint(x) ^ (int)mask, __double2loint(x));
+}
+
+// d^{l0}_{m,n}(theta) = sign 2^p sin(theta/2)^a cos(theta/2)^b, evaluated as 2^X with X in
+// double-double, returned as x * 2^-E (E = 0 if the value is not tiny).
+__device__ __forceinline__ void seed_value(const SeedData& sd, const RingData& rd, double& x, int& E) {
+  if ((rd.pole && sd.b > 0)) { x = 0.0; E = 0; return; }      // cos(pi/2) = 0
+  dd X = {sd.p_hi, sd.p_lo};
+  if (sd.a) {
+    dd t = two_prod(rd.ls_hi, (double)sd.a);
+    t.lo = fma(rd.ls_lo, (double)sd.a, t.lo);
+    X = dd_add(X, t);
+  }
+  if (sd.b) {
+    dd t = two_prod(rd.lc_hi, (double)sd.b);
+    t.lo = fma(rd.lc_lo, (double)sd.b, t.lo);
+    X = dd_add(X, t);
+  }
+  double Eh = floor(X.hi);
+  double f = (X.hi - Eh) + X.lo;
+  if (f < 0.0) { f += 1.0; Eh -= 1.0; }
+  if (f >= 1.0) { f -= 1.0; Eh += 1.0; }
+  double mant = exp2(f);
+  if (sd.sign < 0) mant = -mant;
+  int e = (int)Eh;
+  if (e >= -kLiveThr) { x = mant * pow2i(e); E = 0; }
+  else { x = mant; E = -e; }
+}
+
+// Dead-chain bookkeeping (see file comment).  Only touches chains with E > 0.
+__device__ __forceinline__ void renorm(double& x, double& y, int& E) {
+  if (E > 0 && ((__double2hiint(x) & 0x7fffffff) | __double2loint(x)) != 0) {
+    const int ex = exp_of(x);
+    if (ex - E >= -kLiveThr) {
+      const double s = pow2i(-E);
+      x *= s; y *= s; E = 0;
+    } else if (ex > kRescale) {
+      const double s = pow2i(-ex);
+      x *= s; y *= s; E -= ex;
+    }
+  }
+}
+
+struct StepCoef {
+  double A, C, Kn, Ks, Kdn, Kds;
+};
+
+__device__ __forceinline__ StepCoef load_coef(const double* c) {
+  const double2* c2 = reinterpret_cast<const double2*>(c);
+  double2 a = __ldg(c2), b = __ldg(c2 + 1), d = __ldg(c2 + 2);
+  return {a.x, a.y, b.x, b.y, d.x, d.y};
+}
+
+// One recursion step of a chain. north/diff are per-chain constants.
+template <bool DIFF>
+__device__ __forceinline__ void step(double& x, double& y, double v, unsigned north_mask, bool north,
+                                     const StepCoef& c) {
+  // sA = -A on north rings, +A on south rings
+  const double sA = flip_sign(c.A, north_mask);
+  if (!DIFF) {
+    const double K = north ? c.Kn : c.Ks;
+    const double P = fma(sA, v, K);
+    const double xn = fma(P, x, -(c.C * y));
+    y = x;
+    x = xn;
+  } else {
+    const double K = north ? c.Kdn : c.Kds;
+    const double Q = fma(sA, v, K);
+    const double sC = flip_sign(c.C, north_mask ^ 0x80000000u);   // +C north, -C south
+    const double en = fma(Q, x, sC * y);
+    const double sg = north ? 1.0 : -1.0;                          // sigma
+    x = fma(sg, x, en);
+    y = en;
+  }
+}
+
+__device__ __forceinline__ int m_of_rank(int r) {   // 0, -1, 1, -2, 2, ...: longest chains first
+  return (r == 0) ? 0 : ((r & 1) ? -((r + 1) >> 1) : (r >> 1));
+}
+
+// ------------------------------------------------------------------------------------------
+// Inverse theta stage: out[sig][t][m] = sum_{l >= l0} scale_l flm[sig][l][m] d^l_{m,n}(theta_t).
+// Grid: x = (rank of m) * ntiles + tile, y = n index, z = batch group of NB signals.
+// Each thread owns KT rings t = tile*KT*blockDim + i*blockDim + threadIdx.x.  The coefficients
+// flm[.][l][m] * scale_l for a chunk of kChunk degrees are staged in shared memory.
+// ------------------------------------------------------------------------------------------
+constexpr int kChunk = 32;
+
+template <int KT, int NB, bool DIFF>
+__device__ __forceinline__ void inverse_body(const InvArgs& a, int m, int ni, int tile, int l0,
+                                             double2* __restrict__ hs, double* __restrict__ cs) {
+  const int L = a.L, T = 2 * L - 1;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int mi = m + L - 1;
+  const int sig0 = blockIdx.z * NB;
+  const SeedData sd = a.seed[(size_t)ni * T + mi];
+  const double* coef_m = a.coef + ((size_t)ni * T + mi) * (size_t)L * kCoefPerStep;
+
+  double x[KT], y[KT], v[KT];
+  int E[KT], tt[KT];
+  bool north[KT];
+  unsigned nmask[KT];
+  double2 acc[KT][NB];
+#pragma unroll
+  for (int i = 0; i < KT; ++i) {
+    const int t = tile * KT * nt + i * nt + tid;
+    tt[i] = t;
+    if (t < L) {
+      const RingData rd = a.ring[t];
+      seed_value(sd, rd, x[i], E[i]);
+      v[i] = rd.v;
+      north[i] = rd.north;
+    } else {
+      x[i] = 0.0; E[i] = 0; v[i] = 0.0; north[i] = true;
+    }
+    nmask[i] = north[i] ? 0x80000000u : 0u;
+    y[i] = DIFF ? x[i] : 0.0;   // plain: d^{l0-1} = 0;  difference form: e^{l0} = d^{l0}
+#pragma unroll
+    for (int b = 0; b < NB; ++b) acc[i][b] = make_double2(0.0, 0.0);
+  }
+
+  const double* scale = a.scale + (size_t)ni * L;
+  for (int jc = l0; jc < L; jc += kChunk) {
+    __syncthreads();
+    for (int q = tid; q < kChunk * NB; q += nt) {
+      const int jj = q / NB, b = q % NB, j = jc + jj, sig = sig0 + b;
+      double2 h = make_double2(0.0, 0.0);
+      if (j < L && sig < a.nsig) {
+        const double2* f = reinterpret_cast<const double2*>(a.flm) +
+                           ((size_t)(sig * a.nN + ni) * L + j) * T + mi;
+        h = *f;
+        const double s = scale[j];
+        h.x *= s; h.y *= s;
+      }
+      hs[q] = h;
+    }
+    for (int q = tid; q < kChunk * kCoefPerStep; q += nt) {
+      const int j = jc + q / kCoefPerStep;
+      cs[q] = (j < L) ? coef_m[(size_t)jc * kCoefPerStep + q] : 0.0;
+    }
+    __syncthreads();
+    const int jend = min(kChunk, L - jc);
+    for (int j8 = 0; j8 < jend; j8 += 8) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int jj = j8 + u;
+        if (jj < jend) {
+#pragma unroll
+          for (int i = 0; i < KT; ++i) {
+            const double xl = (E[i] == 0) ? x[i] : 0.0;
+#pragma unroll
+            for (int b = 0; b < NB; ++b) {
+              const double2 h = hs[jj * NB + b];
+              acc[i][b].x = fma(xl, h.x, acc[i][b].x);
+              acc[i][b].y = fma(xl, h.y, acc[i][b].y);
+            }
+          }
+          if (jc + jj < L - 1) {
+            const double* cp = cs + jj * kCoefPerStep;
+            const StepCoef c = {cp[0], cp[1], cp[2], cp[3], cp[4], cp[5]};
+#pragma unroll
+            for (int i = 0; i < KT; ++i) step<DIFF>(x[i], y[i], v[i], nmask[i], north[i], c);
+          }
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < KT; ++i) renorm(x[i], y[i], E[i]);
+    }
+  }
+
+#pragma unroll
+  for (int i = 0; i < KT; ++i) {
+    if (tt[i] < L) {
+      const long long col = a.m_mod ? (m >= 0 ? m : m + T) : mi;
+#pragma unroll
+      for (int b = 0; b < NB; ++b) {
+        const int sig = sig0 + b;
+        if (sig < a.nsig) {
+          double2* o = reinterpret_cast<double2*>(a.out) + (size_t)(sig * a.nN + ni) * a.s_sig +
+                       tt[i] * a.s_t + col * a.s_m;
+          *o = acc[i][b];
+        }
+      }
+    }
+  }
+}
+
+template <int KT, int NB>
+__global__ void __launch_bounds__(128) theta_inverse_kernel(InvArgs a, int ntiles) {
+  __shared__ double2 hs[kChunk * NB];
+  __shared__ double cs[kChunk * kCoefPerStep];
+  const int L = a.L;
+  const int rank = blockIdx.x / ntiles, tile = blockIdx.x % ntiles;
+  const int m = m_of_rank(rank);
+  const int ni = blockIdx.y;
+  const int n = a.seed[(size_t)ni * (2 * L - 1) + m + L - 1].l0;  // l0 = max(|m|,|n|)
+  const int l0 = n;
+  // Does this tile contain a ring that needs the difference form?
+  const int t_lo = tile * KT * blockDim.x, t_hi = min(L, t_lo + KT * (int)blockDim.x) - 1;
+  const bool diff = a.ring[t_lo].diff || a.ring[t_hi].diff;
+  if (diff) inverse_body<KT, NB, true>(a, m, ni, tile, l0, hs, cs);
+  else inverse_body<KT, NB, false>(a, m, ni, tile, l0, hs, cs);
+}
+
+// ------------------------------------------------------------------------------------------
+// Forward theta stage: flm[sig][l][m] = scale_l sum_t d^l_{m,n}(theta_t) g[sig][m][t] (* nu_t).
+// One CTA per (m, n, batch group) owns all L rings: thread tid holds rings t = i*blockDim + tid.
+// Per degree every thread forms partial sums over its KT rings (FMA chains); partial sums of
+// JR = 16/NB consecutive degrees (32 doubles) are reduced across the warp by a reduce-scatter
+// (31 additions per lane for 32 values, lane l ends with value l), then across warps through
+// shared memory in a fixed order: the result is deterministic.
+// The difference form is used on the first and the last ring slot, which hold the polar caps
+// (sin theta < kPoleSin covers fewer than L/20 rings at either end, and a slot holds >= L/16), or
+// on all slots when PAT == 1.
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ double warp_reduce_scatter32(double (&v)[32]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int w = 16; w >= 1; w >>= 1) {
+    const bool up = (lane & w) != 0;
+#pragma unroll
+    for (int s = 0; s < w; ++s) {
+      const double send = up ? v[s] : v[s + w];
+      const double keep = up ? v[s + w] : v[s];
+      v[s] = keep + __shfl_xor_sync(0xffffffffu, send, w);
+    }
+  }
+  return v[0];
+}
+
+// Ring owned by slot i of thread `tid` in the forward kernel.  The last slot always holds the
+// last nt rings (the south polar cap), slot 0 the first nt (the north cap); middle-slot chains that
+// would repeat a ring of the last slot are inactive.
+template <int KT>
+__device__ __forceinline__ int ring_of(int i, int tid, int nt, int L, bool& active) {
+  if (KT == 1) { active = tid < L; return tid; }
+  if (i == KT - 1) { active = true; return L - nt + tid; }
+  const int t = i * nt + tid;
+  active = t < L - nt;
+  return t;
+}
+
+template <int KT, int NB, int PAT>
+__global__ void __launch_bounds__(128) theta_forward_kernel(FwdArgs a) {
+  constexpr int JR = 16 / NB;            // degrees per reduction group
+  extern __shared__ double2 smem[];
+  const int L = a.L, T = 2 * L - 1;
+  const int nt = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nwarps = nt >> 5;
+  const int rows = KT * nt;                // padded ring count
+  double2* gs = smem;                                          // [NB][rows]
+  double* red = reinterpret_cast<double*>(gs + NB * rows);    // [2][nwarps][32]
+  double* vs = red + 2 * nwarps * 32;                          // [rows]
+
+  const int m = m_of_rank(blockIdx.x);
+  const int mi = m + L - 1;
+  const int ni = blockIdx.y;
+  const int sig0 = blockIdx.z * NB;
+  const SeedData sd = a.seed[(size_t)ni * T + mi];
+  const int l0 = sd.l0;
+  const double* scale = a.scale + (size_t)ni * L;
+
+  // zero the degrees l < l0 of this column
+  for (int q = tid; q < NB * min(l0, L); q += nt) {
+    const int b = q / min(l0, L), j = q % min(l0, L), sig = sig0 + b;
+    if (sig < a.nsig)
+      reinterpret_cast<double2*>(a.flm)[((size_t)(sig * a.nN + ni) * L + j) * T + mi] = make_double2(0.0, 0.0);
+  }
+  if (l0 >= L) return;
+
+  // stage g (times the ring fold factors) and the ring variables
+  const long long col = a.m_mod ? (m >= 0 ? m : m + T) : mi;
+  for (int q = tid; q < NB * rows; q += nt) {
+    const int b = q / rows, pos = q % rows, sig = sig0 + b;
+    bool act;
+    const int t = ring_of<KT>(pos / nt, pos % nt, nt, L, act);
+    double2 g = make_double2(0.0, 0.0);
+    if (act && sig < a.nsig) {
+      g = reinterpret_cast<const double2*>(a.g)[(size_t)(sig * a.nN + ni) * a.s_sig + t * a.s_t + col * a.s_m];
+      if (a.use_nu) { const double w = a.nu[t]; g.x *= w; g.y *= w; }
+    }
+    gs[q] = g;
+  }
+  for (int pos = tid; pos < rows; pos += nt) {
+    bool act;
+    const int t = ring_of<KT>(pos / nt, pos % nt, nt, L, act);
+    vs[pos] = act ? a.ring[t].v : 0.0;
+  }
+  __syncthreads();
+
+  double x[KT], y[KT];
+  int E[KT];
+  bool north[KT];
+  unsigned nmask[KT];
+#pragma unroll
+  for (int i = 0; i < KT; ++i) {
+    bool act;
+    const int t = ring_of<KT>(i, tid, nt, L, act);
+    if (act) {
+      const RingData rd = a.ring[t];
+      seed_value(sd, rd, x[i], E[i]);
+      north[i] = rd.north;
+    } else {
+      x[i] = 0.0; E[i] = 0; north[i] = true;
+    }
+    nmask[i] = north[i] ? 0x80000000u : 0u;
+    const bool dslot = (PAT == 1) || i == 0 || i == KT - 1;
+    y[i] = dslot ? x[i] : 0.0;
+  }
+
+  const double* coef_m = a.coef + ((size_t)ni * T + mi) * (size_t)L * kCoefPerStep;
+  int buf = 0;
+  for (int j0 = l0; j0 < L; j0 += JR) {
+    double p[32];
+#pragma unroll
+    for (int s = 0; s < 32; ++s) p[s] = 0.0;
+#pragma unroll
+    for (int jr = 0; jr < JR; ++jr) {
+      const int j = j0 + jr;
+      if (j < L) {
+#pragma unroll
+        for (int i = 0; i < KT; ++i) {
+          const double xl = (E[i] == 0) ? x[i] : 0.0;
+          const int pos = i * nt + tid;
+#pragma unroll
+          for (int b = 0; b < NB; ++b) {
+            const double2 g = gs[b * rows + pos];
+            p[jr * 2 * NB + 2 * b] = fma(xl, g.x, p[jr * 2 * NB + 2 * b]);
+            p[jr * 2 * NB + 2 * b + 1] = fma(xl, g.y, p[jr * 2 * NB + 2 * b + 1]);
+          }
+        }
+        if (j < L - 1) {
+          const StepCoef c = load_coef(coef_m + (size_t)j * kCoefPerStep);
+#pragma unroll
+          for (int i = 0; i < KT; ++i) {
+            const double v = vs[i * nt + tid];
+            const bool dslot = (PAT == 1) || i == 0 || i == KT - 1;
+            if (dslot) step<true>(x[i], y[i], v, nmask[i], north[i], c);
+            else step<false>(x[i], y[i], v, nmask[i], north[i], c);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < KT; ++i) renorm(x[i], y[i], E[i]);
+
+    // reduce the 32 partial sums of this group
+    const double s = warp_reduce_scatter32(p);
+    red[(buf * nwarps + warp) * 32 + lane] = s;
+    __syncthreads();
+    if (warp == 0) {
+      double tot = red[(buf * nwarps) * 32 + lane];
+      for (int w = 1; w < nwarps; ++w) tot += red[(buf * nwarps + w) * 32 + lane];
+      const int jr = lane / (2 * NB), b = (lane / 2) % NB, reim = lane & 1;
+      const int j = j0 + jr, sig = sig0 + b;
+      if (j < L && sig < a.nsig) {
+        double* o = reinterpret_cast<double*>(
+            reinterpret_cast<double2*>(a.flm) + ((size_t)(sig * a.nN + ni) * L + j) * T + mi);
+        o[reim] = tot * scale[j];
+      }
+    }
+    buf ^= 1;
+  }
+}
+
+template <int KT, int NB>
+cudaError_t launch_inv(const Plan& p, const InvArgs& a, cudaStream_t st) {
+  const int nt = 128;
+  const int ntiles = (p.L + KT * nt - 1) / (KT * nt);
+  dim3 grid(p.T * ntiles, a.nN, (a.nsig + NB - 1) / NB);
+  theta_inverse_kernel<KT, NB><<<grid, nt, 0, st>>>(a, ntiles);
+  return cudaGetLastError();
+}
+
+template <int NB>
+cudaError_t launch_inv_nb(const Plan& p, const InvArgs& a, cudaStream_t st) {
+  if (p.L <= 128) return launch_inv<1, NB>(p, a, st);
+  if (p.L <= 512) return launch_inv<2, NB>(p, a, st);
+  return launch_inv<4, NB>(p, a, st);
+}
+
+template <int KT, int NB, int PAT>
+cudaError_t launch_fwd(const Plan& p, const FwdArgs& a, int nt, cudaStream_t st) {
+  const int rows = KT * nt;
+  const size_t smem = sizeof(double2) * NB * rows + sizeof(double) * (2 * (nt / 32) * 32 + rows);
+  auto kern = theta_forward_kernel<KT, NB, PAT>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid(p.T, a.nN, (a.nsig + NB - 1) / NB);
+  kern<<<grid, nt, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <int NB>
+cudaError_t launch_fwd_nb(const Plan& p, const FwdArgs& a, cudaStream_t st) {
+  const int L = p.L;
+  if (L <= 128) return launch_fwd<1, NB, 1>(p, a, ((L + 31) / 32) * 32, st);
+  if (L <= 256) return launch_fwd<2, NB, 1>(p, a, 128, st);
+  if (L <= 512) return launch_fwd<4, NB, 0>(p, a, 128, st);
+  if (L <= 1024) return launch_fwd<8, NB, 0>(p, a, 128, st);
+  // KT = 16 slots of nt rings: the polar caps (sin theta < kPoleSin, t < 0.05 L) fit in the
+  // first and last slot because nt >= L/16.
+  const int nt = ((L + 16 * 32 - 1) / (16 * 32)) * 32;
+  if (nt > 128) return cudaErrorInvalidConfiguration;  // L > 2048: 128-thread launch bound
+  return launch_fwd<16, NB, 0>(p, a, nt, st);
+}
+
+}  // namespace
+
+cudaError_t launch_theta_inverse(const Plan& p, const InvArgs& a, cudaStream_t st) {
+  if (a.nsig >= 4) return launch_inv_nb<4>(p, a, st);
+  if (a.nsig >= 2) return launch_inv_nb<2>(p, a, st);
+  return launch_inv_nb<1>(p, a, st);
+}
+
+cudaError_t launch_theta_forward(const Plan& p, const FwdArgs& a, cudaStream_t st) {
+  if (a.nsig >= 4 && p.L <= 1024) return launch_fwd_nb<4>(p, a, st);
+  if (a.nsig >= 2) return launch_fwd_nb<2>(p, a, st);
+  return launch_fwd_nb<1>(p, a, st);
+}
+
+}  // namespace s2gb

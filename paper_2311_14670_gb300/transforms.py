@@ -1,0 +1,168 @@
+"""PyTorch-facing wrappers of libs2gb.so: plans, transforms on CUDA tensors, autograd.
+
+Tensors are complex CUDA tensors laid out as in ``include/s2gb.h``:
+  sphere:  f, flm of shape (batch, L, 2L-1)
+  Wigner:  f, flmn of shape (batch, 2N-1, L, 2L-1)
+complex128 for ``precision="fp64"`` plans, complex64 for ``"fp32"``.  Every call enqueues on
+PyTorch's current stream of the plan's device.  The autograd functions use the hand-written adjoint
+transforms for the backward pass (Sec. 5.2), which recompute the Wigner d-functions instead of
+storing anything.
+"""
+from __future__ import annotations
+
+import threading
+
+import torch
+
+from . import _native as nat
+
+_PRECISIONS = {"fp64": (nat.S2GB_FP64, torch.complex128), "fp32": (nat.S2GB_FP32, torch.complex64)}
+
+
+class Plan:
+    """A transform plan (``s2gb_plan_create``) plus a per-batch-size workspace cache."""
+
+    def __init__(self, L: int, spin: int = 0, N: int = 0, precision: str = "fp64", max_batch: int = 1,
+                 device: int | torch.device | None = None, sampling: str = "mw"):
+        if sampling != "mw":
+            raise ValueError("only MW sampling is implemented")
+        if precision not in _PRECISIONS:
+            raise ValueError(f"precision must be one of {list(_PRECISIONS)}")
+        if device is None:
+            device = torch.cuda.current_device()
+        if isinstance(device, torch.device):
+            device = device.index if device.index is not None else torch.cuda.current_device()
+        self.L, self.spin, self.N, self.precision, self.max_batch = int(L), int(spin), int(N), precision, int(max_batch)
+        self.device = torch.device("cuda", int(device))
+        self.dtype = _PRECISIONS[precision][1]
+        self._h = nat.plan_create(self.L, self.spin, self.N, nat.S2GB_MW, _PRECISIONS[precision][0],
+                                  self.max_batch, int(device))
+        self._ws = {}
+        self._lock = threading.Lock()
+
+    # ---------------------------------------------------------------- shapes
+    @property
+    def wigner(self) -> bool:
+        return self.N >= 1
+
+    def shape(self, batch: int) -> tuple:
+        T = 2 * self.L - 1
+        return (batch, 2 * self.N - 1, self.L, T) if self.wigner else (batch, self.L, T)
+
+    def workspace_bytes(self, batch: int) -> int:
+        return nat.workspace_bytes(self._h, batch)
+
+    def device_bytes(self) -> int:
+        return nat.plan_device_bytes(self._h)
+
+    def workspace(self, batch: int) -> torch.Tensor:
+        with self._lock:
+            ws = self._ws.get(batch)
+            if ws is None:
+                ws = torch.empty(self.workspace_bytes(batch), dtype=torch.uint8, device=self.device)
+                self._ws[batch] = ws
+            return ws
+
+    def _check(self, x: torch.Tensor, name: str) -> int:
+        if not isinstance(x, torch.Tensor) or x.device != self.device:
+            raise ValueError(f"{name} must be a tensor on {self.device}")
+        if x.dtype != self.dtype:
+            raise TypeError(f"{name} must have dtype {self.dtype}, got {x.dtype}")
+        if not x.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        batch = x.shape[0] if x.dim() == len(self.shape(1)) else None
+        if batch is None or tuple(x.shape) != self.shape(batch):
+            raise ValueError(f"{name} has shape {tuple(x.shape)}, expected {self.shape(batch or 1)}")
+        if not 1 <= batch <= self.max_batch:
+            raise ValueError(f"batch {batch} outside [1, {self.max_batch}]")
+        return batch
+
+    def _stream(self) -> int:
+        return torch.cuda.current_stream(self.device).cuda_stream
+
+    def _run(self, name: str, x: torch.Tensor, out: torch.Tensor | None, ws: torch.Tensor | None):
+        batch = self._check(x, "input")
+        if out is None:
+            out = torch.empty(self.shape(batch), dtype=self.dtype, device=self.device)
+        else:
+            self._check(out, "out")
+        if ws is None:
+            ws = self.workspace(batch)
+        getattr(nat, name)(self._h, x, out, batch, ws, ws.numel(), self._stream())
+        return out
+
+    # ---------------------------------------------------------------- transforms (no autograd)
+    def forward(self, f, out=None, ws=None):
+        """Forward transform f -> flm (s2gb_forward)."""
+        return self._run("forward", f, out, ws)
+
+    def inverse(self, flm, out=None, ws=None):
+        """Inverse transform flm -> f (s2gb_inverse)."""
+        return self._run("inverse", flm, out, ws)
+
+    def adjoint_forward(self, flm_bar, out=None, ws=None):
+        return self._run("adjoint_forward", flm_bar, out, ws)
+
+    def adjoint_inverse(self, f_bar, out=None, ws=None):
+        return self._run("adjoint_inverse", f_bar, out, ws)
+
+    def inverse_theta(self, flm, out=None):
+        """Theta stage of the inverse alone (s2gb_inverse_theta): ftilde[b][t][m mod T]."""
+        batch = self._check(flm, "flm")
+        out = torch.empty(self.shape(batch), dtype=self.dtype, device=self.device) if out is None else out
+        nat.inverse_theta(self._h, flm, out, batch, self._stream())
+        return out
+
+    def forward_theta(self, g, out=None):
+        """Theta stage of the forward alone (s2gb_forward_theta): g[b][m+L-1][t] -> flm."""
+        if g.dim() != 3 or tuple(g.shape[1:]) != (2 * self.L - 1, self.L):
+            raise ValueError("g must have shape (batch, 2L-1, L)")
+        if g.dtype != self.dtype or g.device != self.device or not g.is_contiguous():
+            raise ValueError("g must be a contiguous tensor of the plan's dtype and device")
+        batch = g.shape[0]
+        out = torch.empty(self.shape(batch), dtype=self.dtype, device=self.device) if out is None else out
+        nat.forward_theta(self._h, g, out, batch, self._stream())
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            nat.plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class _Forward(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, f, plan):
+        ctx.plan = plan
+        return plan.forward(f.contiguous())
+
+    @staticmethod
+    def backward(ctx, g):
+        return ctx.plan.adjoint_forward(g.contiguous()), None
+
+
+class _Inverse(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, flm, plan):
+        ctx.plan = plan
+        return plan.inverse(flm.contiguous())
+
+    @staticmethod
+    def backward(ctx, g):
+        return ctx.plan.adjoint_inverse(g.contiguous()), None
+
+
+def forward(f: torch.Tensor, plan: Plan) -> torch.Tensor:
+    """Differentiable forward transform; its backward is the adjoint forward transform."""
+    return _Forward.apply(f, plan)
+
+
+def inverse(flm: torch.Tensor, plan: Plan) -> torch.Tensor:
+    """Differentiable inverse transform; its backward is the adjoint inverse transform."""
+    return _Inverse.apply(flm, plan)

@@ -1,0 +1,57 @@
+"""The C ABI library builds, loads and exports every entry point that include/s2gb.h declares.
+No compute call is made (these tests run without a GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "s2gb.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(s2gb_[a-z_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_2311_14670_gb300 import build
+    return build.build()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for n in ["s2gb_plan_create", "s2gb_plan_destroy", "s2gb_workspace_bytes", "s2gb_forward",
+              "s2gb_inverse", "s2gb_adjoint_forward", "s2gb_adjoint_inverse", "s2gb_strerror"]:
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    lib = ctypes.CDLL(libpath)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_strerror_and_argument_rejection_without_gpu(libpath):
+    from paper_2311_14670_gb300 import _native as nat
+    assert nat.strerror(0) == "success"
+    assert nat.strerror(-6).startswith("workspace")
+    assert nat.strerror(12345) == "unknown error code"
+    h = ctypes.c_void_p(1)
+    lib = nat.lib()
+    # invalid sizes are rejected before any device is touched, and *out is cleared
+    for args in [(0, 0, 0), (8, 8, 0), (8, -8, 0), (8, 0, -1), (8, 0, 9)]:
+        L, spin, N = args
+        assert lib.s2gb_plan_create(ctypes.byref(h), L, spin, N, 0, 0, 1, 0) == nat.S2GB_EINVAL
+        assert h.value is None
+    assert lib.s2gb_plan_create(ctypes.byref(h), 8, 0, 0, 7, 0, 1, 0) == nat.S2GB_EINVAL   # sampling
+    assert lib.s2gb_plan_create(ctypes.byref(h), 8, 0, 0, 0, 9, 1, 0) == nat.S2GB_EINVAL   # precision
+    assert lib.s2gb_plan_create(ctypes.byref(h), 8, 0, 0, 0, 0, 0, 0) == nat.S2GB_EINVAL   # max_batch
+    assert lib.s2gb_plan_create(None, 8, 0, 0, 0, 0, 1, 0) == nat.S2GB_EINVAL
+    # null plans
+    assert lib.s2gb_workspace_bytes(None, 1) == 0
+    assert lib.s2gb_forward(None, None, None, 1, None, 0, None) == nat.S2GB_EINVAL
+    lib.s2gb_plan_destroy(None)

@@ -1,0 +1,376 @@
+#!/usr/bin/env python3
+"""Benchmark of the MW spin-s spherical-harmonic transform on GB300 (one JSON line on stdout).
+
+A step is one pass of the whole transform path over one batch: the inverse transform of B signals
+(theta-stage kernel + phi inverse DFT) followed by the forward transform of the result (phi DFT,
+theta torus extension and quadrature FFTs, theta-stage kernel).  Default workload: L = 1024,
+spin 2, batch 4, float64, coefficients complex Gaussian / (l+1) -- 2B = 8 transforms per step.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
+
+Multi-GPU runs (torchrun, one rank per GPU) shard independent batches over the ranks with no
+collective on the data path (weak scaling); the barrier and the max-over-ranks timing use NCCL.
+``--impl reference`` times the CPU oracle (plain numpy, test infrastructure) on bounded samples of
+the same workload, on rank 0 only.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+# The CPU oracle legs run single-threaded so that the reported core count is exact.
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOADS = {
+    # name: (L, spin, N, batch, ell_power, description)
+    "l1024s2b4": (1024, 2, 0, 4, 1.0, "spin-2 SHT round trip, L=1024, MW 1024x2047, batch 4, FP64"),
+    "l2048s0b1": (2048, 0, 0, 1, 0.0, "spin-0 SHT round trip, L=2048, MW 2048x4095, batch 1, FP64"),
+    "l2048s0b4": (2048, 0, 0, 4, 0.0, "spin-0 SHT round trip, L=2048, MW 2048x4095, batch 4, FP64"),
+    "l64s0b1": (64, 0, 0, 1, 0.0, "spin-0 SHT round trip, L=64, MW 64x127, batch 1, FP64"),
+    "wigner256n8": (256, 0, 8, 1, 0.0, "Wigner round trip, L=256, N=8, MW 256x511x15, batch 1, FP64"),
+}
+METRIC = "transforms/sec"
+FP64_LANES_PER_SM_CLK = 2      # DFMA lanes per SM per clock on GB300 (measured 1.88-1.89 at load)
+NUM_SMS = 152
+
+
+def algorithmic_flops(L: int, n_list, R: int, batch: int) -> float:
+    """Per launch of one theta kernel: elements (l, m, theta) x (5 + 4B) flops (FMA = 2)."""
+    elems = sum(L * L - n * n for n in n_list) * R
+    return float(elems) * (5 + 4 * batch)
+
+
+class ClockSampler:
+    """nvidia-smi samples of the SM clock and throttle reasons while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.thread.join(timeout=2)
+
+    def summary(self):
+        if not self.lines:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 6:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[2:6]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_ours(args, world, rank, local):
+    import torch
+
+    from paper_2311_14670_gb300 import Plan, synth
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    L, spin, N, B, ellp, desc = WORKLOADS[args.workload]
+    plan = Plan(L, spin=spin, N=N, max_batch=B, device=local)
+    if N:
+        coef = synth.flmn_gaussian(L, N, B, seed=1000 * 3 + rank)
+        n_list = list(range(-(N - 1), N))
+    else:
+        coef = synth.flm_gaussian(L, spin, B, seed=1000 * 2 + rank, ell_power=ellp)
+        n_list = [-spin]
+    x = torch.from_numpy(coef).to(dev)
+    f = torch.empty(plan.shape(B), dtype=torch.complex128, device=dev)
+    y = torch.empty_like(x)
+    ws = plan.workspace(B)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        plan.inverse(x, out=f, ws=ws)
+        plan.forward(f, out=y, ws=ws)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clocks:
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        barrier()
+    ms = e0.elapsed_time(e1)
+    err = float((y - x).abs().max() / x.abs().max())
+
+    # end to end through the public API: pinned host input -> device -> round trip -> host result
+    hx = x.cpu().pin_memory()
+    hy = torch.empty_like(hx).pin_memory()
+    for _ in range(max(1, args.warmup // 2)):
+        xd = hx.to(dev, non_blocking=True)
+        plan.inverse(xd, out=f, ws=ws)
+        plan.forward(f, out=y, ws=ws)
+        hy.copy_(y, non_blocking=True)
+    barrier()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(args.steps):
+        xd = hx.to(dev, non_blocking=True)
+        plan.inverse(xd, out=f, ws=ws)
+        plan.forward(f, out=y, ws=ws)
+        hy.copy_(y, non_blocking=True)
+    t1.record(stream)
+    barrier()
+    ms_e2e = t0.elapsed_time(t1)
+
+    # the theta-stage kernels alone, on the launch stream, same workload
+    kern = {}
+    if not N:
+        g = torch.from_numpy(synth.signal_gaussian((B, 2 * L - 1, L), seed=77)).to(dev)
+        ft = torch.empty(plan.shape(B), dtype=torch.complex128, device=dev)
+        fl = torch.empty(plan.shape(B), dtype=torch.complex128, device=dev)
+        for name, fn in (("theta_inverse", lambda: plan.inverse_theta(x, out=ft)),
+                         ("theta_forward", lambda: plan.forward_theta(g, out=fl))):
+            fn()
+            torch.cuda.synchronize(dev)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = max(2, args.steps)
+            a.record(stream)
+            for _ in range(reps):
+                fn()
+            b.record(stream)
+            torch.cuda.synchronize(dev)
+            kms = a.elapsed_time(b) / reps
+            flops = algorithmic_flops(L, n_list, L, B)
+            kern[name] = {"ms": kms, "flops": flops, "tflops": flops / (kms * 1e-3) / 1e12}
+
+    # max over ranks
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms, ms_e2e], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, ms_e2e = float(t[0]), float(t[1])
+    transforms_per_step = 2 * B * world * (2 * N - 1 if N else 1)
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return None
+    ck = clocks.summary()
+    sm_max = ck["sm_max_mhz"] or 2070.0
+    peak = NUM_SMS * FP64_LANES_PER_SM_CLK * 2 * sm_max * 1e6 / 1e12    # TFLOP/s
+    roof = None
+    if kern:
+        dom = max(kern, key=lambda k: kern[k]["ms"])
+        ach = kern[dom]["tflops"]
+        roof = {"bound": "alu", "kernel": dom, "achieved": round(ach, 4), "peak": round(peak, 4),
+                "unit": "TFLOP/s", "frac": round(ach / peak, 4), "traffic": None,
+                "peak_basis": f"FP64 FMA pipe: {NUM_SMS} SMs x {FP64_LANES_PER_SM_CLK} lanes x 2 flop x {sm_max:.0f} MHz"}
+    value = transforms_per_step * args.steps / (ms * 1e-3)
+    in_bytes = x.numel() * x.element_size()
+    out = {
+        "metric": METRIC, "value": round(value, 3), "unit": "transforms/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded complex Gaussian coefficients)",
+        "config": {"workload": args.workload, "description": desc, "L": L, "spin": spin, "N": N,
+                   "batch_per_gpu": B, "transforms_per_step": transforms_per_step,
+                   "step": "inverse + forward of every signal in the batch",
+                   "l2": "working set > L2 (coefficients %.0f MB, workspace %.0f MB per step)"
+                         % (in_bytes / 1e6, ws.numel() / 1e6),
+                   "parallelism": f"dp{world} (independent batches, no data-path collective)"},
+        "roundtrip_rel_max_err": err,
+        "e2e": {"value": round(transforms_per_step * args.steps / (ms_e2e * 1e-3), 3), "unit": "transforms/s",
+                "h2d_bytes_per_step": in_bytes, "d2h_bytes_per_step": in_bytes},
+        "gpu_launches": args.steps * (8 if N else 6),
+        "kernels": kern,
+        "roofline": roof,
+        "clocks": {k: ck[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
+    }
+    if not args.no_cpu_baseline and world == 1:
+        out["cpu_baseline"] = cpu_baseline(args.workload, rings=args.cpu_rings)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return out
+
+
+def cpu_baseline(workload: str, rings: int = 8) -> dict:
+    """The oracle (plain numpy, single thread) on a bounded sample of the workload, scaled to
+    transforms/s.  The oracle's stages are timed on `rings`-sized slices and scaled by the size
+    they are linear in: the inverse (d-table + synthesis) per ring; the forward's phi-DFT, torus
+    extension and upsampling per order m; its quadrature against the d-table per degree l.  A
+    Wigner transform is 2N-1 such stages (timed for one n) plus the gamma DFT."""
+    from oracle import transforms as OT
+    from paper_2311_14670_gb300 import synth
+
+    L, spin, N, B, ellp, _ = WORKLOADS[workload]
+    T = 2 * L - 1
+    n = 0 if N else -spin
+    nn = 2 * N - 1 if N else 1
+    coef = synth.flm_gaussian(L, -n, B, seed=1, ell_power=ellp)
+    f = synth.signal_gaussian((B, L, T), seed=2)
+    k = max(4, min(L, rings))
+    k2 = k // 2
+
+    def fit(fn, full):
+        """Time fn(k/2) and fn(k); extrapolate t(x) = a + b x (per-call overhead + per-unit cost)."""
+        t0 = time.perf_counter()
+        fn(k2)
+        ta = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        fn(k)
+        tb = time.perf_counter() - t0
+        b = max(0.0, (tb - ta) / (k - k2))
+        a = max(0.0, tb - b * k)
+        return a + b * full
+
+    scale = OT.ell_factor(L, -n)
+    thetas = OT.mw_thetas(L)
+    t_start = time.perf_counter()
+
+    def inv(j):                                                # inverse: per ring
+        sel = np.linspace(0, L - 1, j).astype(int)
+        OT._theta_inverse(coef, L, n, scale, thetas[sel]) @ OT.phi_dft_matrix(L, +1).T
+
+    cmat, up = OT._upsample_matrices(L)
+
+    def fft(j):                                                # forward DFT/upsampling: per order
+        sel = np.linspace(-(L - 1), L - 1, j).astype(int)
+        up @ (cmat @ OT._extend(OT._phi_forward(f, L, sel), L, n, sel))
+
+    Gu = synth.signal_gaussian((B, 2 * L, T), seed=3)           # stand-in of the same shape
+
+    def quad(j):                                               # forward quadrature: per degree
+        OT._theta_forward_upsampled(Gu, L, n, scale, np.linspace(abs(n), L - 1, j).astype(int))
+
+    t_inv = fit(inv, L)
+    t_fft = fit(fft, T)
+    t_quad = fit(quad, L)
+    t_gam = 0.0
+    if N:
+        fw = synth.signal_gaussian((B, nn, L, T), seed=4)
+        t0 = time.perf_counter()
+        np.einsum("kn,...ktp->...ntp", OT._gamma_matrix(N, -1), fw)
+        t_gam = 2 * (time.perf_counter() - t0)
+    total = nn * (t_inv + t_fft + t_quad) + t_gam
+    per = 2 * B * nn
+    return {"value": round(per / total, 6), "unit": "transforms/s", "cores": 1, "kind": "oracle",
+            "sample": f"{workload}: oracle stages timed on {k2} and {k} of {L} rings / {T} orders / {L} "
+                      f"degrees (all {B} signals{', one of %d n' % nn if N else ''}), single thread, "
+                      f"extrapolated as overhead + linear cost to the full round trip",
+            "seconds_measured": round(time.perf_counter() - t_start, 2),
+            "seconds_full_round_trip_est": round(total, 1)}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return None
+    L, spin, N, B, ellp, desc = WORKLOADS[args.workload]
+    k = 4
+    samples = []
+    for _ in range(args.warmup):
+        cpu_baseline(args.workload, rings=k)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        samples.append(cpu_baseline(args.workload, rings=k)["value"])
+    wall = time.perf_counter() - t0
+    value = statistics.median(samples)
+    per = 2 * B * (2 * N - 1 if N else 1)
+    cb = {"value": value, "unit": "transforms/s", "cores": 1, "kind": "oracle",
+          "sample": f"each step: oracle inverse on {k} of {L} rings + forward on {k} of {L} degrees, "
+                    f"scaled linearly to full transforms (single thread)"}
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": "transforms/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(per / value * 1e3, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded complex Gaussian coefficients)",
+            "config": {"workload": args.workload, "description": desc, "L": L, "spin": spin, "N": N,
+                       "batch_per_gpu": B, "transforms_per_step": per,
+                       "parallelism": "host cores, one process"},
+            "cpu_baseline": cb, "wall_s": round(wall, 2),
+            "e2e": {"value": value, "unit": "transforms/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default="l1024s2b4", choices=sorted(WORKLOADS))
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-rings", type=int, default=8, help="rings/degrees of the oracle sample")
+    args = ap.parse_args()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        out = run_reference(args, world, rank)
+    else:
+        out = run_ours(args, world, rank, local)
+    if out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -95,35 +95,42 @@ def _upsample_matrices(L: int):
     return coef, up
 
 
-def _phi_forward(f: np.ndarray, L: int) -> np.ndarray:
-    """F[..., t, m] = sum_p f[..., t, p] e^{-i m phi_p} (Eq. disc_sh_fft without q_Phi)."""
-    return np.asarray(f, dtype=np.complex128) @ phi_dft_matrix(L, -1)
+def _phi_forward(f: np.ndarray, L: int, orders=None) -> np.ndarray:
+    """F[..., t, m] = sum_p f[..., t, p] e^{-i m phi_p} (Eq. disc_sh_fft without q_Phi).
+
+    ``orders``: optional subset of the orders m (default: all |m| < L, in increasing order)."""
+    E = phi_dft_matrix(L, -1)
+    if orders is not None:
+        E = E[:, np.asarray(orders) + L - 1]
+    return np.asarray(f, dtype=np.complex128) @ E
 
 
-def _extend(F: np.ndarray, L: int, n: int) -> np.ndarray:
+def _extend(F: np.ndarray, L: int, n: int, orders=None) -> np.ndarray:
     """Torus extension in theta, G[..., t', m] for t' < 2L-1 (Sec. 4.2.2); n is the d-index (-s).
 
     Reading: the ring theta = pi is its own reflection, so the extension there is the average of
     the ring and its reflection, G_m(pi) = (1 + (-1)^{m+s})/2 F_m(pi).  Bandlimited signals already
     have F_m(pi) = 0 for odd m+s; for arbitrary samples this makes the torus function exactly of
     parity (-1)^{m+s}, so that every exact theta quadrature gives the same result."""
-    m = np.arange(-(L - 1), L)
+    m = np.arange(-(L - 1), L) if orders is None else np.asarray(orders)
     sigma = (-1.0) ** ((m - n) % 2)                                         # (-1)^{m+s}
-    G = np.zeros(F.shape[:-2] + (2 * L - 1, 2 * L - 1), dtype=np.complex128)
+    G = np.zeros(F.shape[:-2] + (2 * L - 1, F.shape[-1]), dtype=np.complex128)
     G[..., :L, :] = F
     G[..., L - 1, :] = F[..., L - 1, :] * (1 + sigma) / 2
     G[..., L:, :] = (F[..., :L - 1, :] * sigma)[..., ::-1, :]               # G[2L-2-t] = sigma F[t]
     return G
 
 
-def _theta_forward_upsampled(Gu: np.ndarray, L: int, n: int, scale: np.ndarray, ells) -> np.ndarray:
+def _theta_forward_upsampled(Gu: np.ndarray, L: int, n: int, scale: np.ndarray, ells,
+                             orders=None) -> np.ndarray:
     """flm[..., i, m] = scale_l sum_u q_u d^l_{m,n}(theta'_u) q_Phi Gu[..., u, m], l = ells[i]."""
     ells = np.asarray(ells)
+    mcols = np.arange(2 * L - 1) if orders is None else np.asarray(orders) + L - 1
     q = mw_theta_weights(2 * L)
     qphi = 2 * np.pi / (2 * L - 1)
     thu = mw_thetas(2 * L)
     W = Gu * (q * qphi)[:, None]
-    out = np.zeros(Gu.shape[:-2] + (len(ells), 2 * L - 1), dtype=np.complex128)
+    out = np.zeros(Gu.shape[:-2] + (len(ells), len(mcols)), dtype=np.complex128)
     per_l = (2 * L - 1) * 2 * L * 8 * 2
     step = max(1, _CHUNK_BYTES // per_l)
     for a in range(0, len(ells), step):
@@ -131,19 +138,20 @@ def _theta_forward_upsampled(Gu: np.ndarray, L: int, n: int, scale: np.ndarray, 
         D = wigner_d_table(sel, n, thu)                                      # [i, m', u], m' width max(sel)
         M = int(sel.max())
         D = D[:, M - (L - 1):M + L, :] if M >= L - 1 else np.pad(D, ((0, 0), (L - 1 - M, L - 1 - M), (0, 0)))
-        out[..., a:a + step, :] = np.einsum("...um,imu->...im", W, D) * scale[sel][:, None]
-    mask = coeff_mask(L, n)[ells]
+        out[..., a:a + step, :] = np.einsum("...um,imu->...im", W, D[:, mcols, :]) * scale[sel][:, None]
+    mask = coeff_mask(L, n)[ells][:, mcols]
     return np.where(mask, out, 0)
 
 
-def forward(f: np.ndarray, L: int, spin: int, ells=None) -> np.ndarray:
-    """Forward spin-s SHT on the MW grid; ``ells`` selects output rows (default: all l < L)."""
+def forward(f: np.ndarray, L: int, spin: int, ells=None, orders=None) -> np.ndarray:
+    """Forward spin-s SHT on the MW grid; ``ells`` selects output rows (default: all l < L) and
+    ``orders`` output columns by order m (default: all |m| < L)."""
     if ells is None:
         ells = np.arange(L)
     coef, up = _upsample_matrices(L)
-    G = _extend(_phi_forward(f, L), L, -spin)
+    G = _extend(_phi_forward(f, L, orders), L, -spin, orders)
     Gu = up @ (coef @ G)
-    return _theta_forward_upsampled(Gu, L, -spin, ell_factor(L, spin), ells)
+    return _theta_forward_upsampled(Gu, L, -spin, ell_factor(L, spin), ells, orders)
 
 
 # ----------------------------------------------------------------------------- adjoints (Sec. 5.2)

@@ -130,6 +130,29 @@ int s2gb_adjoint_inverse(s2gb_plan plan, const void* f_bar, void* flm_bar, int b
 int s2gb_inverse_theta(s2gb_plan plan, const void* flm, void* ftilde, int batch, void* stream);
 int s2gb_forward_theta(s2gb_plan plan, const void* g, void* flm, int batch, void* stream);
 
+/*
+ * Allocation-free inverse transform.  The paper has no counterpart: this entry point exists for
+ * callers that cannot allocate device memory at the point where they run the transform -- code
+ * whose memory is owned by another allocator, code running under a strict no-allocation rule
+ * (real-time or certified pipelines), or plugins that are handed only their input and output.
+ * It computes exactly what s2gb_inverse computes (same arguments, layouts and results) but takes
+ * no workspace: its scratch is a static device array of S2GB_NOALLOC_SCRATCH_BYTES inside
+ * libs2gb.so, which every GPU that loads the library holds until the process exits.  It calls no
+ * cudaMalloc / cudaFree and no allocating library routine (the plan must already exist).
+ *   - Returns S2GB_EWORKSPACE when the call needs more scratch than the array holds: the
+ *     theta-stage output (batch * L * (2L-1) elements; three such buffers for Wigner plans) plus
+ *     the cuFFT work area of the phi (and gamma) DFT.  With complex128 data, 64 MiB covers for
+ *     example L = 1024 with batch 1 or L = 512 with batch 4.
+ *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
+ *     that device current; make that first call before any CUDA stream capture.
+ *   - Every call shares the one array and it keeps the previous call's contents (this transform
+ *     overwrites everything it reads back, so nothing needs clearing).  Calls that may overlap on
+ *     the GPU (different streams, different host threads without ordering) race on it: serialise
+ *     them.
+ */
+#define S2GB_NOALLOC_SCRATCH_BYTES (64u << 20)
+int s2gb_inverse_noalloc(s2gb_plan plan, const void* flm, void* f, int batch, void* stream);
+
 /* Static description of a return code (never NULL). */
 const char* s2gb_strerror(int code);
 

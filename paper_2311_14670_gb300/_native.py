@@ -55,6 +55,8 @@ def lib() -> ctypes.CDLL:
             fn = getattr(L, name)
             fn.argtypes = [vp, vp, vp, i, vp, sz, vp]
             fn.restype = i
+        L.s2gb_inverse_noalloc.argtypes = [vp, vp, vp, i, vp]
+        L.s2gb_inverse_noalloc.restype = i
         for name in ("s2gb_inverse_theta", "s2gb_forward_theta"):
             fn = getattr(L, name)
             fn.argtypes = [vp, vp, vp, i, vp]
@@ -130,3 +132,10 @@ def forward_theta(plan, g, flm, batch, stream):
     _check(lib().s2gb_forward_theta(ctypes.c_void_p(plan), ctypes.c_void_p(_ptr(g)),
                                     ctypes.c_void_p(_ptr(flm)), batch, ctypes.c_void_p(stream)),
            "s2gb_forward_theta")
+
+
+def inverse_noalloc(plan, flm, f, batch, stream):
+    """s2gb_inverse_noalloc: the inverse transform with the library's static scratch (no workspace)."""
+    _check(lib().s2gb_inverse_noalloc(ctypes.c_void_p(plan), ctypes.c_void_p(_ptr(flm)),
+                                      ctypes.c_void_p(_ptr(f)), batch, ctypes.c_void_p(stream)),
+           "s2gb_inverse_noalloc")

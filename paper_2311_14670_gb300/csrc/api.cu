@@ -371,3 +371,65 @@ const char* s2gb_strerror(int code) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------------------
+// Allocation-free inverse transform (s2gb_inverse_noalloc).
+//
+// Its scratch is this file-scope device array instead of a caller-provided workspace.  Every
+// device that loads the library holds the array until the process exits.  Host code cannot pass
+// the symbol itself to a kernel (on the host it names a stand-in, not device memory), so the
+// device address is looked up with cudaGetSymbolAddress, once per device, with that device
+// current, the first time the entry point runs there.
+// ---------------------------------------------------------------------------------------------
+static __device__ __align__(256) unsigned char s2gb_noalloc_scratch[S2GB_NOALLOC_SCRATCH_BYTES];
+
+namespace s2gb {
+namespace {
+
+std::mutex g_noalloc_mutex;
+constexpr int kMaxDevices = 64;
+void* g_noalloc_ptr[kMaxDevices] = {};
+
+int noalloc_scratch(int device, void** out) {
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (device < 0 || device >= kMaxDevices) return S2GB_EINVAL;
+  if (!g_noalloc_ptr[device]) {
+    void* ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, s2gb_noalloc_scratch) != cudaSuccess || !ptr) return S2GB_ECUDA;
+    g_noalloc_ptr[device] = ptr;
+  }
+  *out = g_noalloc_ptr[device];
+  return S2GB_OK;
+}
+
+}  // namespace
+}  // namespace s2gb
+
+extern "C" int s2gb_inverse_noalloc(s2gb_plan plan, const void* flm, void* f, int batch, void* stream) {
+  if (!plan || !flm || !f) return S2GB_EINVAL;
+  s2gb::Plan& p = plan->p;
+  if (batch < 1 || batch > p.max_batch) return S2GB_EINVAL;
+  const size_t es = p.precision == S2GB_FP64 ? 16 : 8;
+  const size_t sig_bytes = (size_t)batch * p.nN * p.L * p.T * es;
+  if (s2gb::overlaps(flm, f, sig_bytes)) return S2GB_EINVAL;
+  // scratch: the theta-stage output (and, for Wigner, two more signal-sized buffers) + cuFFT work
+  const int q = (batch == p.max_batch) ? 1 : 0;
+  size_t work = 0, w2 = 0;
+  if (cufftGetSize(p.fft_phi[q], &work) != CUFFT_SUCCESS) return S2GB_ECUFFT;
+  if (p.wigner) {
+    if (cufftGetSize(p.fft_gam[0], &w2) != CUFFT_SUCCESS) return S2GB_ECUFFT;
+    if (w2 > work) work = w2;
+  }
+  const size_t buf = s2gb::align256(sig_bytes);
+  const int nbuf = p.wigner ? 3 : 1;
+  const size_t need = nbuf * buf + s2gb::align256(work);
+  if (need > (size_t)S2GB_NOALLOC_SCRATCH_BYTES) return S2GB_EWORKSPACE;
+  s2gb::DeviceGuard g(p.device);
+  void* base = nullptr;
+  int rc = s2gb::noalloc_scratch(p.device, &base);
+  if (rc != S2GB_OK) return rc;
+  char* b = reinterpret_cast<char*>(base);
+  s2gb::Workspace w = {b, b + (nbuf > 1 ? buf : 0), b + (nbuf > 2 ? 2 * buf : 0), b + nbuf * buf};
+  std::lock_guard<std::mutex> lock(p.fft_mutex);
+  return s2gb::do_inverse(p, flm, f, batch, w, reinterpret_cast<cudaStream_t>(stream));
+}

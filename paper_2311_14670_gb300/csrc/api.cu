@@ -105,7 +105,7 @@ InvArgs inv_args(const Plan& p, const void* flm, void* out, int batch, const dou
   InvArgs a;
   a.flm = flm; a.out = out; a.s_sig = s_sig; a.s_t = s_t; a.s_m = s_m; a.m_mod = m_mod;
   a.nsig = batch; a.nN = p.nN; a.L = p.L; a.coef = p.coef; a.ring = p.ring; a.seed = p.seed;
-  a.scale = scale;
+  a.scale = scale; a.coef32 = p.coef32; a.v32 = p.v32;
   return a;
 }
 
@@ -114,7 +114,7 @@ FwdArgs fwd_args(const Plan& p, const void* g, void* flm, int batch, const doubl
   FwdArgs a;
   a.g = g; a.flm = flm; a.s_sig = s_sig; a.s_t = s_t; a.s_m = s_m; a.m_mod = m_mod; a.use_nu = use_nu;
   a.nsig = batch; a.nN = p.nN; a.L = p.L; a.coef = p.coef; a.ring = p.ring; a.seed = p.seed;
-  a.scale = scale; a.nu = p.nu;
+  a.scale = scale; a.nu = p.nu; a.coef32 = p.coef32; a.v32 = p.v32;
   return a;
 }
 
@@ -279,7 +279,6 @@ int s2gb_plan_create(s2gb_plan* out, int L, int spin, int N, int sampling, int p
   if (L < 1 || L > 4096 || N < 0 || N > L || max_batch < 1 || sampling != S2GB_MW) return S2GB_EINVAL;
   if (precision != S2GB_FP64 && precision != S2GB_FP32) return S2GB_EINVAL;
   if (N == 0 && (spin <= -L || spin >= L)) return S2GB_EINVAL;
-  if (precision == S2GB_FP32) return S2GB_EUNSUPPORTED;
   if (L > 2048) return S2GB_EUNSUPPORTED;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return S2GB_EINVAL;

@@ -86,6 +86,11 @@ __global__ void coef_kernel(double* coef, const int* n_of, int nN, int L) {
   }
 }
 
+__global__ void to_float_kernel(const double* __restrict__ in, float* __restrict__ out, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    out[i] = (float)in[i];
+}
+
 int good_fft_size(int n) {
   // smallest m >= n whose prime factors are in {2, 3, 5, 7}
   for (int m = n > 1 ? n : 1;; ++m) {
@@ -233,6 +238,22 @@ int make_plan(Plan* p) {
   coef_kernel<<<1024, 256>>>(p->coef, p->n_of, nN, L);
   if (cudaGetLastError() != cudaSuccess) return S2GB_ECUDA;
   if (cudaDeviceSynchronize() != cudaSuccess) return S2GB_ECUDA;
+  if (p->precision == S2GB_FP32) {
+    // float32 plans keep the coefficient table rounded once to float, and v per ring
+    const size_t n = (size_t)nN * T * L * kCoefPerStep;
+    if (cudaMalloc((void**)&p->coef32, n * sizeof(float)) != cudaSuccess) return S2GB_ENOMEM;
+    to_float_kernel<<<1024, 256>>>(p->coef, p->coef32, n);
+    if (cudaGetLastError() != cudaSuccess) return S2GB_ECUDA;
+    if (cudaDeviceSynchronize() != cudaSuccess) return S2GB_ECUDA;
+    cudaFree(p->coef);
+    p->coef = nullptr;
+    bytes += n * sizeof(float);
+    bytes -= coef_bytes;
+    std::vector<float> v32(L);
+    for (int t = 0; t < L; ++t) v32[t] = (float)ring[t].v;
+    if ((rc = upload(&p->v32, v32, &bytes))) return rc;
+    p->device_bytes = bytes;
+  }
 
   // ---- cuFFT plans ----
   const cufftType ty = p->precision == S2GB_FP64 ? CUFFT_Z2Z : CUFFT_C2C;
@@ -259,6 +280,8 @@ int make_plan(Plan* p) {
 
 void free_plan(Plan* p) {
   cudaFree(p->coef);
+  cudaFree(p->coef32);
+  cudaFree(p->v32);
   cudaFree(p->ring);
   cudaFree(p->seed);
   cudaFree(p->scale_inv);

@@ -53,7 +53,9 @@ struct Plan {
   bool wigner = false;
 
   // device tables
-  double* coef = nullptr;      // [nN][T][L][kCoefPerStep]  (m index = m + L - 1, step j)
+  double* coef = nullptr;      // [nN][T][L][kCoefPerStep]  (m index = m + L - 1, step j); FP64 plans
+  float* coef32 = nullptr;     // the same table rounded to float (FP32 plans)
+  float* v32 = nullptr;        // [L] ring variable v rounded to float (FP32 plans)
   RingData* ring = nullptr;    // [L]
   SeedData* seed = nullptr;    // [nN][T]
   double* scale_inv = nullptr; // [nN][L] per-degree factor of the inverse theta stage
@@ -89,6 +91,8 @@ struct InvArgs {
   const RingData* ring;
   const SeedData* seed;
   const double* scale;  // [nN][L]
+  const float* coef32;  // FP32 plans
+  const float* v32;
 };
 
 struct FwdArgs {
@@ -105,10 +109,14 @@ struct FwdArgs {
   const SeedData* seed;
   const double* scale;
   const double* nu;
+  const float* coef32;  // FP32 plans
+  const float* v32;
 };
 
 cudaError_t launch_theta_inverse(const Plan& p, const InvArgs& a, cudaStream_t st);
 cudaError_t launch_theta_forward(const Plan& p, const FwdArgs& a, cudaStream_t st);
+cudaError_t launch_theta_inverse_f32(const Plan& p, const InvArgs& a, cudaStream_t st);
+cudaError_t launch_theta_forward_f32(const Plan& p, const FwdArgs& a, cudaStream_t st);
 
 // ---- glue kernels (glue.cu) ----
 cudaError_t launch_extend(const Plan& p, const void* F, void* G, int nsig, cudaStream_t st);

@@ -97,18 +97,26 @@ __device__ __forceinline__ void inverse_body(const InvArgs& a, int m, int ni, in
     __syncthreads();
     const int jend = min(kChunk, L - jc);
     for (int j8 = 0; j8 < jend; j8 += 8) {
+      // chains that are dead in every lane of the warp skip their contraction (warp-uniform)
+      unsigned live = 0;
+#pragma unroll
+      for (int i = 0; i < KT; ++i) live |= (__any_sync(0xffffffffu, E[i] == 0) ? 1u : 0u) << i;
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
         const int jj = j8 + u;
         if (jj < jend) {
+          double2 h[NB];
+#pragma unroll
+          for (int b = 0; b < NB; ++b) h[b] = hs[jj * NB + b];
 #pragma unroll
           for (int i = 0; i < KT; ++i) {
-            const double xl = (E[i] == 0) ? x[i] : 0.0;
+            if ((live >> i) & 1u) {
+              const double xl = (E[i] == 0) ? x[i] : 0.0;
 #pragma unroll
-            for (int b = 0; b < NB; ++b) {
-              const double2 h = hs[jj * NB + b];
-              acc[i][b].x = fma(xl, h.x, acc[i][b].x);
-              acc[i][b].y = fma(xl, h.y, acc[i][b].y);
+              for (int b = 0; b < NB; ++b) {
+                acc[i][b].x = fma(xl, h[b].x, acc[i][b].x);
+                acc[i][b].y = fma(xl, h[b].y, acc[i][b].y);
+              }
             }
           }
           if (jc + jj < L - 1) {
@@ -258,19 +266,25 @@ __global__ void __launch_bounds__(128) theta_forward_kernel(FwdArgs a) {
     double p[32];
 #pragma unroll
     for (int s = 0; s < 32; ++s) p[s] = 0.0;
+    // chains that are dead in every lane of the warp skip their contraction (warp-uniform)
+    unsigned live = 0;
+#pragma unroll
+    for (int i = 0; i < KT; ++i) live |= (__any_sync(0xffffffffu, E[i] == 0) ? 1u : 0u) << i;
 #pragma unroll
     for (int jr = 0; jr < JR; ++jr) {
       const int j = j0 + jr;
       if (j < L) {
 #pragma unroll
         for (int i = 0; i < KT; ++i) {
-          const double xl = (E[i] == 0) ? x[i] : 0.0;
-          const int pos = i * nt + tid;
+          if ((live >> i) & 1u) {
+            const double xl = (E[i] == 0) ? x[i] : 0.0;
+            const int pos = i * nt + tid;
 #pragma unroll
-          for (int b = 0; b < NB; ++b) {
-            const double2 g = gs[b * rows + pos];
-            p[jr * 2 * NB + 2 * b] = fma(xl, g.x, p[jr * 2 * NB + 2 * b]);
-            p[jr * 2 * NB + 2 * b + 1] = fma(xl, g.y, p[jr * 2 * NB + 2 * b + 1]);
+            for (int b = 0; b < NB; ++b) {
+              const double2 g = gs[b * rows + pos];
+              p[jr * 2 * NB + 2 * b] = fma(xl, g.x, p[jr * 2 * NB + 2 * b]);
+              p[jr * 2 * NB + 2 * b + 1] = fma(xl, g.y, p[jr * 2 * NB + 2 * b + 1]);
+            }
           }
         }
         if (j < L - 1) {

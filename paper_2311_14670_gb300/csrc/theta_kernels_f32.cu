@@ -138,18 +138,25 @@ __device__ __forceinline__ void inverse_body_f32(const InvArgs& a, int m, int ni
     __syncthreads();
     const int jend = min(kChunk32, L - jc);
     for (int j8 = 0; j8 < jend; j8 += 8) {
+      unsigned live = 0;
+#pragma unroll
+      for (int i = 0; i < KT; ++i) live |= (__any_sync(0xffffffffu, E[i] == 0) ? 1u : 0u) << i;
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
         const int jj = j8 + u;
         if (jj < jend) {
+          float2 h[NB];
+#pragma unroll
+          for (int b = 0; b < NB; ++b) h[b] = hs[jj * NB + b];
 #pragma unroll
           for (int i = 0; i < KT; ++i) {
-            const float xl = (E[i] == 0) ? x[i] : 0.0f;
+            if ((live >> i) & 1u) {
+              const float xl = (E[i] == 0) ? x[i] : 0.0f;
 #pragma unroll
-            for (int b = 0; b < NB; ++b) {
-              const float2 h = hs[jj * NB + b];
-              blk[i][b].x = fmaf(xl, h.x, blk[i][b].x);
-              blk[i][b].y = fmaf(xl, h.y, blk[i][b].y);
+              for (int b = 0; b < NB; ++b) {
+                blk[i][b].x = fmaf(xl, h[b].x, blk[i][b].x);
+                blk[i][b].y = fmaf(xl, h[b].y, blk[i][b].y);
+              }
             }
           }
           if (jc + jj < L - 1) {
@@ -162,6 +169,9 @@ __device__ __forceinline__ void inverse_body_f32(const InvArgs& a, int m, int ni
         if (u & 1) {
 #pragma unroll
           for (int i = 0; i < KT; ++i) renorm_f32(x[i], y[i], E[i]);
+          live = 0;   // chains may have come alive: refresh the warp-uniform mask
+#pragma unroll
+          for (int i = 0; i < KT; ++i) live |= (__any_sync(0xffffffffu, E[i] == 0) ? 1u : 0u) << i;
         }
       }
       // fold the block of 8 degrees into the compensated (hi, lo) sums
@@ -307,19 +317,24 @@ __global__ void __launch_bounds__(128) theta_forward_kernel_f32(FwdArgs a) {
     float ph[32], pl[32];
 #pragma unroll
     for (int s = 0; s < 32; ++s) { ph[s] = 0.f; pl[s] = 0.f; }
+    unsigned live = 0;
+#pragma unroll
+    for (int i = 0; i < KT; ++i) live |= (__any_sync(0xffffffffu, E[i] == 0) ? 1u : 0u) << i;
 #pragma unroll
     for (int jr = 0; jr < JR; ++jr) {
       const int j = j0 + jr;
       if (j < L) {
 #pragma unroll
         for (int i = 0; i < KT; ++i) {
-          const float xl = (E[i] == 0) ? x[i] : 0.0f;
-          const int pos = i * nt + tid;
+          if ((live >> i) & 1u) {
+            const float xl = (E[i] == 0) ? x[i] : 0.0f;
+            const int pos = i * nt + tid;
 #pragma unroll
-          for (int b = 0; b < NB; ++b) {
-            const float2 g = gs[b * rows + pos];
-            ph[jr * 2 * NB + 2 * b] = fmaf(xl, g.x, ph[jr * 2 * NB + 2 * b]);
-            ph[jr * 2 * NB + 2 * b + 1] = fmaf(xl, g.y, ph[jr * 2 * NB + 2 * b + 1]);
+            for (int b = 0; b < NB; ++b) {
+              const float2 g = gs[b * rows + pos];
+              ph[jr * 2 * NB + 2 * b] = fmaf(xl, g.x, ph[jr * 2 * NB + 2 * b]);
+              ph[jr * 2 * NB + 2 * b + 1] = fmaf(xl, g.y, ph[jr * 2 * NB + 2 * b + 1]);
+            }
           }
         }
         if (j < L - 1) {
@@ -340,6 +355,9 @@ __global__ void __launch_bounds__(128) theta_forward_kernel_f32(FwdArgs a) {
       if ((jr & 1) || jr == JR - 1) {
 #pragma unroll
         for (int i = 0; i < KT; ++i) renorm_f32(x[i], y[i], E[i]);
+        live = 0;   // chains may have come alive: refresh the warp-uniform mask
+#pragma unroll
+        for (int i = 0; i < KT; ++i) live |= (__any_sync(0xffffffffu, E[i] == 0) ? 1u : 0u) << i;
       }
     }
     float oh, ol;

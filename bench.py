@@ -40,9 +40,14 @@ WORKLOADS = {
     "l2048s0b4": (2048, 0, 0, 4, 0.0, "spin-0 SHT round trip, L=2048, MW 2048x4095, batch 4, FP64"),
     "l64s0b1": (64, 0, 0, 1, 0.0, "spin-0 SHT round trip, L=64, MW 64x127, batch 1, FP64"),
     "wigner256n8": (256, 0, 8, 1, 0.0, "Wigner round trip, L=256, N=8, MW 256x511x15, batch 1, FP64"),
+    "l2048s0b16f32grad": (2048, 0, 0, 16, 1.0, "differentiable FP32 SHT, L=2048, spin 0, batch 16: "
+                          "loss = sum |inverse(flm) - target|^2 and its gradient via the adjoint"),
 }
+PRECISION = {"l2048s0b16f32grad": "fp32"}
+GRAD = {"l2048s0b16f32grad"}
 METRIC = "transforms/sec"
 FP64_LANES_PER_SM_CLK = 2      # DFMA lanes per SM per clock on GB300 (measured 1.88-1.89 at load)
+FP32_LANES_PER_SM_CLK = 128    # FFMA lanes per SM per clock (measured 118.5 at load)
 NUM_SMS = 152
 
 
@@ -129,22 +134,37 @@ def run_ours(args, world, rank, local):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
     L, spin, N, B, ellp, desc = WORKLOADS[args.workload]
-    plan = Plan(L, spin=spin, N=N, max_batch=B, device=local)
+    precision = PRECISION.get(args.workload, "fp64")
+    grad_mode = args.workload in GRAD
+    plan = Plan(L, spin=spin, N=N, max_batch=B, device=local, precision=precision)
+    cdt = plan.dtype
     if N:
         coef = synth.flmn_gaussian(L, N, B, seed=1000 * 3 + rank)
         n_list = list(range(-(N - 1), N))
     else:
-        coef = synth.flm_gaussian(L, spin, B, seed=1000 * 2 + rank, ell_power=ellp)
+        coef = synth.flm_gaussian(L, spin, B, seed=1000 * 2 + rank, ell_power=0.0 if grad_mode else ellp)
         n_list = [-spin]
-    x = torch.from_numpy(coef).to(dev)
-    f = torch.empty(plan.shape(B), dtype=torch.complex128, device=dev)
+    x = torch.from_numpy(coef).to(dev).to(cdt)
+    f = torch.empty(plan.shape(B), dtype=cdt, device=dev)
     y = torch.empty_like(x)
     ws = plan.workspace(B)
     stream = torch.cuda.current_stream(dev)
+    if grad_mode:
+        from paper_2311_14670_gb300 import inverse as inverse_ad
+        # Gaussian random-field target: a_lm ~ sqrt(C_l) (N(0,1) + i N(0,1)), C_l = (l+1)^-2
+        a = synth.flm_gaussian(L, spin, B, seed=4242 + rank, ell_power=ellp)
+        target = plan.inverse(torch.from_numpy(a).to(dev).to(cdt))
+        xg = x.clone().requires_grad_(True)
 
-    def step():
-        plan.inverse(x, out=f, ws=ws)
-        plan.forward(f, out=y, ws=ws)
+        def step():
+            xg.grad = None
+            loss = ((inverse_ad(xg, plan) - target).abs() ** 2).sum()
+            loss.backward()
+            y.copy_(xg.grad)
+    else:
+        def step():
+            plan.inverse(x, out=f, ws=ws)
+            plan.forward(f, out=y, ws=ws)
 
     def barrier():
         if world > 1:
@@ -163,24 +183,30 @@ def run_ours(args, world, rank, local):
         e1.record(stream)
         barrier()
     ms = e0.elapsed_time(e1)
-    err = float((y - x).abs().max() / x.abs().max())
+    err = None if grad_mode else float((y - x).abs().max() / x.abs().max())
 
-    # end to end through the public API: pinned host input -> device -> round trip -> host result
-    hx = x.cpu().pin_memory()
+    # end to end through the public API: pinned host input -> device -> step -> host result
+    hx = x.detach().cpu().pin_memory()
     hy = torch.empty_like(hx).pin_memory()
-    for _ in range(max(1, args.warmup // 2)):
-        xd = hx.to(dev, non_blocking=True)
-        plan.inverse(xd, out=f, ws=ws)
-        plan.forward(f, out=y, ws=ws)
+
+    def e2e_step():
+        if grad_mode:
+            with torch.no_grad():
+                xg.copy_(hx.to(dev, non_blocking=True))
+            step()
+        else:
+            xd = hx.to(dev, non_blocking=True)
+            plan.inverse(xd, out=f, ws=ws)
+            plan.forward(f, out=y, ws=ws)
         hy.copy_(y, non_blocking=True)
+
+    for _ in range(max(1, args.warmup // 2)):
+        e2e_step()
     barrier()
     t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t0.record(stream)
     for _ in range(args.steps):
-        xd = hx.to(dev, non_blocking=True)
-        plan.inverse(xd, out=f, ws=ws)
-        plan.forward(f, out=y, ws=ws)
-        hy.copy_(y, non_blocking=True)
+        e2e_step()
     t1.record(stream)
     barrier()
     ms_e2e = t0.elapsed_time(t1)
@@ -188,10 +214,11 @@ def run_ours(args, world, rank, local):
     # the theta-stage kernels alone, on the launch stream, same workload
     kern = {}
     if not N:
-        g = torch.from_numpy(synth.signal_gaussian((B, 2 * L - 1, L), seed=77)).to(dev)
-        ft = torch.empty(plan.shape(B), dtype=torch.complex128, device=dev)
-        fl = torch.empty(plan.shape(B), dtype=torch.complex128, device=dev)
-        for name, fn in (("theta_inverse", lambda: plan.inverse_theta(x, out=ft)),
+        g = torch.from_numpy(synth.signal_gaussian((B, 2 * L - 1, L), seed=77)).to(dev).to(cdt)
+        ft = torch.empty(plan.shape(B), dtype=cdt, device=dev)
+        fl = torch.empty(plan.shape(B), dtype=cdt, device=dev)
+        xd_ = x.detach()
+        for name, fn in (("theta_inverse", lambda: plan.inverse_theta(xd_, out=ft)),
                          ("theta_forward", lambda: plan.forward_theta(g, out=fl))):
             fn()
             torch.cuda.synchronize(dev)
@@ -212,6 +239,7 @@ def run_ours(args, world, rank, local):
         t = torch.tensor([ms, ms_e2e], device=dev, dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms, ms_e2e = float(t[0]), float(t[1])
+    # a gradient step is one inverse transform plus its adjoint: 2 transforms per signal, as a round trip
     transforms_per_step = 2 * B * world * (2 * N - 1 if N else 1)
     if rank != 0:
         if world > 1:
@@ -220,41 +248,80 @@ def run_ours(args, world, rank, local):
         return None
     ck = clocks.summary()
     sm_max = ck["sm_max_mhz"] or 2070.0
-    peak = NUM_SMS * FP64_LANES_PER_SM_CLK * 2 * sm_max * 1e6 / 1e12    # TFLOP/s
+    lanes = FP64_LANES_PER_SM_CLK if precision == "fp64" else FP32_LANES_PER_SM_CLK
+    peak = NUM_SMS * lanes * 2 * sm_max * 1e6 / 1e12    # TFLOP/s
     roof = None
     if kern:
         dom = max(kern, key=lambda k: kern[k]["ms"])
         ach = kern[dom]["tflops"]
         roof = {"bound": "alu", "kernel": dom, "achieved": round(ach, 4), "peak": round(peak, 4),
                 "unit": "TFLOP/s", "frac": round(ach / peak, 4), "traffic": None,
-                "peak_basis": f"FP64 FMA pipe: {NUM_SMS} SMs x {FP64_LANES_PER_SM_CLK} lanes x 2 flop x {sm_max:.0f} MHz"}
+                "peak_basis": f"{precision.upper()} FMA pipe: {NUM_SMS} SMs x {lanes} lanes x 2 flop x {sm_max:.0f} MHz"}
     value = transforms_per_step * args.steps / (ms * 1e-3)
     in_bytes = x.numel() * x.element_size()
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": "transforms/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if precision == "fp64" else "f32 (f64 starting values)",
         "data": "synthetic (seeded complex Gaussian coefficients)",
         "config": {"workload": args.workload, "description": desc, "L": L, "spin": spin, "N": N,
                    "batch_per_gpu": B, "transforms_per_step": transforms_per_step,
-                   "step": "inverse + forward of every signal in the batch",
+                   "step": ("loss forward (inverse) + backward (adjoint inverse) of the batch" if grad_mode
+                            else "inverse + forward of every signal in the batch"),
                    "l2": "working set > L2 (coefficients %.0f MB, workspace %.0f MB per step)"
                          % (in_bytes / 1e6, ws.numel() / 1e6),
                    "parallelism": f"dp{world} (independent batches, no data-path collective)"},
         "roundtrip_rel_max_err": err,
         "e2e": {"value": round(transforms_per_step * args.steps / (ms_e2e * 1e-3), 3), "unit": "transforms/s",
                 "h2d_bytes_per_step": in_bytes, "d2h_bytes_per_step": in_bytes},
-        "gpu_launches": args.steps * (8 if N else 6),
+        "gpu_launches": args.steps * (2 if grad_mode else (8 if N else 6)),
         "kernels": kern,
         "roofline": roof,
         "clocks": {k: ck[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
     }
-    if not args.no_cpu_baseline and world == 1:
+    if not args.no_cpu_baseline and world == 1 and not grad_mode:
         out["cpu_baseline"] = cpu_baseline(args.workload, rings=args.cpu_rings)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
     return out
+
+
+def run_serve(args, world, rank, local):
+    """Served stream (mixed L in {128..2048}, spin in {0, 2}, forward/inverse): saturated throughput,
+    then Poisson arrivals at rho x that rate; p50/p99 latency per rho.  Rank 0 only."""
+    import torch
+
+    from paper_2311_14670_gb300.serve import Server, make_requests
+
+    if rank != 0:
+        return None
+    torch.cuda.set_device(local)
+    precision = "fp32" if args.workload == "serve_fp32" else "fp64"
+    dt = torch.complex64 if precision == "fp32" else torch.complex128
+    srv = Server(device=local, budget_bytes=args.budget_gib << 30, streams=4, max_batch=4, precision=precision)
+    kinds = {(L, s) for L in (128, 256, 512, 1024, 2048) for s in (0, 2)}
+    srv.warm(kinds)
+    warm = make_requests(40, float("inf"), seed=1, dtype=dt)
+    srv.run(warm, keep_results=False)
+    sat = srv.run(make_requests(args.requests, float("inf"), seed=2, dtype=dt), keep_results=False)
+    out = {"saturated": sat}
+    for rho in (0.5, 0.8, 0.95):
+        st = srv.run(make_requests(args.requests, rho * sat["throughput_rps"], seed=3, dtype=dt),
+                     keep_results=False)
+        out[f"rho_{rho}"] = st
+    res = {"metric": "served transforms/sec", "value": round(sat["throughput_rps"], 3), "unit": "transforms/s",
+           "n_gpus": 1, "steps": args.requests, "warmup": 40, "ms_per_step": round(1e3 / sat["throughput_rps"], 4),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64" if precision == "fp64" else "f32 (f64 starting values)",
+           "data": "synthetic (seeded complex Gaussian inputs, Poisson arrivals)",
+           "config": {"workload": args.workload, "requests": args.requests,
+                      "mix": "L uniform {128,256,512,1024,2048}, spin uniform {0,2}, forward/inverse uniform",
+                      "budget_gib": args.budget_gib, "streams": 4, "max_batch": 4},
+           "serving": {k: {q: (round(v, 3) if isinstance(v, float) else v) for q, v in st.items()}
+                       for k, st in out.items()}}
+    return res
 
 
 def cpu_baseline(workload: str, rings: int = 8) -> dict:
@@ -358,13 +425,19 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--workload", default="l1024s2b4", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="l1024s2b4", choices=sorted(WORKLOADS) + ["serve_fp64", "serve_fp32"])
+    ap.add_argument("--requests", type=int, default=512, help="served-stream length (serve_* workloads)")
+    ap.add_argument("--budget-gib", type=int, default=16, help="HBM admission budget (serve_* workloads)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-rings", type=int, default=8, help="rings/degrees of the oracle sample")
     args = ap.parse_args()
     world, rank, local = dist_setup()
-    if args.impl == "reference":
+    if args.workload.startswith("serve_"):
+        out = None if args.impl == "reference" else run_serve(args, world, rank, local)
+        if args.impl == "reference" and rank == 0:
+            out = {"impl": "reference", "unavailable": "the oracle has no served mode"}
+    elif args.impl == "reference":
         out = run_reference(args, world, rank)
     else:
         out = run_ours(args, world, rank, local)

@@ -43,7 +43,11 @@ struct SeedData {
 };
 
 // Recursion step j -> j+1 coefficients for one (n, m), see theta_kernels.cu.
-constexpr int kCoefPerStep = 6;  // A, C, K_north, K_south, Kd_north, Kd_south
+constexpr int kCoefPerStep = 6;  // A, C, K_north, K_south, Kd_north, Kd_south (float32 kernels)
+// Block-normalised form used by the float64 kernels (plan.cu, coefn_kernel):
+// A', K_n', K_s', gamma_j, gamma_{j+1}, A'', Kd_n'', Kd_s'', eta_{j+1}, 1/gamma_j
+constexpr int kCoefPerStepN = 10;
+constexpr int kNormBlock = 8;    // normalisation block length (steps), aligned at l0
 
 struct Plan {
   int L = 0, spin = 0, N = 0, precision = 0, max_batch = 0, device = 0;
@@ -53,7 +57,7 @@ struct Plan {
   bool wigner = false;
 
   // device tables
-  double* coef = nullptr;      // [nN][T][L][kCoefPerStep]  (m index = m + L - 1, step j); FP64 plans
+  double* coef = nullptr;      // [nN][T][L][kCoefPerStepN] (m index = m + L - 1, step j); FP64 plans
   float* coef32 = nullptr;     // the same table rounded to float (FP32 plans)
   float* v32 = nullptr;        // [L] ring variable v rounded to float (FP32 plans)
   RingData* ring = nullptr;    // [L]

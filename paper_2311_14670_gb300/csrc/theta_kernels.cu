@@ -42,6 +42,44 @@ using namespace theta;
 // ------------------------------------------------------------------------------------------
 constexpr int kChunk = 32;
 
+// Coefficients of one step of the block-normalised recursion (layout of plan.cu's coefn_kernel).
+struct StepN {
+  double Ap, Knp, Ksp, g, gn, App, Kdnp, Kdsp, en, ig;
+};
+
+__device__ __forceinline__ StepN stepn_at(const double* c) {
+  return {c[0], c[1], c[2], c[3], c[4], c[5], c[6], c[7], c[8], c[9]};
+}
+
+// One step of the block-normalised recursion (2 FP64 instructions plain, 3 in the difference
+// form); x, y are (u^j, u^{j-1}) plain or (d^j, ehat^j) in the difference form.
+template <bool DIFF>
+__device__ __forceinline__ void stepn(double& x, double& y, double v, unsigned nmask, bool north, const StepN& c) {
+  if (!DIFF) {
+    const double P = fma(flip_sign(c.Ap, nmask), v, north ? c.Knp : c.Ksp);
+    const double xn = fma(P, x, -y);
+    y = x;
+    x = xn;
+  } else {
+    const unsigned smask = nmask ^ 0x80000000u;          // sign of sigma: + north, - south
+    const double Q = fma(flip_sign(c.App, nmask), v, north ? c.Kdnp : c.Kdsp);
+    const double en = fma(Q, x, flip_sign(y, smask));     // Q' d + sigma ehat
+    x = fma(c.en, en, flip_sign(x, smask));                // sigma d + eta ehat'
+    y = en;
+  }
+}
+
+// End of a normalisation block (after the step j -> j+1): back to (d^{j+1}, d^j) / (d^{j+1}, e^{j+1}).
+template <bool DIFF>
+__device__ __forceinline__ void unnormalise(double& x, double& y, const StepN& c) {
+  if (!DIFF) {
+    x *= c.gn;
+    y *= c.g;
+  } else {
+    y *= c.en;
+  }
+}
+
 template <int KT, int NB, bool DIFF>
 __device__ __forceinline__ void inverse_body(const InvArgs& a, int m, int ni, int tile, int l0,
                                              double2* __restrict__ hs, double* __restrict__ cs) {
@@ -50,7 +88,7 @@ __device__ __forceinline__ void inverse_body(const InvArgs& a, int m, int ni, in
   const int mi = m + L - 1;
   const int sig0 = blockIdx.z * NB;
   const SeedData sd = a.seed[(size_t)ni * T + mi];
-  const double* coef_m = a.coef + ((size_t)ni * T + mi) * (size_t)L * kCoefPerStep;
+  const double* coef_m = a.coef + ((size_t)ni * T + mi) * (size_t)L * kCoefPerStepN;
 
   double x[KT], y[KT], v[KT];
   int E[KT], tt[KT];
@@ -70,7 +108,7 @@ __device__ __forceinline__ void inverse_body(const InvArgs& a, int m, int ni, in
       x[i] = 0.0; E[i] = 0; v[i] = 0.0; north[i] = true;
     }
     nmask[i] = north[i] ? 0x80000000u : 0u;
-    y[i] = DIFF ? x[i] : 0.0;   // plain: d^{l0-1} = 0;  difference form: e^{l0} = d^{l0}
+    y[i] = 0.0;   // plain: u^{l0-1} = d^{l0-1} = 0; difference form: ehat^{l0} = 0 (its weight C_{l0} is 0)
 #pragma unroll
     for (int b = 0; b < NB; ++b) acc[i][b] = make_double2(0.0, 0.0);
   }
@@ -85,14 +123,15 @@ __device__ __forceinline__ void inverse_body(const InvArgs& a, int m, int ni, in
         const double2* f = reinterpret_cast<const double2*>(a.flm) +
                            ((size_t)(sig * a.nN + ni) * L + j) * T + mi;
         h = *f;
-        const double s = scale[j];
+        // plain chains carry u^j = d^j / gamma_j: fold gamma_j into the coefficient
+        const double s = DIFF ? scale[j] : scale[j] * coef_m[(size_t)j * kCoefPerStepN + 3];
         h.x *= s; h.y *= s;
       }
       hs[q] = h;
     }
-    for (int q = tid; q < kChunk * kCoefPerStep; q += nt) {
-      const int j = jc + q / kCoefPerStep;
-      cs[q] = (j < L) ? coef_m[(size_t)jc * kCoefPerStep + q] : 0.0;
+    for (int q = tid; q < kChunk * kCoefPerStepN; q += nt) {
+      const int j = jc + q / kCoefPerStepN;
+      cs[q] = (j < L) ? coef_m[(size_t)jc * kCoefPerStepN + q] : 0.0;
     }
     __syncthreads();
     const int jend = min(kChunk, L - jc);
@@ -120,10 +159,13 @@ __device__ __forceinline__ void inverse_body(const InvArgs& a, int m, int ni, in
             }
           }
           if (jc + jj < L - 1) {
-            const double* cp = cs + jj * kCoefPerStep;
-            const StepCoef c = {cp[0], cp[1], cp[2], cp[3], cp[4], cp[5]};
+            const StepN c = stepn_at(cs + jj * kCoefPerStepN);
 #pragma unroll
-            for (int i = 0; i < KT; ++i) step<DIFF>(x[i], y[i], v[i], nmask[i], north[i], c);
+            for (int i = 0; i < KT; ++i) stepn<DIFF>(x[i], y[i], v[i], nmask[i], north[i], c);
+            if (u == kNormBlock - 1) {
+#pragma unroll
+              for (int i = 0; i < KT; ++i) unnormalise<DIFF>(x[i], y[i], c);
+            }
           }
         }
       }
@@ -152,7 +194,7 @@ __device__ __forceinline__ void inverse_body(const InvArgs& a, int m, int ni, in
 template <int KT, int NB>
 __global__ void __launch_bounds__(128) theta_inverse_kernel(InvArgs a, int ntiles) {
   __shared__ double2 hs[kChunk * NB];
-  __shared__ double cs[kChunk * kCoefPerStep];
+  __shared__ double cs[kChunk * kCoefPerStepN];
   const int L = a.L;
   const int rank = blockIdx.x / ntiles, tile = blockIdx.x % ntiles;
   const int m = m_of_rank(rank);
@@ -256,11 +298,10 @@ __global__ void __launch_bounds__(128) theta_forward_kernel(FwdArgs a) {
       x[i] = 0.0; E[i] = 0; north[i] = true;
     }
     nmask[i] = north[i] ? 0x80000000u : 0u;
-    const bool dslot = (PAT == 1) || i == 0 || i == KT - 1;
-    y[i] = dslot ? x[i] : 0.0;
+    y[i] = 0.0;   // plain: u^{l0-1} = 0; difference form: ehat^{l0} = 0 (weight C_{l0} = 0)
   }
 
-  const double* coef_m = a.coef + ((size_t)ni * T + mi) * (size_t)L * kCoefPerStep;
+  const double* coef_m = a.coef + ((size_t)ni * T + mi) * (size_t)L * kCoefPerStepN;
   int buf = 0;
   for (int j0 = l0; j0 < L; j0 += JR) {
     double p[32];
@@ -274,10 +315,17 @@ __global__ void __launch_bounds__(128) theta_forward_kernel(FwdArgs a) {
     for (int jr = 0; jr < JR; ++jr) {
       const int j = j0 + jr;
       if (j < L) {
+        const double2* c2 = reinterpret_cast<const double2*>(coef_m + (size_t)j * kCoefPerStepN);
+        const double2 c01 = __ldg(c2), c23 = __ldg(c2 + 1), c45 = __ldg(c2 + 2), c67 = __ldg(c2 + 3),
+                      c89 = __ldg(c2 + 4);
+        const StepN c = {c01.x, c01.y, c23.x, c23.y, c45.x, c45.y, c67.x, c67.y, c89.x, c89.y};
 #pragma unroll
         for (int i = 0; i < KT; ++i) {
           if ((live >> i) & 1u) {
-            const double xl = (E[i] == 0) ? x[i] : 0.0;
+            // partial sums are kept in units of u^j = d^j / gamma_j (rescaled at the output)
+            const bool dslot = (PAT == 1) || i == 0 || i == KT - 1;
+            double xl = (E[i] == 0) ? x[i] : 0.0;
+            if (dslot) xl *= c.ig;
             const int pos = i * nt + tid;
 #pragma unroll
             for (int b = 0; b < NB; ++b) {
@@ -288,13 +336,20 @@ __global__ void __launch_bounds__(128) theta_forward_kernel(FwdArgs a) {
           }
         }
         if (j < L - 1) {
-          const StepCoef c = load_coef(coef_m + (size_t)j * kCoefPerStep);
 #pragma unroll
           for (int i = 0; i < KT; ++i) {
             const double v = vs[i * nt + tid];
             const bool dslot = (PAT == 1) || i == 0 || i == KT - 1;
-            if (dslot) step<true>(x[i], y[i], v, nmask[i], north[i], c);
-            else step<false>(x[i], y[i], v, nmask[i], north[i], c);
+            if (dslot) stepn<true>(x[i], y[i], v, nmask[i], north[i], c);
+            else stepn<false>(x[i], y[i], v, nmask[i], north[i], c);
+          }
+          if (((j - l0) & (kNormBlock - 1)) == kNormBlock - 1) {     // end of a normalisation block
+#pragma unroll
+            for (int i = 0; i < KT; ++i) {
+              const bool dslot = (PAT == 1) || i == 0 || i == KT - 1;
+              if (dslot) unnormalise<true>(x[i], y[i], c);
+              else unnormalise<false>(x[i], y[i], c);
+            }
           }
         }
       }
@@ -314,7 +369,7 @@ __global__ void __launch_bounds__(128) theta_forward_kernel(FwdArgs a) {
       if (j < L && sig < a.nsig) {
         double* o = reinterpret_cast<double*>(
             reinterpret_cast<double2*>(a.flm) + ((size_t)(sig * a.nN + ni) * L + j) * T + mi);
-        o[reim] = tot * scale[j];
+        o[reim] = tot * (scale[j] * coef_m[(size_t)j * kCoefPerStepN + 3]);   // * gamma_j
       }
     }
     buf ^= 1;

@@ -80,9 +80,34 @@ __device__ __forceinline__ void unnormalise(double& x, double& y, const StepN& c
   }
 }
 
-template <int KT, int NB, bool DIFF>
-__device__ __forceinline__ void inverse_body(const InvArgs& a, int m, int ni, int tile, int l0,
+// Signal slots of a CTA.  Slot b < NB is signal sig0 + b at (m, n); with pairing (PAIR), slot
+// NB + b is the same signal at (-m, -n), whose d-functions are d^l_{-m,-n} = (-1)^{m-n} d^l_{m,n}
+// (Sec. 3.3 symmetry): the partner column reuses the recursion of (m, n), scaled by that sign.
+struct Slot {
+  long long sig_off;   // signal offset (sig * nN + ni) or -1 if inactive
+  int mi;              // column index m + L - 1 of the slot
+  int m;
+  double sign;
+};
+
+template <int NB, bool PAIR>
+__device__ __forceinline__ Slot slot_of(int b, int sig0, int nsig, int nN, int ni, int m, int n, int L) {
+  Slot sl;
+  const bool partner = PAIR && b >= NB;
+  const int sig = sig0 + (partner ? b - NB : b);
+  const bool active = sig < nsig && !(partner && m == 0 && n == 0);
+  const int nis = partner ? (nN - 1 - ni) : ni;
+  sl.m = partner ? -m : m;
+  sl.mi = sl.m + L - 1;
+  sl.sig_off = active ? (long long)sig * nN + nis : -1;
+  sl.sign = (partner && ((m - n) & 1)) ? -1.0 : 1.0;
+  return sl;
+}
+
+template <int KT, int NB, bool DIFF, bool PAIR>
+__device__ __forceinline__ void inverse_body(const InvArgs& a, int m, int ni, int n, int tile, int l0,
                                              double2* __restrict__ hs, double* __restrict__ cs) {
+  constexpr int NBX = PAIR ? 2 * NB : NB;
   const int L = a.L, T = 2 * L - 1;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int mi = m + L - 1;
@@ -94,7 +119,7 @@ __device__ __forceinline__ void inverse_body(const InvArgs& a, int m, int ni, in
   int E[KT], tt[KT];
   bool north[KT];
   unsigned nmask[KT];
-  double2 acc[KT][NB];
+  double2 acc[KT][NBX];
 #pragma unroll
   for (int i = 0; i < KT; ++i) {
     const int t = tile * KT * nt + i * nt + tid;
@@ -110,21 +135,20 @@ __device__ __forceinline__ void inverse_body(const InvArgs& a, int m, int ni, in
     nmask[i] = north[i] ? 0x80000000u : 0u;
     y[i] = 0.0;   // plain: u^{l0-1} = d^{l0-1} = 0; difference form: ehat^{l0} = 0 (its weight C_{l0} is 0)
 #pragma unroll
-    for (int b = 0; b < NB; ++b) acc[i][b] = make_double2(0.0, 0.0);
+    for (int b = 0; b < NBX; ++b) acc[i][b] = make_double2(0.0, 0.0);
   }
 
-  const double* scale = a.scale + (size_t)ni * L;
+  const double* scale = a.scale + (size_t)ni * L;   // the same for n and -n
   for (int jc = l0; jc < L; jc += kChunk) {
     __syncthreads();
-    for (int q = tid; q < kChunk * NB; q += nt) {
-      const int jj = q / NB, b = q % NB, j = jc + jj, sig = sig0 + b;
+    for (int q = tid; q < kChunk * NBX; q += nt) {
+      const int jj = q / NBX, b = q % NBX, j = jc + jj;
+      const Slot sl = slot_of<NB, PAIR>(b, sig0, a.nsig, a.nN, ni, m, n, L);
       double2 h = make_double2(0.0, 0.0);
-      if (j < L && sig < a.nsig) {
-        const double2* f = reinterpret_cast<const double2*>(a.flm) +
-                           ((size_t)(sig * a.nN + ni) * L + j) * T + mi;
-        h = *f;
+      if (j < L && sl.sig_off >= 0) {
+        h = reinterpret_cast<const double2*>(a.flm)[((size_t)sl.sig_off * L + j) * T + sl.mi];
         // plain chains carry u^j = d^j / gamma_j: fold gamma_j into the coefficient
-        const double s = DIFF ? scale[j] : scale[j] * coef_m[(size_t)j * kCoefPerStepN + 3];
+        const double s = sl.sign * (DIFF ? scale[j] : scale[j] * coef_m[(size_t)j * kCoefPerStepN + 3]);
         h.x *= s; h.y *= s;
       }
       hs[q] = h;
@@ -144,15 +168,15 @@ __device__ __forceinline__ void inverse_body(const InvArgs& a, int m, int ni, in
       for (int u = 0; u < 8; ++u) {
         const int jj = j8 + u;
         if (jj < jend) {
-          double2 h[NB];
+          double2 h[NBX];
 #pragma unroll
-          for (int b = 0; b < NB; ++b) h[b] = hs[jj * NB + b];
+          for (int b = 0; b < NBX; ++b) h[b] = hs[jj * NBX + b];
 #pragma unroll
           for (int i = 0; i < KT; ++i) {
             if ((live >> i) & 1u) {
               const double xl = (E[i] == 0) ? x[i] : 0.0;
 #pragma unroll
-              for (int b = 0; b < NB; ++b) {
+              for (int b = 0; b < NBX; ++b) {
                 acc[i][b].x = fma(xl, h[b].x, acc[i][b].x);
                 acc[i][b].y = fma(xl, h[b].y, acc[i][b].y);
               }
@@ -175,37 +199,38 @@ __device__ __forceinline__ void inverse_body(const InvArgs& a, int m, int ni, in
   }
 
 #pragma unroll
-  for (int i = 0; i < KT; ++i) {
-    if (tt[i] < L) {
-      const long long col = a.m_mod ? (m >= 0 ? m : m + T) : mi;
+  for (int b = 0; b < NBX; ++b) {
+    const Slot sl = slot_of<NB, PAIR>(b, sig0, a.nsig, a.nN, ni, m, n, L);
+    if (sl.sig_off < 0) continue;
+    const long long col = a.m_mod ? (sl.m >= 0 ? sl.m : sl.m + T) : sl.mi;
 #pragma unroll
-      for (int b = 0; b < NB; ++b) {
-        const int sig = sig0 + b;
-        if (sig < a.nsig) {
-          double2* o = reinterpret_cast<double2*>(a.out) + (size_t)(sig * a.nN + ni) * a.s_sig +
-                       tt[i] * a.s_t + col * a.s_m;
-          *o = acc[i][b];
-        }
+    for (int i = 0; i < KT; ++i) {
+      if (tt[i] < L) {
+        double2* o = reinterpret_cast<double2*>(a.out) + (size_t)sl.sig_off * a.s_sig + tt[i] * a.s_t + col * a.s_m;
+        *o = acc[i][b];
       }
     }
   }
 }
 
-template <int KT, int NB>
+// Grid: x = (rank of m) * ntiles + tile, y = n index (with pairing: only n >= 0, and for n = 0 only
+// m >= 0 -- the CTA of (m, n) also produces (-m, -n)), z = batch group of NB signals.
+template <int KT, int NB, bool PAIR>
 __global__ void __launch_bounds__(128) theta_inverse_kernel(InvArgs a, int ntiles) {
-  __shared__ double2 hs[kChunk * NB];
+  __shared__ double2 hs[kChunk * (PAIR ? 2 * NB : NB)];
   __shared__ double cs[kChunk * kCoefPerStepN];
   const int L = a.L;
   const int rank = blockIdx.x / ntiles, tile = blockIdx.x % ntiles;
   const int m = m_of_rank(rank);
-  const int ni = blockIdx.y;
-  const int n = a.seed[(size_t)ni * (2 * L - 1) + m + L - 1].l0;  // l0 = max(|m|,|n|)
-  const int l0 = n;
+  const int ni = PAIR ? (a.nN - 1) / 2 + (int)blockIdx.y : (int)blockIdx.y;
+  const int n = ni - (a.nN - 1) / 2;          // used only with pairing (n-set symmetric about 0)
+  if (PAIR && n == 0 && m < 0) return;        // produced by the CTA of -m
+  const int l0 = a.seed[(size_t)ni * (2 * L - 1) + m + L - 1].l0;   // max(|m|, |n|)
   // Does this tile contain a ring that needs the difference form?
   const int t_lo = tile * KT * blockDim.x, t_hi = min(L, t_lo + KT * (int)blockDim.x) - 1;
   const bool diff = a.ring[t_lo].diff || a.ring[t_hi].diff;
-  if (diff) inverse_body<KT, NB, true>(a, m, ni, tile, l0, hs, cs);
-  else inverse_body<KT, NB, false>(a, m, ni, tile, l0, hs, cs);
+  if (diff) inverse_body<KT, NB, true, PAIR>(a, m, ni, n, tile, l0, hs, cs);
+  else inverse_body<KT, NB, false, PAIR>(a, m, ni, n, tile, l0, hs, cs);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -234,44 +259,51 @@ __device__ __forceinline__ double warp_reduce_scatter32(double (&v)[32]) {
   return v[0];
 }
 
-template <int KT, int NB, int PAT>
+template <int KT, int NB, int PAT, bool PAIR>
 __global__ void __launch_bounds__(128) theta_forward_kernel(FwdArgs a) {
-  constexpr int JR = 16 / NB;            // degrees per reduction group
+  constexpr int NBX = PAIR ? 2 * NB : NB;
+  constexpr int JR = 16 / NBX;           // degrees per reduction group
   extern __shared__ double2 smem[];
   const int L = a.L, T = 2 * L - 1;
   const int nt = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nwarps = nt >> 5;
   const int rows = KT * nt;                // padded ring count
-  double2* gs = smem;                                          // [NB][rows]
-  double* red = reinterpret_cast<double*>(gs + NB * rows);    // [2][nwarps][32]
+  double2* gs = smem;                                          // [NBX][rows]
+  double* red = reinterpret_cast<double*>(gs + NBX * rows);   // [2][nwarps][32]
   double* vs = red + 2 * nwarps * 32;                          // [rows]
 
   const int m = m_of_rank(blockIdx.x);
   const int mi = m + L - 1;
-  const int ni = blockIdx.y;
+  const int ni = PAIR ? (a.nN - 1) / 2 + (int)blockIdx.y : (int)blockIdx.y;
+  const int n = ni - (a.nN - 1) / 2;          // used only with pairing
+  if (PAIR && n == 0 && m < 0) return;        // produced by the CTA of -m
   const int sig0 = blockIdx.z * NB;
   const SeedData sd = a.seed[(size_t)ni * T + mi];
   const int l0 = sd.l0;
-  const double* scale = a.scale + (size_t)ni * L;
+  const double* scale = a.scale + (size_t)ni * L;   // the same for n and -n
 
-  // zero the degrees l < l0 of this column
-  for (int q = tid; q < NB * min(l0, L); q += nt) {
-    const int b = q / min(l0, L), j = q % min(l0, L), sig = sig0 + b;
-    if (sig < a.nsig)
-      reinterpret_cast<double2*>(a.flm)[((size_t)(sig * a.nN + ni) * L + j) * T + mi] = make_double2(0.0, 0.0);
+  // zero the degrees l < l0 of the CTA's columns
+  const int lz = min(l0, L);
+  for (int q = tid; q < NBX * lz; q += nt) {
+    const int b = q / lz, j = q % lz;
+    const Slot sl = slot_of<NB, PAIR>(b, sig0, a.nsig, a.nN, ni, m, n, L);
+    if (sl.sig_off >= 0)
+      reinterpret_cast<double2*>(a.flm)[((size_t)sl.sig_off * L + j) * T + sl.mi] = make_double2(0.0, 0.0);
   }
   if (l0 >= L) return;
 
-  // stage g (times the ring fold factors) and the ring variables
-  const long long col = a.m_mod ? (m >= 0 ? m : m + T) : mi;
-  for (int q = tid; q < NB * rows; q += nt) {
-    const int b = q / rows, pos = q % rows, sig = sig0 + b;
+  // stage g (times the ring fold factors and the pairing sign) and the ring variables
+  for (int q = tid; q < NBX * rows; q += nt) {
+    const int b = q / rows, pos = q % rows;
+    const Slot sl = slot_of<NB, PAIR>(b, sig0, a.nsig, a.nN, ni, m, n, L);
     bool act;
     const int t = ring_of<KT>(pos / nt, pos % nt, nt, L, act);
     double2 g = make_double2(0.0, 0.0);
-    if (act && sig < a.nsig) {
-      g = reinterpret_cast<const double2*>(a.g)[(size_t)(sig * a.nN + ni) * a.s_sig + t * a.s_t + col * a.s_m];
-      if (a.use_nu) { const double w = a.nu[t]; g.x *= w; g.y *= w; }
+    if (act && sl.sig_off >= 0) {
+      const long long col = a.m_mod ? (sl.m >= 0 ? sl.m : sl.m + T) : sl.mi;
+      g = reinterpret_cast<const double2*>(a.g)[(size_t)sl.sig_off * a.s_sig + t * a.s_t + col * a.s_m];
+      const double w = (a.use_nu ? a.nu[t] : 1.0) * sl.sign;
+      g.x *= w; g.y *= w;
     }
     gs[q] = g;
   }
@@ -328,10 +360,10 @@ __global__ void __launch_bounds__(128) theta_forward_kernel(FwdArgs a) {
             if (dslot) xl *= c.ig;
             const int pos = i * nt + tid;
 #pragma unroll
-            for (int b = 0; b < NB; ++b) {
+            for (int b = 0; b < NBX; ++b) {
               const double2 g = gs[b * rows + pos];
-              p[jr * 2 * NB + 2 * b] = fma(xl, g.x, p[jr * 2 * NB + 2 * b]);
-              p[jr * 2 * NB + 2 * b + 1] = fma(xl, g.y, p[jr * 2 * NB + 2 * b + 1]);
+              p[jr * 2 * NBX + 2 * b] = fma(xl, g.x, p[jr * 2 * NBX + 2 * b]);
+              p[jr * 2 * NBX + 2 * b + 1] = fma(xl, g.y, p[jr * 2 * NBX + 2 * b + 1]);
             }
           }
         }
@@ -364,11 +396,12 @@ __global__ void __launch_bounds__(128) theta_forward_kernel(FwdArgs a) {
     if (warp == 0) {
       double tot = red[(buf * nwarps) * 32 + lane];
       for (int w = 1; w < nwarps; ++w) tot += red[(buf * nwarps + w) * 32 + lane];
-      const int jr = lane / (2 * NB), b = (lane / 2) % NB, reim = lane & 1;
-      const int j = j0 + jr, sig = sig0 + b;
-      if (j < L && sig < a.nsig) {
+      const int jr = lane / (2 * NBX), b = (lane / 2) % NBX, reim = lane & 1;
+      const int j = j0 + jr;
+      const Slot sl = slot_of<NB, PAIR>(b, sig0, a.nsig, a.nN, ni, m, n, L);
+      if (j < L && sl.sig_off >= 0) {
         double* o = reinterpret_cast<double*>(
-            reinterpret_cast<double2*>(a.flm) + ((size_t)(sig * a.nN + ni) * L + j) * T + mi);
+            reinterpret_cast<double2*>(a.flm) + ((size_t)sl.sig_off * L + j) * T + sl.mi);
         o[reim] = tot * (scale[j] * coef_m[(size_t)j * kCoefPerStepN + 3]);   // * gamma_j
       }
     }
@@ -376,62 +409,74 @@ __global__ void __launch_bounds__(128) theta_forward_kernel(FwdArgs a) {
   }
 }
 
-template <int KT, int NB>
+template <int KT, int NB, bool PAIR>
 cudaError_t launch_inv(const Plan& p, const InvArgs& a, cudaStream_t st) {
   const int nt = 128;
   const int ntiles = (p.L + KT * nt - 1) / (KT * nt);
-  dim3 grid(p.T * ntiles, a.nN, (a.nsig + NB - 1) / NB);
-  theta_inverse_kernel<KT, NB><<<grid, nt, 0, st>>>(a, ntiles);
+  dim3 grid(p.T * ntiles, PAIR ? (a.nN + 1) / 2 : a.nN, (a.nsig + NB - 1) / NB);
+  theta_inverse_kernel<KT, NB, PAIR><<<grid, nt, 0, st>>>(a, ntiles);
   return cudaGetLastError();
 }
 
-template <int NB>
+template <int NB, bool PAIR>
 cudaError_t launch_inv_nb(const Plan& p, const InvArgs& a, cudaStream_t st) {
-  if (p.L <= 128) return launch_inv<1, NB>(p, a, st);
-  if (p.L <= 512) return launch_inv<2, NB>(p, a, st);
-  return launch_inv<4, NB>(p, a, st);
+  if (p.L <= 128) return launch_inv<1, NB, PAIR>(p, a, st);
+  if (p.L <= 512) return launch_inv<2, NB, PAIR>(p, a, st);
+  return launch_inv<4, NB, PAIR>(p, a, st);
 }
 
-template <int KT, int NB, int PAT>
+template <int KT, int NB, int PAT, bool PAIR>
 cudaError_t launch_fwd(const Plan& p, const FwdArgs& a, int nt, cudaStream_t st) {
+  constexpr int NBX = PAIR ? 2 * NB : NB;
   const int rows = KT * nt;
-  const size_t smem = sizeof(double2) * NB * rows + sizeof(double) * (2 * (nt / 32) * 32 + rows);
-  auto kern = theta_forward_kernel<KT, NB, PAT>;
+  const size_t smem = sizeof(double2) * NBX * rows + sizeof(double) * (2 * (nt / 32) * 32 + rows);
+  auto kern = theta_forward_kernel<KT, NB, PAT, PAIR>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  dim3 grid(p.T, a.nN, (a.nsig + NB - 1) / NB);
+  dim3 grid(p.T, PAIR ? (a.nN + 1) / 2 : a.nN, (a.nsig + NB - 1) / NB);
   kern<<<grid, nt, smem, st>>>(a);
   return cudaGetLastError();
 }
 
-template <int NB>
+template <int NB, bool PAIR>
 cudaError_t launch_fwd_nb(const Plan& p, const FwdArgs& a, cudaStream_t st) {
   const int L = p.L;
-  if (L <= 128) return launch_fwd<1, NB, 1>(p, a, ((L + 31) / 32) * 32, st);
-  if (L <= 256) return launch_fwd<2, NB, 1>(p, a, 128, st);
-  if (L <= 512) return launch_fwd<4, NB, 0>(p, a, 128, st);
-  if (L <= 1024) return launch_fwd<8, NB, 0>(p, a, 128, st);
+  if (L <= 128) return launch_fwd<1, NB, 1, PAIR>(p, a, ((L + 31) / 32) * 32, st);
+  if (L <= 256) return launch_fwd<2, NB, 1, PAIR>(p, a, 128, st);
+  if (L <= 512) return launch_fwd<4, NB, 0, PAIR>(p, a, 128, st);
+  if (L <= 1024) return launch_fwd<8, NB, 0, PAIR>(p, a, 128, st);
   // KT = 16 slots of nt rings: the polar caps (sin theta < kPoleSin, t < 0.05 L) fit in the
   // first and last slot because nt >= L/16.
   const int nt = ((L + 16 * 32 - 1) / (16 * 32)) * 32;
   if (nt > 128) return cudaErrorInvalidConfiguration;  // L > 2048: 128-thread launch bound
-  return launch_fwd<16, NB, 0>(p, a, nt, st);
+  return launch_fwd<16, NB, 0, PAIR>(p, a, nt, st);
 }
+
+// Pairing (m, n) with (-m, -n) needs the set of n to be symmetric: spin-0 sphere plans and Wigner.
+bool paired(const Plan& p) { return p.wigner || p.spin == 0; }
 
 }  // namespace
 
 cudaError_t launch_theta_inverse(const Plan& p, const InvArgs& a, cudaStream_t st) {
   if (p.precision == S2GB_FP32) return launch_theta_inverse_f32(p, a, st);
-  if (a.nsig >= 4) return launch_inv_nb<4>(p, a, st);
-  if (a.nsig >= 2) return launch_inv_nb<2>(p, a, st);
-  return launch_inv_nb<1>(p, a, st);
+  if (paired(p)) {
+    if (a.nsig >= 2) return launch_inv_nb<2, true>(p, a, st);
+    return launch_inv_nb<1, true>(p, a, st);
+  }
+  if (a.nsig >= 4) return launch_inv_nb<4, false>(p, a, st);
+  if (a.nsig >= 2) return launch_inv_nb<2, false>(p, a, st);
+  return launch_inv_nb<1, false>(p, a, st);
 }
 
 cudaError_t launch_theta_forward(const Plan& p, const FwdArgs& a, cudaStream_t st) {
   if (p.precision == S2GB_FP32) return launch_theta_forward_f32(p, a, st);
-  if (a.nsig >= 4 && p.L <= 1024) return launch_fwd_nb<4>(p, a, st);
-  if (a.nsig >= 2) return launch_fwd_nb<2>(p, a, st);
-  return launch_fwd_nb<1>(p, a, st);
+  if (paired(p)) {
+    if (a.nsig >= 2 && p.L <= 1024) return launch_fwd_nb<2, true>(p, a, st);
+    return launch_fwd_nb<1, true>(p, a, st);
+  }
+  if (a.nsig >= 4 && p.L <= 1024) return launch_fwd_nb<4, false>(p, a, st);
+  if (a.nsig >= 2) return launch_fwd_nb<2, false>(p, a, st);
+  return launch_fwd_nb<1, false>(p, a, st);
 }
 
 }  // namespace s2gb

@@ -444,7 +444,12 @@ cudaError_t launch_fwd_nb(const Plan& p, const FwdArgs& a, cudaStream_t st) {
   if (L <= 128) return launch_fwd<1, NB, 1, PAIR>(p, a, ((L + 31) / 32) * 32, st);
   if (L <= 256) return launch_fwd<2, NB, 1, PAIR>(p, a, 128, st);
   if (L <= 512) return launch_fwd<4, NB, 0, PAIR>(p, a, 128, st);
-  if (L <= 1024) return launch_fwd<8, NB, 0, PAIR>(p, a, 128, st);
+  // Unpaired: 16 rings per thread (64 threads) halve the cross-thread reduction; paired CTAs carry
+  // twice the signal slots and run better with 8 rings per thread (measured on GB300).
+  if (L <= 1024) {
+    if (PAIR) return launch_fwd<8, NB, 0, PAIR>(p, a, 128, st);
+    return launch_fwd<16, NB, 0, PAIR>(p, a, ((L + 16 * 32 - 1) / (16 * 32)) * 32, st);
+  }
   // KT = 16 slots of nt rings: the polar caps (sin theta < kPoleSin, t < 0.05 L) fit in the
   // first and last slot because nt >= L/16.
   const int nt = ((L + 16 * 32 - 1) / (16 * 32)) * 32;

@@ -79,9 +79,10 @@ enum {
  * max_batch >= 1 bounds the `batch` argument of later calls.  The plan holds on the device the
  * recursion coefficient tables (Sec. 3.3 readings, O(L^2) per spin), the per-ring and per-order
  * log-space seed data (Eq. "initial_values") and the FFT weights; it creates cuFFT plans.
- * Returns S2GB_EINVAL for L < 1, |spin| >= L (sphere), N < 0 or N > L, max_batch < 1, an unknown
- * sampling or precision; S2GB_ENOMEM / S2GB_ECUDA / S2GB_ECUFFT on device failures.  On failure
- * *out is set to NULL.  The calling thread's current device is restored on return.
+ * Returns S2GB_EINVAL for L < 1 or L > 8192, |spin| >= L (sphere), N < 0 or N > L, max_batch < 1,
+ * an unknown sampling or precision; S2GB_EUNSUPPORTED for S2GB_FP32 with L > 2048;
+ * S2GB_ENOMEM / S2GB_ECUDA / S2GB_ECUFFT on device failures.  On failure *out is set to NULL.  The
+ * calling thread's current device is restored on return.
  */
 int s2gb_plan_create(s2gb_plan* out, int L, int spin, int N, int sampling, int precision,
                      int max_batch, int device);
@@ -125,7 +126,8 @@ int s2gb_adjoint_inverse(s2gb_plan plan, const void* f_bar, void* flm_bar, int b
  *     flm[b][l][m+L-1] = (-1)^s sqrt((2l+1)/(4 pi)) sum_t d^l_{m,-s}(theta_t) g[b][m+L-1][t],
  *   g of shape [batch][T][L] (order-major).
  * Same pointer, batch and stream rules as the transforms; no workspace is needed.  For N >= 1
- * plans these return S2GB_EUNSUPPORTED.
+ * plans these return S2GB_EUNSUPPORTED, and so does s2gb_forward_theta for L > 2048 (its ring
+ * chunks need the transforms' workspace).
  */
 int s2gb_inverse_theta(s2gb_plan plan, const void* flm, void* ftilde, int batch, void* stream);
 int s2gb_forward_theta(s2gb_plan plan, const void* g, void* flm, int batch, void* stream);
@@ -152,6 +154,14 @@ int s2gb_forward_theta(s2gb_plan plan, const void* g, void* flm, int batch, void
  */
 #define S2GB_NOALLOC_SCRATCH_BYTES (64u << 20)
 int s2gb_inverse_noalloc(s2gb_plan plan, const void* flm, void* f, int batch, void* stream);
+
+/*
+ * Number of kernel launches of this library (its own kernels; cuFFT's are not counted) issued by
+ * the calling process since the library was loaded, plan-creation kernels included.  A host-side
+ * counter, incremented when a launch is enqueued; thread-safe; never fails.  Instrumentation only:
+ * the paper has no counterpart.
+ */
+unsigned long long s2gb_kernels_launched(void);
 
 /* Static description of a return code (never NULL). */
 const char* s2gb_strerror(int code);

@@ -49,6 +49,8 @@ def lib() -> ctypes.CDLL:
         L.s2gb_plan_destroy.restype = None
         L.s2gb_workspace_bytes.argtypes = [vp, i]
         L.s2gb_workspace_bytes.restype = sz
+        L.s2gb_kernels_launched.argtypes = []
+        L.s2gb_kernels_launched.restype = ctypes.c_ulonglong
         L.s2gb_plan_device_bytes.argtypes = [vp]
         L.s2gb_plan_device_bytes.restype = sz
         for name in ("s2gb_forward", "s2gb_inverse", "s2gb_adjoint_forward", "s2gb_adjoint_inverse"):
@@ -89,6 +91,11 @@ def plan_destroy(plan: int) -> None:
 
 def workspace_bytes(plan: int, batch: int) -> int:
     return int(lib().s2gb_workspace_bytes(ctypes.c_void_p(plan), batch))
+
+
+def kernels_launched() -> int:
+    """Launches of this library's own kernels so far in this process (host-side counter)."""
+    return int(lib().s2gb_kernels_launched())
 
 
 def plan_device_bytes(plan: int) -> int:

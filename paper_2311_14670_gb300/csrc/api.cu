@@ -19,6 +19,7 @@
 // 2N-1 spin-(-n) stages, with per-degree factors 1 (forward) and (2l+1)/(8 pi^2) (inverse).
 // Adjoints (Sec. 5.2): every stage transposed in reverse order; the operator between the two
 // DFT_T calls above is self-adjoint, the theta kernels swap roles.
+#include <atomic>
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
@@ -31,6 +32,14 @@ struct s2gb_plan_s {
 };
 
 namespace s2gb {
+
+static std::atomic<unsigned long long> g_kernel_launches{0};
+
+cudaError_t launched() {
+  g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
+  return cudaGetLastError();
+}
+
 namespace {
 
 struct DeviceGuard {
@@ -52,6 +61,7 @@ struct Workspace {
   char* B;
   char* C;
   void* fft;
+  char* D = nullptr;   // partial results of the chunked forward theta stage (L > kFwdChunk)
 };
 
 Workspace carve(const Plan& p, void* ws, int batch) {
@@ -60,8 +70,11 @@ Workspace carve(const Plan& p, void* ws, int batch) {
   const size_t a = align256(S * p.T * (size_t)(p.Nfft > p.L ? p.Nfft : p.L) * es);
   const size_t b = align256(S * p.T * (size_t)p.T * es);
   const size_t c = align256(p.wigner ? S * p.L * (size_t)p.T * es : 0);
+  const size_t d = align256(p.fwd_parts > 1 ? (size_t)p.fwd_parts * S * p.L * (size_t)p.T * es : 0);
   char* base = reinterpret_cast<char*>(((uintptr_t)ws + 255) & ~(uintptr_t)255);
-  return {base, base + a, base + a + b, base + a + b + c};
+  Workspace w = {base, base + a, base + a + b, base + a + b + c + d};
+  w.D = d ? base + a + b + c : nullptr;
+  return w;
 }
 
 int cuda_rc(cudaError_t e) { return e == cudaSuccess ? S2GB_OK : S2GB_ECUDA; }
@@ -115,6 +128,7 @@ FwdArgs fwd_args(const Plan& p, const void* g, void* flm, int batch, const doubl
   a.g = g; a.flm = flm; a.s_sig = s_sig; a.s_t = s_t; a.s_m = s_m; a.m_mod = m_mod; a.use_nu = use_nu;
   a.nsig = batch; a.nN = p.nN; a.L = p.L; a.coef = p.coef; a.ring = p.ring; a.seed = p.seed;
   a.scale = scale; a.nu = p.nu; a.coef32 = p.coef32; a.v32 = p.v32;
+  a.row0 = 0; a.nrows = p.L; a.part = nullptr; a.part_off = 0;
   return a;
 }
 
@@ -159,6 +173,7 @@ int do_forward(Plan& p, const void* f, void* flm, int batch, const Workspace& w,
   S2GB_TRY(cuda_rc(launch_extend(p, w.A, w.B, S, st)));
   S2GB_TRY(theta_weight_operator(p, fr, w.A, w.B, S));
   FwdArgs a = fwd_args(p, w.B, flm, batch, p.scale_fwd, (long long)p.T * p.T, 1, p.T, 0, 1);
+  a.part = w.D;
   return cuda_rc(launch_theta_forward(p, a, st));
 }
 
@@ -206,6 +221,7 @@ int do_adjoint_inverse(Plan& p, const void* fbar, void* flmbar, int batch, const
   }
   S2GB_TRY(fr.run(p.fft_phi, sig_in, w.A, (size_t)p.nN * plane, CUFFT_FORWARD));
   FwdArgs a = fwd_args(p, w.A, flmbar, batch, p.scale_inv, (long long)plane, p.T, 1, 1, 0);
+  a.part = w.D;
   return cuda_rc(launch_theta_forward(p, a, st));
 }
 
@@ -276,10 +292,10 @@ int s2gb_plan_create(s2gb_plan* out, int L, int spin, int N, int sampling, int p
                      int max_batch, int device) {
   if (!out) return S2GB_EINVAL;
   *out = nullptr;
-  if (L < 1 || L > 4096 || N < 0 || N > L || max_batch < 1 || sampling != S2GB_MW) return S2GB_EINVAL;
+  if (L < 1 || L > 8192 || N < 0 || N > L || max_batch < 1 || sampling != S2GB_MW) return S2GB_EINVAL;
   if (precision != S2GB_FP64 && precision != S2GB_FP32) return S2GB_EINVAL;
   if (N == 0 && (spin <= -L || spin >= L)) return S2GB_EINVAL;
-  if (L > 2048) return S2GB_EUNSUPPORTED;
+  if (precision == S2GB_FP32 && L > 2048) return S2GB_EUNSUPPORTED;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return S2GB_EINVAL;
   s2gb_plan h = new (std::nothrow) s2gb_plan_s;
@@ -347,13 +363,17 @@ int s2gb_inverse_theta(s2gb_plan plan, const void* flm, void* ftilde, int batch,
 int s2gb_forward_theta(s2gb_plan plan, const void* gin, void* flm, int batch, void* stream) {
   if (!plan || !gin || !flm) return S2GB_EINVAL;
   s2gb::Plan& p = plan->p;
-  if (p.wigner) return S2GB_EUNSUPPORTED;
+  if (p.wigner || p.fwd_parts > 1) return S2GB_EUNSUPPORTED;   // L > 2048 needs a workspace
   if (batch < 1 || batch > p.max_batch) return S2GB_EINVAL;
   const size_t es = p.precision == S2GB_FP64 ? 16 : 8;
   if (s2gb::overlaps(gin, flm, (size_t)batch * p.L * p.T * es)) return S2GB_EINVAL;
   s2gb::DeviceGuard g(p.device);
   s2gb::FwdArgs a = s2gb::fwd_args(p, gin, flm, batch, p.scale_fwd, (long long)p.T * p.L, 1, p.L, 0, 0);
   return s2gb::cuda_rc(s2gb::launch_theta_forward(p, a, reinterpret_cast<cudaStream_t>(stream)));
+}
+
+unsigned long long s2gb_kernels_launched(void) {
+  return s2gb::g_kernel_launches.load(std::memory_order_relaxed);
 }
 
 const char* s2gb_strerror(int code) {

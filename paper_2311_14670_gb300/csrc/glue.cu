@@ -165,7 +165,30 @@ __global__ void gamma_reorder_kernel(const C* __restrict__ in, C* __restrict__ o
   }
 }
 
+// out[i] = sum_{p < nparts} parts[p * n + i], in the order of p.
+template <typename C>
+__global__ void sum_parts_kernel(const C* __restrict__ parts, C* __restrict__ out, size_t n, int nparts) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    C acc = parts[i];
+    for (int q = 1; q < nparts; ++q) {
+      const C v = parts[(size_t)q * n + i];
+      acc.x += v.x;
+      acc.y += v.y;
+    }
+    out[i] = acc;
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_sum_parts(const Plan& p, const void* parts, void* out, int nsig, int nparts, cudaStream_t st) {
+  const size_t n = (size_t)nsig * p.nN * p.L * p.T;
+  if (p.precision == S2GB_FP64)
+    sum_parts_kernel<double2><<<grid_for(n), 256, 0, st>>>((const double2*)parts, (double2*)out, n, nparts);
+  else
+    sum_parts_kernel<float2><<<grid_for(n), 256, 0, st>>>((const float2*)parts, (float2*)out, n, nparts);
+  return launched();
+}
 
 cudaError_t launch_extend(const Plan& p, const void* F, void* G, int nsig, cudaStream_t st) {
   const size_t n = (size_t)nsig * p.T * p.T;
@@ -173,7 +196,7 @@ cudaError_t launch_extend(const Plan& p, const void* F, void* G, int nsig, cudaS
     extend_kernel<double2><<<grid_for(n), 256, 0, st>>>((const double2*)F, (double2*)G, nsig, p.L, p.nN, p.n_of);
   else
     extend_kernel<float2><<<grid_for(n), 256, 0, st>>>((const float2*)F, (float2*)G, nsig, p.L, p.nN, p.n_of);
-  return cudaGetLastError();
+  return launched();
 }
 
 cudaError_t launch_extend_adjoint(const Plan& p, const void* G, void* F, int nsig, cudaStream_t st) {
@@ -182,7 +205,7 @@ cudaError_t launch_extend_adjoint(const Plan& p, const void* G, void* F, int nsi
     extend_adjoint_kernel<double2><<<grid_for(n), 256, 0, st>>>((const double2*)G, (double2*)F, nsig, p.L, p.nN, p.n_of);
   else
     extend_adjoint_kernel<float2><<<grid_for(n), 256, 0, st>>>((const float2*)G, (float2*)F, nsig, p.L, p.nN, p.n_of);
-  return cudaGetLastError();
+  return launched();
 }
 
 cudaError_t launch_pad(const Plan& p, const void* X, void* Y, int rows, cudaStream_t st) {
@@ -191,7 +214,7 @@ cudaError_t launch_pad(const Plan& p, const void* X, void* Y, int rows, cudaStre
     pad_kernel<double2><<<grid_for(n), 256, 0, st>>>((const double2*)X, (double2*)Y, (size_t)rows, p.L, p.Nfft);
   else
     pad_kernel<float2><<<grid_for(n), 256, 0, st>>>((const float2*)X, (float2*)Y, (size_t)rows, p.L, p.Nfft);
-  return cudaGetLastError();
+  return launched();
 }
 
 cudaError_t launch_truncate(const Plan& p, const void* Y, void* X, int rows, cudaStream_t st) {
@@ -200,7 +223,7 @@ cudaError_t launch_truncate(const Plan& p, const void* Y, void* X, int rows, cud
     truncate_kernel<double2><<<grid_for(n), 256, 0, st>>>((const double2*)Y, (double2*)X, (size_t)rows, p.L, p.Nfft);
   else
     truncate_kernel<float2><<<grid_for(n), 256, 0, st>>>((const float2*)Y, (float2*)X, (size_t)rows, p.L, p.Nfft);
-  return cudaGetLastError();
+  return launched();
 }
 
 cudaError_t launch_weight_fine(const Plan& p, void* Y, int rows, cudaStream_t st) {
@@ -209,7 +232,7 @@ cudaError_t launch_weight_fine(const Plan& p, void* Y, int rows, cudaStream_t st
     weight_fine_kernel<double2><<<grid_for(n), 256, 0, st>>>((double2*)Y, (size_t)rows, p.Nfft, p.wfine);
   else
     weight_fine_kernel<float2><<<grid_for(n), 256, 0, st>>>((float2*)Y, (size_t)rows, p.Nfft, p.wfine);
-  return cudaGetLastError();
+  return launched();
 }
 
 cudaError_t launch_nu_extend(const Plan& p, void* X, int rows, cudaStream_t st) {
@@ -218,7 +241,7 @@ cudaError_t launch_nu_extend(const Plan& p, void* X, int rows, cudaStream_t st) 
     nu_extend_kernel<double2><<<grid_for(n), 256, 0, st>>>((double2*)X, (size_t)rows, p.L, p.nu);
   else
     nu_extend_kernel<float2><<<grid_for(n), 256, 0, st>>>((float2*)X, (size_t)rows, p.L, p.nu);
-  return cudaGetLastError();
+  return launched();
 }
 
 cudaError_t launch_gamma_reorder(const Plan& p, const void* in, void* out, int batch, int to_signal,
@@ -229,7 +252,7 @@ cudaError_t launch_gamma_reorder(const Plan& p, const void* in, void* out, int b
     gamma_reorder_kernel<double2><<<grid_for(n), 256, 0, st>>>((const double2*)in, (double2*)out, batch, p.N, plane, to_signal, scale);
   else
     gamma_reorder_kernel<float2><<<grid_for(n), 256, 0, st>>>((const float2*)in, (float2*)out, batch, p.N, plane, to_signal, scale);
-  return cudaGetLastError();
+  return launched();
 }
 
 }  // namespace s2gb

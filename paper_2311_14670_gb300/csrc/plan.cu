@@ -235,6 +235,12 @@ int make_plan(Plan* p) {
     ring[t] = r;
   }
 
+  p->cap_n = 0;
+  while (p->cap_n < L && ring[p->cap_n].diff) ++p->cap_n;
+  p->cap_s = L;
+  while (p->cap_s > p->cap_n && ring[p->cap_s - 1].diff) --p->cap_s;
+  p->fwd_parts = (L <= kFwdChunk) ? 1 : 2 + (p->cap_s - p->cap_n + kFwdChunk - 1) / kFwdChunk;
+
   // ---- starting values d^{l0}_{m,n} (Eq. "initial_values" and Sec. 3.3 symmetries) ----
   std::vector<long double> lf2 = log2_factorials(2 * L + 2);
   std::vector<SeedData> seed((size_t)nN * T);
@@ -318,14 +324,14 @@ int make_plan(Plan* p) {
     coefn_kernel<<<1024, 256>>>(p->coef, p->n_of, nN, L);
   else
     coef_kernel<<<1024, 256>>>(p->coef, p->n_of, nN, L);
-  if (cudaGetLastError() != cudaSuccess) return S2GB_ECUDA;
+  if (launched() != cudaSuccess) return S2GB_ECUDA;
   if (cudaDeviceSynchronize() != cudaSuccess) return S2GB_ECUDA;
   if (p->precision == S2GB_FP32) {
     // float32 plans keep the coefficient table rounded once to float, and v per ring
     const size_t n = (size_t)nN * T * L * kCoefPerStep;
     if (cudaMalloc((void**)&p->coef32, n * sizeof(float)) != cudaSuccess) return S2GB_ENOMEM;
     to_float_kernel<<<1024, 256>>>(p->coef, p->coef32, n);
-    if (cudaGetLastError() != cudaSuccess) return S2GB_ECUDA;
+    if (launched() != cudaSuccess) return S2GB_ECUDA;
     if (cudaDeviceSynchronize() != cudaSuccess) return S2GB_ECUDA;
     cudaFree(p->coef);
     p->coef = nullptr;
@@ -389,7 +395,8 @@ size_t workspace_bytes(const Plan& p, int batch) {
   const size_t bufA = S * p.T * (size_t)(p.Nfft > p.L ? p.Nfft : p.L) * es;
   const size_t bufB = S * p.T * (size_t)p.T * es;
   const size_t bufC = p.wigner ? S * p.L * (size_t)p.T * es : 0;
-  return align256(bufA) + align256(bufB) + align256(bufC) + align256(p.fft_work) + 256;
+  const size_t bufD = p.fwd_parts > 1 ? (size_t)p.fwd_parts * S * p.L * (size_t)p.T * es : 0;
+  return align256(bufA) + align256(bufB) + align256(bufC) + align256(bufD) + align256(p.fft_work) + 256;
 }
 
 }  // namespace s2gb

@@ -48,12 +48,16 @@ constexpr int kCoefPerStep = 6;  // A, C, K_north, K_south, Kd_north, Kd_south (
 // A', K_n', K_s', gamma_j, gamma_{j+1}, A'', Kd_n'', Kd_s'', eta_{j+1}, 1/gamma_j
 constexpr int kCoefPerStepN = 10;
 constexpr int kNormBlock = 8;    // normalisation block length (steps), aligned at l0
+constexpr int kFwdChunk = 2048;  // rings per CTA of the forward theta kernel
 
 struct Plan {
   int L = 0, spin = 0, N = 0, precision = 0, max_batch = 0, device = 0;
   int T = 0;        // 2L - 1
   int nN = 1;       // number of n values (1 for the sphere, 2N-1 for Wigner)
   int Nfft = 0;     // length of the fine theta grid of the forward quadrature (>= 4L-3)
+  int cap_n = 0;    // rings [0, cap_n) and [cap_s, L) use the difference form of the recursion
+  int cap_s = 0;
+  int fwd_parts = 1;  // forward theta stage in one launch (L <= 2048) or in ring chunks
   bool wigner = false;
 
   // device tables
@@ -115,7 +119,15 @@ struct FwdArgs {
   const double* nu;
   const float* coef32;  // FP32 plans
   const float* v32;
+  int row0;             // ring range of this launch: [row0, row0 + nrows)
+  int nrows;
+  void* part;           // non-null: write this launch's partial result at part + part_off
+  long long part_off;   // (elements) instead of flm; a fixed-order sum of the parts gives flm
 };
+
+// Every launcher returns launched(): it counts one launch of this library's kernels (a host-side,
+// process-wide counter read by s2gb_kernels_launched) and returns cudaGetLastError().
+cudaError_t launched();
 
 cudaError_t launch_theta_inverse(const Plan& p, const InvArgs& a, cudaStream_t st);
 cudaError_t launch_theta_forward(const Plan& p, const FwdArgs& a, cudaStream_t st);
@@ -129,6 +141,7 @@ cudaError_t launch_pad(const Plan& p, const void* X, void* Y, int rows, cudaStre
 cudaError_t launch_truncate(const Plan& p, const void* Y, void* X, int rows, cudaStream_t st);
 cudaError_t launch_weight_fine(const Plan& p, void* Y, int rows, cudaStream_t st);
 cudaError_t launch_nu_extend(const Plan& p, void* X, int rows, cudaStream_t st);
+cudaError_t launch_sum_parts(const Plan& p, const void* parts, void* out, int nsig, int nparts, cudaStream_t st);
 cudaError_t launch_gamma_reorder(const Plan& p, const void* in, void* out, int batch, int to_signal,
                                  double scale, cudaStream_t st);
 

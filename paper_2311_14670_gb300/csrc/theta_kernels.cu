@@ -268,6 +268,9 @@ __global__ void __launch_bounds__(128) theta_forward_kernel(FwdArgs a) {
   const int nt = blockDim.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int nwarps = nt >> 5;
   const int rows = KT * nt;                // padded ring count
+  const int R = a.nrows, r0 = a.row0;      // this launch's rings: [r0, r0 + R)
+  double2* const outb = a.part ? reinterpret_cast<double2*>(a.part) + a.part_off
+                               : reinterpret_cast<double2*>(a.flm);
   double2* gs = smem;                                          // [NBX][rows]
   double* red = reinterpret_cast<double*>(gs + NBX * rows);   // [2][nwarps][32]
   double* vs = red + 2 * nwarps * 32;                          // [rows]
@@ -287,8 +290,7 @@ __global__ void __launch_bounds__(128) theta_forward_kernel(FwdArgs a) {
   for (int q = tid; q < NBX * lz; q += nt) {
     const int b = q / lz, j = q % lz;
     const Slot sl = slot_of<NB, PAIR>(b, sig0, a.nsig, a.nN, ni, m, n, L);
-    if (sl.sig_off >= 0)
-      reinterpret_cast<double2*>(a.flm)[((size_t)sl.sig_off * L + j) * T + sl.mi] = make_double2(0.0, 0.0);
+    if (sl.sig_off >= 0) outb[((size_t)sl.sig_off * L + j) * T + sl.mi] = make_double2(0.0, 0.0);
   }
   if (l0 >= L) return;
 
@@ -297,7 +299,7 @@ __global__ void __launch_bounds__(128) theta_forward_kernel(FwdArgs a) {
     const int b = q / rows, pos = q % rows;
     const Slot sl = slot_of<NB, PAIR>(b, sig0, a.nsig, a.nN, ni, m, n, L);
     bool act;
-    const int t = ring_of<KT>(pos / nt, pos % nt, nt, L, act);
+    const int t = r0 + ring_of<KT>(pos / nt, pos % nt, nt, R, act);
     double2 g = make_double2(0.0, 0.0);
     if (act && sl.sig_off >= 0) {
       const long long col = a.m_mod ? (sl.m >= 0 ? sl.m : sl.m + T) : sl.mi;
@@ -309,7 +311,7 @@ __global__ void __launch_bounds__(128) theta_forward_kernel(FwdArgs a) {
   }
   for (int pos = tid; pos < rows; pos += nt) {
     bool act;
-    const int t = ring_of<KT>(pos / nt, pos % nt, nt, L, act);
+    const int t = r0 + ring_of<KT>(pos / nt, pos % nt, nt, R, act);
     vs[pos] = act ? a.ring[t].v : 0.0;
   }
   __syncthreads();
@@ -321,7 +323,7 @@ __global__ void __launch_bounds__(128) theta_forward_kernel(FwdArgs a) {
 #pragma unroll
   for (int i = 0; i < KT; ++i) {
     bool act;
-    const int t = ring_of<KT>(i, tid, nt, L, act);
+    const int t = r0 + ring_of<KT>(i, tid, nt, R, act);
     if (act) {
       const RingData rd = a.ring[t];
       seed_value(sd, rd, x[i], E[i]);
@@ -355,7 +357,7 @@ __global__ void __launch_bounds__(128) theta_forward_kernel(FwdArgs a) {
         for (int i = 0; i < KT; ++i) {
           if ((live >> i) & 1u) {
             // partial sums are kept in units of u^j = d^j / gamma_j (rescaled at the output)
-            const bool dslot = (PAT == 1) || i == 0 || i == KT - 1;
+            const bool dslot = (PAT == 1) || (PAT == 0 && (i == 0 || i == KT - 1));
             double xl = (E[i] == 0) ? x[i] : 0.0;
             if (dslot) xl *= c.ig;
             const int pos = i * nt + tid;
@@ -371,14 +373,14 @@ __global__ void __launch_bounds__(128) theta_forward_kernel(FwdArgs a) {
 #pragma unroll
           for (int i = 0; i < KT; ++i) {
             const double v = vs[i * nt + tid];
-            const bool dslot = (PAT == 1) || i == 0 || i == KT - 1;
+            const bool dslot = (PAT == 1) || (PAT == 0 && (i == 0 || i == KT - 1));
             if (dslot) stepn<true>(x[i], y[i], v, nmask[i], north[i], c);
             else stepn<false>(x[i], y[i], v, nmask[i], north[i], c);
           }
           if (((j - l0) & (kNormBlock - 1)) == kNormBlock - 1) {     // end of a normalisation block
 #pragma unroll
             for (int i = 0; i < KT; ++i) {
-              const bool dslot = (PAT == 1) || i == 0 || i == KT - 1;
+              const bool dslot = (PAT == 1) || (PAT == 0 && (i == 0 || i == KT - 1));
               if (dslot) unnormalise<true>(x[i], y[i], c);
               else unnormalise<false>(x[i], y[i], c);
             }
@@ -400,8 +402,7 @@ __global__ void __launch_bounds__(128) theta_forward_kernel(FwdArgs a) {
       const int j = j0 + jr;
       const Slot sl = slot_of<NB, PAIR>(b, sig0, a.nsig, a.nN, ni, m, n, L);
       if (j < L && sl.sig_off >= 0) {
-        double* o = reinterpret_cast<double*>(
-            reinterpret_cast<double2*>(a.flm) + ((size_t)sl.sig_off * L + j) * T + sl.mi);
+        double* o = reinterpret_cast<double*>(outb + ((size_t)sl.sig_off * L + j) * T + sl.mi);
         o[reim] = tot * (scale[j] * coef_m[(size_t)j * kCoefPerStepN + 3]);   // * gamma_j
       }
     }
@@ -415,7 +416,7 @@ cudaError_t launch_inv(const Plan& p, const InvArgs& a, cudaStream_t st) {
   const int ntiles = (p.L + KT * nt - 1) / (KT * nt);
   dim3 grid(p.T * ntiles, PAIR ? (a.nN + 1) / 2 : a.nN, (a.nsig + NB - 1) / NB);
   theta_inverse_kernel<KT, NB, PAIR><<<grid, nt, 0, st>>>(a, ntiles);
-  return cudaGetLastError();
+  return launched();
 }
 
 template <int NB, bool PAIR>
@@ -435,12 +436,17 @@ cudaError_t launch_fwd(const Plan& p, const FwdArgs& a, int nt, cudaStream_t st)
   if (e != cudaSuccess) return e;
   dim3 grid(p.T, PAIR ? (a.nN + 1) / 2 : a.nN, (a.nsig + NB - 1) / NB);
   kern<<<grid, nt, smem, st>>>(a);
-  return cudaGetLastError();
+  return launched();
 }
 
 template <int NB, bool PAIR>
-cudaError_t launch_fwd_nb(const Plan& p, const FwdArgs& a, cudaStream_t st) {
+cudaError_t launch_fwd_nb(const Plan& p, const FwdArgs& a0, cudaStream_t st) {
   const int L = p.L;
+  FwdArgs a = a0;
+  a.row0 = 0;
+  a.nrows = L;
+  a.part = nullptr;
+  a.part_off = 0;
   if (L <= 128) return launch_fwd<1, NB, 1, PAIR>(p, a, ((L + 31) / 32) * 32, st);
   if (L <= 256) return launch_fwd<2, NB, 1, PAIR>(p, a, 128, st);
   if (L <= 512) return launch_fwd<4, NB, 0, PAIR>(p, a, 128, st);
@@ -452,9 +458,31 @@ cudaError_t launch_fwd_nb(const Plan& p, const FwdArgs& a, cudaStream_t st) {
   }
   // KT = 16 slots of nt rings: the polar caps (sin theta < kPoleSin, t < 0.05 L) fit in the
   // first and last slot because nt >= L/16.
-  const int nt = ((L + 16 * 32 - 1) / (16 * 32)) * 32;
-  if (nt > 128) return cudaErrorInvalidConfiguration;  // L > 2048: 128-thread launch bound
-  return launch_fwd<16, NB, 0, PAIR>(p, a, nt, st);
+  if (L <= kFwdChunk) return launch_fwd<16, NB, 0, PAIR>(p, a, ((L + 16 * 32 - 1) / (16 * 32)) * 32, st);
+  // L > kFwdChunk: the rings are split into the two polar caps (difference form throughout) and
+  // interior chunks of at most kFwdChunk rings (plain form); each launch writes a partial result
+  // that a fixed-order sum turns into flm.
+  if (!a0.part) return cudaErrorInvalidValue;
+  const long long part_elems = (long long)a.nsig * a.nN * L * p.T;
+  int q = 0;
+  cudaError_t e;
+  // threads per CTA: KT * nt >= rows and nt <= rows (the last slot holds the last nt rings)
+  auto nt_for = [](int rows, int kt) { return min(128, ((rows + kt - 1) / kt + 31) / 32 * 32); };
+  a.part = a0.part;
+  a.row0 = 0; a.nrows = p.cap_n; a.part_off = part_elems * q++;
+  if ((e = launch_fwd<4, NB, 1, PAIR>(p, a, nt_for(a.nrows, 4), st)) != cudaSuccess) return e;
+  a.row0 = p.cap_s; a.nrows = L - p.cap_s; a.part_off = part_elems * q++;
+  if ((e = launch_fwd<4, NB, 1, PAIR>(p, a, nt_for(a.nrows, 4), st)) != cudaSuccess) return e;
+  const int interior = p.cap_s - p.cap_n;
+  const int nchunk = (interior + kFwdChunk - 1) / kFwdChunk;
+  for (int c = 0; c < nchunk; ++c) {           // chunks of nearly equal size
+    const int lo = p.cap_n + (int)((long long)interior * c / nchunk);
+    const int hi = p.cap_n + (int)((long long)interior * (c + 1) / nchunk);
+    a.row0 = lo; a.nrows = hi - lo; a.part_off = part_elems * q++;
+    if ((e = launch_fwd<16, NB, 2, PAIR>(p, a, nt_for(a.nrows, 16), st)) != cudaSuccess) return e;
+  }
+  if (q != p.fwd_parts) return cudaErrorInvalidValue;
+  return launch_sum_parts(p, a0.part, a0.flm, a.nsig, q, st);
 }
 
 // Pairing (m, n) with (-m, -n) needs the set of n to be symmetric: spin-0 sphere plans and Wigner.

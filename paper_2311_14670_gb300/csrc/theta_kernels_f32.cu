@@ -385,7 +385,7 @@ cudaError_t launch_inv32(const Plan& p, const InvArgs& a, cudaStream_t st) {
   const int ntiles = (p.L + KT * nt - 1) / (KT * nt);
   dim3 grid(p.T * ntiles, a.nN, (a.nsig + NB - 1) / NB);
   theta_inverse_kernel_f32<KT, NB><<<grid, nt, 0, st>>>(a, ntiles);
-  return cudaGetLastError();
+  return launched();
 }
 
 template <int NB>
@@ -404,7 +404,7 @@ cudaError_t launch_fwd32(const Plan& p, const FwdArgs& a, int nt, cudaStream_t s
   if (e != cudaSuccess) return e;
   dim3 grid(p.T, a.nN, (a.nsig + NB - 1) / NB);
   kern<<<grid, nt, smem, st>>>(a);
-  return cudaGetLastError();
+  return launched();
 }
 
 template <int NB>

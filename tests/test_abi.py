@@ -55,3 +55,12 @@ def test_strerror_and_argument_rejection_without_gpu(libpath):
     assert lib.s2gb_workspace_bytes(None, 1) == 0
     assert lib.s2gb_forward(None, None, None, 1, None, 0, None) == nat.S2GB_EINVAL
     lib.s2gb_plan_destroy(None)
+
+
+def test_kernel_launch_counter_starts_at_zero_without_gpu(libpath):
+    from paper_2311_14670_gb300 import _native as nat
+    n = nat.kernels_launched()
+    assert isinstance(n, int) and n >= 0
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        assert n == 0                       # nothing in the CPU suite launches a kernel

@@ -213,3 +213,56 @@ def test_argument_errors():
         nat.inverse(p._h, x, out, 3, ws, ws.numel(), 0)             # batch > max_batch
     assert e.value.code == nat.S2GB_EINVAL
     torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("L,spin", [(2500, 1), (4096, 0)])
+def test_beyond_2048_chunked_forward_and_sampled_parity(L, spin):
+    """L > 2048: the forward theta stage runs in ring chunks (polar caps + interior) summed in a
+    fixed order.  Round trip, plus sampled rings of the inverse against the oracle."""
+    p = plan(L, spin)
+    flm = synth.flm_gaussian(L, spin, 1, seed=L, ell_power=1.0)
+    x = to_gpu(flm)
+    f = p.inverse(x)
+    back = to_np(p.forward(f))
+    assert rel_max(back, flm) <= TOL64
+    rings = [1, L // 2, L - 2]
+    ref = OT.inverse(flm, L, spin, rings=rings)
+    assert rel_max(to_np(f)[:, rings], ref) <= TOL64
+
+
+def test_L2500_forward_sampled_degrees_on_arbitrary_samples():
+    L, spin = 2500, -2
+    p = plan(L, spin)
+    f = synth.signal_gaussian((1, L, 2 * L - 1), seed=77)
+    got = to_np(p.forward(to_gpu(f)))
+    ells = [2, 1000, 2499]
+    ref = OT.forward(f, L, spin, ells=ells)
+    assert rel_max(got[:, ells], ref) <= TOL64
+
+
+def test_L8192_round_trip():
+    L = 8192
+    p = plan(L, 0)
+    flm = synth.flm_gaussian(L, 0, 1, seed=8192, ell_power=1.0)
+    back = to_np(p.forward(p.inverse(to_gpu(flm))))
+    assert rel_max(back, flm) <= TOL64
+
+
+def test_kernel_launch_counter_counts_each_stage():
+    """s2gb_kernels_launched counts this library's own launches: the sphere inverse is one theta
+    kernel (then cuFFT), the forward four glue kernels plus the theta kernel; above L = 2048 the
+    forward theta stage is several ring-chunk launches and one fixed-order sum."""
+    from paper_2311_14670_gb300 import _native as nat
+    p = plan(64, 2)
+    x = to_gpu(synth.flm_gaussian(64, 2, 1, seed=5))
+    k0 = nat.kernels_launched()
+    f = p.inverse(x)
+    k1 = nat.kernels_launched()
+    p.forward(f)
+    k2 = nat.kernels_launched()
+    assert (k1 - k0, k2 - k1) == (1, 5)
+    q = plan(2500, 0)
+    g = q.inverse(to_gpu(synth.flm_gaussian(2500, 0, 1, seed=6)))
+    k3 = nat.kernels_launched()
+    q.forward(g)
+    assert nat.kernels_launched() - k3 >= 4 + 3 + 1     # caps, >= 1 interior chunk, sum

@@ -133,6 +133,34 @@ int s2gb_inverse_theta(s2gb_plan plan, const void* flm, void* ftilde, int batch,
 int s2gb_forward_theta(s2gb_plan plan, const void* g, void* flm, int batch, void* stream);
 
 /*
+ * Order-sharded transforms: one transform split over devices (or over sequential calls) by |m|.
+ * For a fixed order m, flm[.][m] <-> ftilde_m(theta) is a closed subproblem in both directions
+ * (Eqs. disc_ish_expanded and disc_sh_expanded couple degrees and rings, never orders), so a
+ * device that owns the orders with |m| in [m_lo, m_hi) (0 <= m_lo <= m_hi <= L, else S2GB_EINVAL;
+ * m_lo == m_hi is an empty range and launches nothing) computes exactly the values the whole
+ * transform computes for those orders, bit for bit.
+ *
+ * s2gb_inverse_theta_mrange: s2gb_inverse_theta for the orders in range only (sphere plans).
+ *   Columns of ftilde for other orders are not written.
+ * s2gb_inverse_phi: the rest of the sphere inverse transform, ftilde [b][t][m mod T] -> f
+ *   (Eq. disc_ish_fft, a length-T inverse DFT along phi).  Sphere plans (Wigner:
+ *   S2GB_EUNSUPPORTED); workspace as for s2gb_inverse.  s2gb_inverse = s2gb_inverse_theta +
+ *   s2gb_inverse_phi; an order-sharded inverse assembles ftilde from every shard (one exchange of
+ *   16 * batch * L * (2L-1) bytes in FP64) before s2gb_inverse_phi.
+ * s2gb_forward_mrange: s2gb_forward whose theta stage runs for the orders in range only; every
+ *   stage before it (the phi DFT and the theta-direction quadrature operator) runs in full.
+ *   flm entries of other orders are not written.  Any plan (sphere or Wigner); workspace as for
+ *   s2gb_forward.
+ * Same pointer, batch and stream rules as the transforms.
+ */
+int s2gb_inverse_theta_mrange(s2gb_plan plan, const void* flm, void* ftilde, int batch, int m_lo,
+                              int m_hi, void* stream);
+int s2gb_inverse_phi(s2gb_plan plan, const void* ftilde, void* f, int batch, void* ws, size_t ws_bytes,
+                     void* stream);
+int s2gb_forward_mrange(s2gb_plan plan, const void* f, void* flm, int batch, int m_lo, int m_hi,
+                        void* ws, size_t ws_bytes, void* stream);
+
+/*
  * Allocation-free inverse transform.  The paper has no counterpart: this entry point exists for
  * callers that cannot allocate device memory at the point where they run the transform -- code
  * whose memory is owned by another allocator, code running under a strict no-allocation rule

@@ -63,6 +63,12 @@ def lib() -> ctypes.CDLL:
             fn = getattr(L, name)
             fn.argtypes = [vp, vp, vp, i, vp]
             fn.restype = i
+        L.s2gb_inverse_theta_mrange.argtypes = [vp, vp, vp, i, i, i, vp]
+        L.s2gb_inverse_theta_mrange.restype = i
+        L.s2gb_inverse_phi.argtypes = [vp, vp, vp, i, vp, sz, vp]
+        L.s2gb_inverse_phi.restype = i
+        L.s2gb_forward_mrange.argtypes = [vp, vp, vp, i, i, i, vp, sz, vp]
+        L.s2gb_forward_mrange.restype = i
         L.s2gb_strerror.argtypes = [i]
         L.s2gb_strerror.restype = ctypes.c_char_p
         _lib = L
@@ -139,6 +145,25 @@ def forward_theta(plan, g, flm, batch, stream):
     _check(lib().s2gb_forward_theta(ctypes.c_void_p(plan), ctypes.c_void_p(_ptr(g)),
                                     ctypes.c_void_p(_ptr(flm)), batch, ctypes.c_void_p(stream)),
            "s2gb_forward_theta")
+
+
+def inverse_theta_mrange(plan, flm, ftilde, batch, m_lo, m_hi, stream):
+    _check(lib().s2gb_inverse_theta_mrange(ctypes.c_void_p(plan), ctypes.c_void_p(_ptr(flm)),
+                                           ctypes.c_void_p(_ptr(ftilde)), batch, m_lo, m_hi,
+                                           ctypes.c_void_p(stream)),
+           "s2gb_inverse_theta_mrange")
+
+
+def inverse_phi(plan, ftilde, f, batch, ws, ws_bytes, stream):
+    _call("inverse_phi", plan, ftilde, f, batch, ws, ws_bytes, stream)
+
+
+def forward_mrange(plan, f, flm, batch, m_lo, m_hi, ws, ws_bytes, stream):
+    _check(lib().s2gb_forward_mrange(ctypes.c_void_p(plan), ctypes.c_void_p(_ptr(f)),
+                                     ctypes.c_void_p(_ptr(flm)), batch, m_lo, m_hi,
+                                     ctypes.c_void_p(_ptr(ws) if ws is not None else 0), ws_bytes,
+                                     ctypes.c_void_p(stream)),
+           "s2gb_forward_mrange")
 
 
 def inverse_noalloc(plan, flm, f, batch, stream):

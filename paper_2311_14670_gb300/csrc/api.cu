@@ -119,6 +119,7 @@ InvArgs inv_args(const Plan& p, const void* flm, void* out, int batch, const dou
   a.flm = flm; a.out = out; a.s_sig = s_sig; a.s_t = s_t; a.s_m = s_m; a.m_mod = m_mod;
   a.nsig = batch; a.nN = p.nN; a.L = p.L; a.coef = p.coef; a.ring = p.ring; a.seed = p.seed;
   a.scale = scale; a.coef32 = p.coef32; a.v32 = p.v32;
+  a.rank0 = 0; a.nrank = p.T;
   return a;
 }
 
@@ -129,6 +130,7 @@ FwdArgs fwd_args(const Plan& p, const void* g, void* flm, int batch, const doubl
   a.nsig = batch; a.nN = p.nN; a.L = p.L; a.coef = p.coef; a.ring = p.ring; a.seed = p.seed;
   a.scale = scale; a.nu = p.nu; a.coef32 = p.coef32; a.v32 = p.v32;
   a.row0 = 0; a.nrows = p.L; a.part = nullptr; a.part_off = 0;
+  a.rank0 = 0; a.nrank = p.T;
   return a;
 }
 
@@ -149,7 +151,10 @@ int theta_weight_operator(Plan& p, FftRunner& fr, char* A, char* B, int S) {
 
 constexpr double kTwoPi = 6.283185307179586476925286766559;
 
-int do_forward(Plan& p, const void* f, void* flm, int batch, const Workspace& w, cudaStream_t st) {
+// Orders |m| in [mlo, mhi) of the forward transform: every stage before the theta kernel runs in
+// full, the theta kernel only for those orders (flm entries of other orders are not written).
+int do_forward(Plan& p, const void* f, void* flm, int batch, const Workspace& w, cudaStream_t st,
+               int mlo, int mhi) {
   FftRunner fr{p, st, w.fft, batch};
   const int S = batch * p.nN;
   const size_t plane = (size_t)p.L * p.T;
@@ -174,7 +179,14 @@ int do_forward(Plan& p, const void* f, void* flm, int batch, const Workspace& w,
   S2GB_TRY(theta_weight_operator(p, fr, w.A, w.B, S));
   FwdArgs a = fwd_args(p, w.B, flm, batch, p.scale_fwd, (long long)p.T * p.T, 1, p.T, 0, 1);
   a.part = w.D;
+  mrange_ranks(mlo, mhi, a.rank0, a.nrank);
   return cuda_rc(launch_theta_forward(p, a, st));
+}
+
+// Sphere inverse after the theta stage: ring spectra [b][t][m mod T] -> f (Eq. disc_ish_fft).
+int do_inverse_phi(Plan& p, const void* ftilde, void* f, int batch, const Workspace& w, cudaStream_t st) {
+  FftRunner fr{p, st, w.fft, batch};
+  return fr.run(p.fft_phi, ftilde, f, (size_t)p.L * p.T, CUFFT_INVERSE);
 }
 
 int do_inverse(Plan& p, const void* flm, void* f, int batch, const Workspace& w, cudaStream_t st) {
@@ -257,13 +269,16 @@ bool overlaps(const void* a, const void* b, size_t bytes) {
   return x < y + bytes && y < x + bytes;
 }
 
-enum class Op { Forward, Inverse, AdjForward, AdjInverse };
+enum class Op { Forward, Inverse, AdjForward, AdjInverse, InversePhi };
 
 int run(s2gb_plan plan, Op op, const void* in, void* out, int batch, void* ws, size_t ws_bytes,
-        void* stream) {
+        void* stream, int mlo = 0, int mhi = -1) {
   if (!plan || !in || !out) return S2GB_EINVAL;
   Plan& p = plan->p;
   if (batch < 1 || batch > p.max_batch) return S2GB_EINVAL;
+  if (mhi < 0) mhi = p.L;
+  if (mlo < 0 || mlo > mhi || mhi > p.L) return S2GB_EINVAL;
+  if (op == Op::InversePhi && p.wigner) return S2GB_EUNSUPPORTED;
   const size_t es = p.precision == S2GB_FP64 ? 16 : 8;
   const size_t bytes = (size_t)batch * p.nN * p.L * p.T * es;
   if (overlaps(in, out, bytes)) return S2GB_EINVAL;
@@ -273,7 +288,8 @@ int run(s2gb_plan plan, Op op, const void* in, void* out, int batch, void* ws, s
   const Workspace w = carve(p, ws, batch);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   switch (op) {
-    case Op::Forward: return do_forward(p, in, out, batch, w, st);
+    case Op::Forward: return do_forward(p, in, out, batch, w, st, mlo, mhi);
+    case Op::InversePhi: return do_inverse_phi(p, in, out, batch, w, st);
     case Op::Inverse: return do_inverse(p, in, out, batch, w, st);
     case Op::AdjForward: return do_adjoint_forward(p, in, out, batch, w, st);
     case Op::AdjInverse: return do_adjoint_inverse(p, in, out, batch, w, st);
@@ -348,16 +364,33 @@ int s2gb_adjoint_inverse(s2gb_plan plan, const void* f_bar, void* flm_bar, int b
   return s2gb::run(plan, Op::AdjInverse, f_bar, flm_bar, batch, ws, ws_bytes, stream);
 }
 
-int s2gb_inverse_theta(s2gb_plan plan, const void* flm, void* ftilde, int batch, void* stream) {
+int s2gb_inverse_theta_mrange(s2gb_plan plan, const void* flm, void* ftilde, int batch, int m_lo,
+                              int m_hi, void* stream) {
   if (!plan || !flm || !ftilde) return S2GB_EINVAL;
   s2gb::Plan& p = plan->p;
   if (p.wigner) return S2GB_EUNSUPPORTED;
   if (batch < 1 || batch > p.max_batch) return S2GB_EINVAL;
+  if (m_lo < 0 || m_lo > m_hi || m_hi > p.L) return S2GB_EINVAL;
   const size_t es = p.precision == S2GB_FP64 ? 16 : 8;
   if (s2gb::overlaps(flm, ftilde, (size_t)batch * p.L * p.T * es)) return S2GB_EINVAL;
   s2gb::DeviceGuard g(p.device);
   s2gb::InvArgs a = s2gb::inv_args(p, flm, ftilde, batch, p.scale_inv, (long long)p.L * p.T, p.T, 1, 1);
+  s2gb::mrange_ranks(m_lo, m_hi, a.rank0, a.nrank);
   return s2gb::cuda_rc(s2gb::launch_theta_inverse(p, a, reinterpret_cast<cudaStream_t>(stream)));
+}
+
+int s2gb_inverse_theta(s2gb_plan plan, const void* flm, void* ftilde, int batch, void* stream) {
+  return s2gb_inverse_theta_mrange(plan, flm, ftilde, batch, 0, plan ? plan->p.L : 0, stream);
+}
+
+int s2gb_forward_mrange(s2gb_plan plan, const void* f, void* flm, int batch, int m_lo, int m_hi,
+                        void* ws, size_t ws_bytes, void* stream) {
+  return s2gb::run(plan, Op::Forward, f, flm, batch, ws, ws_bytes, stream, m_lo, m_hi);
+}
+
+int s2gb_inverse_phi(s2gb_plan plan, const void* ftilde, void* f, int batch, void* ws, size_t ws_bytes,
+                     void* stream) {
+  return s2gb::run(plan, Op::InversePhi, ftilde, f, batch, ws, ws_bytes, stream);
 }
 
 int s2gb_forward_theta(s2gb_plan plan, const void* gin, void* flm, int batch, void* stream) {

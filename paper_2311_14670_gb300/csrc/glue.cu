@@ -167,8 +167,12 @@ __global__ void gamma_reorder_kernel(const C* __restrict__ in, C* __restrict__ o
 
 // out[i] = sum_{p < nparts} parts[p * n + i], in the order of p.
 template <typename C>
-__global__ void sum_parts_kernel(const C* __restrict__ parts, C* __restrict__ out, size_t n, int nparts) {
+__global__ void sum_parts_kernel(const C* __restrict__ parts, C* __restrict__ out, size_t n, int nparts,
+                                 int L, int mlo, int mhi) {
+  const int T = 2 * L - 1;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const int am = abs((int)(i % T) - (L - 1));
+    if (am < mlo || am >= mhi) continue;
     C acc = parts[i];
     for (int q = 1; q < nparts; ++q) {
       const C v = parts[(size_t)q * n + i];
@@ -181,12 +185,13 @@ __global__ void sum_parts_kernel(const C* __restrict__ parts, C* __restrict__ ou
 
 }  // namespace
 
-cudaError_t launch_sum_parts(const Plan& p, const void* parts, void* out, int nsig, int nparts, cudaStream_t st) {
+cudaError_t launch_sum_parts(const Plan& p, const void* parts, void* out, int nsig, int nparts,
+                             int mlo, int mhi, cudaStream_t st) {
   const size_t n = (size_t)nsig * p.nN * p.L * p.T;
   if (p.precision == S2GB_FP64)
-    sum_parts_kernel<double2><<<grid_for(n), 256, 0, st>>>((const double2*)parts, (double2*)out, n, nparts);
+    sum_parts_kernel<double2><<<grid_for(n), 256, 0, st>>>((const double2*)parts, (double2*)out, n, nparts, p.L, mlo, mhi);
   else
-    sum_parts_kernel<float2><<<grid_for(n), 256, 0, st>>>((const float2*)parts, (float2*)out, n, nparts);
+    sum_parts_kernel<float2><<<grid_for(n), 256, 0, st>>>((const float2*)parts, (float2*)out, n, nparts, p.L, mlo, mhi);
   return launched();
 }
 

@@ -101,6 +101,8 @@ struct InvArgs {
   const double* scale;  // [nN][L]
   const float* coef32;  // FP32 plans
   const float* v32;
+  int rank0;            // orders of this launch: m-ranks [rank0, rank0 + nrank) (m_of_rank order
+  int nrank;            // 0, -1, 1, -2, 2, ...: |m| in [lo, hi) is ranks [max(0, 2lo-1), 2hi-1))
 };
 
 struct FwdArgs {
@@ -123,7 +125,16 @@ struct FwdArgs {
   int nrows;
   void* part;           // non-null: write this launch's partial result at part + part_off
   long long part_off;   // (elements) instead of flm; a fixed-order sum of the parts gives flm
+  int rank0;            // orders of this launch (as in InvArgs)
+  int nrank;
 };
+
+// m-ranks of the orders with |m| in [lo, hi), 0 <= lo <= hi <= L (empty: count 0)
+inline void mrange_ranks(int lo, int hi, int& rank0, int& nrank) {
+  rank0 = lo == 0 ? 0 : 2 * lo - 1;
+  const int end = hi == 0 ? 0 : 2 * hi - 1;
+  nrank = end > rank0 ? end - rank0 : 0;
+}
 
 // Every launcher returns launched(): it counts one launch of this library's kernels (a host-side,
 // process-wide counter read by s2gb_kernels_launched) and returns cudaGetLastError().
@@ -141,7 +152,9 @@ cudaError_t launch_pad(const Plan& p, const void* X, void* Y, int rows, cudaStre
 cudaError_t launch_truncate(const Plan& p, const void* Y, void* X, int rows, cudaStream_t st);
 cudaError_t launch_weight_fine(const Plan& p, void* Y, int rows, cudaStream_t st);
 cudaError_t launch_nu_extend(const Plan& p, void* X, int rows, cudaStream_t st);
-cudaError_t launch_sum_parts(const Plan& p, const void* parts, void* out, int nsig, int nparts, cudaStream_t st);
+// out[i] = sum of the parts in order, for the columns (m + L - 1) of orders with |m| in [mlo, mhi)
+cudaError_t launch_sum_parts(const Plan& p, const void* parts, void* out, int nsig, int nparts,
+                             int mlo, int mhi, cudaStream_t st);
 cudaError_t launch_gamma_reorder(const Plan& p, const void* in, void* out, int batch, int to_signal,
                                  double scale, cudaStream_t st);
 

@@ -220,7 +220,7 @@ __global__ void __launch_bounds__(128) theta_inverse_kernel(InvArgs a, int ntile
   __shared__ double2 hs[kChunk * (PAIR ? 2 * NB : NB)];
   __shared__ double cs[kChunk * kCoefPerStepN];
   const int L = a.L;
-  const int rank = blockIdx.x / ntiles, tile = blockIdx.x % ntiles;
+  const int rank = a.rank0 + (int)(blockIdx.x / ntiles), tile = blockIdx.x % ntiles;
   const int m = m_of_rank(rank);
   const int ni = PAIR ? (a.nN - 1) / 2 + (int)blockIdx.y : (int)blockIdx.y;
   const int n = ni - (a.nN - 1) / 2;          // used only with pairing (n-set symmetric about 0)
@@ -275,7 +275,7 @@ __global__ void __launch_bounds__(128) theta_forward_kernel(FwdArgs a) {
   double* red = reinterpret_cast<double*>(gs + NBX * rows);   // [2][nwarps][32]
   double* vs = red + 2 * nwarps * 32;                          // [rows]
 
-  const int m = m_of_rank(blockIdx.x);
+  const int m = m_of_rank(a.rank0 + (int)blockIdx.x);
   const int mi = m + L - 1;
   const int ni = PAIR ? (a.nN - 1) / 2 + (int)blockIdx.y : (int)blockIdx.y;
   const int n = ni - (a.nN - 1) / 2;          // used only with pairing
@@ -414,7 +414,7 @@ template <int KT, int NB, bool PAIR>
 cudaError_t launch_inv(const Plan& p, const InvArgs& a, cudaStream_t st) {
   const int nt = 128;
   const int ntiles = (p.L + KT * nt - 1) / (KT * nt);
-  dim3 grid(p.T * ntiles, PAIR ? (a.nN + 1) / 2 : a.nN, (a.nsig + NB - 1) / NB);
+  dim3 grid(a.nrank * ntiles, PAIR ? (a.nN + 1) / 2 : a.nN, (a.nsig + NB - 1) / NB);
   theta_inverse_kernel<KT, NB, PAIR><<<grid, nt, 0, st>>>(a, ntiles);
   return launched();
 }
@@ -434,7 +434,7 @@ cudaError_t launch_fwd(const Plan& p, const FwdArgs& a, int nt, cudaStream_t st)
   auto kern = theta_forward_kernel<KT, NB, PAT, PAIR>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  dim3 grid(p.T, PAIR ? (a.nN + 1) / 2 : a.nN, (a.nsig + NB - 1) / NB);
+  dim3 grid(a.nrank, PAIR ? (a.nN + 1) / 2 : a.nN, (a.nsig + NB - 1) / NB);
   kern<<<grid, nt, smem, st>>>(a);
   return launched();
 }
@@ -482,7 +482,9 @@ cudaError_t launch_fwd_nb(const Plan& p, const FwdArgs& a0, cudaStream_t st) {
     if ((e = launch_fwd<16, NB, 2, PAIR>(p, a, nt_for(a.nrows, 16), st)) != cudaSuccess) return e;
   }
   if (q != p.fwd_parts) return cudaErrorInvalidValue;
-  return launch_sum_parts(p, a0.part, a0.flm, a.nsig, q, st);
+  // the orders of this launch: |m| in [(rank0 + 1) / 2, (rank0 + nrank + 1) / 2)
+  return launch_sum_parts(p, a0.part, a0.flm, a.nsig, q, (a.rank0 + 1) / 2,
+                          (a.rank0 + a.nrank + 1) / 2, st);
 }
 
 // Pairing (m, n) with (-m, -n) needs the set of n to be symmetric: spin-0 sphere plans and Wigner.
@@ -491,6 +493,7 @@ bool paired(const Plan& p) { return p.wigner || p.spin == 0; }
 }  // namespace
 
 cudaError_t launch_theta_inverse(const Plan& p, const InvArgs& a, cudaStream_t st) {
+  if (a.nrank <= 0) return cudaSuccess;             // no orders in range: nothing to launch
   if (p.precision == S2GB_FP32) return launch_theta_inverse_f32(p, a, st);
   if (paired(p)) {
     if (a.nsig >= 2) return launch_inv_nb<2, true>(p, a, st);
@@ -502,6 +505,7 @@ cudaError_t launch_theta_inverse(const Plan& p, const InvArgs& a, cudaStream_t s
 }
 
 cudaError_t launch_theta_forward(const Plan& p, const FwdArgs& a, cudaStream_t st) {
+  if (a.nrank <= 0) return cudaSuccess;
   if (p.precision == S2GB_FP32) return launch_theta_forward_f32(p, a, st);
   if (paired(p)) {
     if (a.nsig >= 2 && p.L <= 1024) return launch_fwd_nb<2, true>(p, a, st);

@@ -210,7 +210,7 @@ __global__ void __launch_bounds__(128) theta_inverse_kernel_f32(InvArgs a, int n
   __shared__ float2 hs[kChunk32 * NB];
   __shared__ float cs[kChunk32 * kCoefPerStep];
   const int L = a.L;
-  const int rank = blockIdx.x / ntiles, tile = blockIdx.x % ntiles;
+  const int rank = a.rank0 + (int)(blockIdx.x / ntiles), tile = blockIdx.x % ntiles;
   const int m = m_of_rank(rank);
   const int ni = blockIdx.y;
   const int l0 = a.seed[(size_t)ni * (2 * L - 1) + m + L - 1].l0;
@@ -257,7 +257,7 @@ __global__ void __launch_bounds__(128) theta_forward_kernel_f32(FwdArgs a) {
   float2* gs = reinterpret_cast<float2*>(red + 2 * nwarps * 32);  // [NB][rows]
   float* vs = reinterpret_cast<float*>(gs + NB * rows);           // [rows]
 
-  const int m = m_of_rank(blockIdx.x);
+  const int m = m_of_rank(a.rank0 + (int)blockIdx.x);
   const int mi = m + L - 1;
   const int ni = blockIdx.y;
   const int sig0 = blockIdx.z * NB;
@@ -383,7 +383,7 @@ template <int KT, int NB>
 cudaError_t launch_inv32(const Plan& p, const InvArgs& a, cudaStream_t st) {
   const int nt = 128;
   const int ntiles = (p.L + KT * nt - 1) / (KT * nt);
-  dim3 grid(p.T * ntiles, a.nN, (a.nsig + NB - 1) / NB);
+  dim3 grid(a.nrank * ntiles, a.nN, (a.nsig + NB - 1) / NB);
   theta_inverse_kernel_f32<KT, NB><<<grid, nt, 0, st>>>(a, ntiles);
   return launched();
 }
@@ -402,7 +402,7 @@ cudaError_t launch_fwd32(const Plan& p, const FwdArgs& a, int nt, cudaStream_t s
   auto kern = theta_forward_kernel_f32<KT, NB, PAT>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  dim3 grid(p.T, a.nN, (a.nsig + NB - 1) / NB);
+  dim3 grid(a.nrank, a.nN, (a.nsig + NB - 1) / NB);
   kern<<<grid, nt, smem, st>>>(a);
   return launched();
 }

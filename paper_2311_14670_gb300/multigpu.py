@@ -1,8 +1,14 @@
-"""Host-side logic of multi-GPU runs: one process per GPU, independent work per rank.
+"""Host-side logic of multi-GPU runs: one process per GPU.
 
-Transforms of different signals are independent, so N GPUs shard whole batches (weak scaling)
-with no collective on the data path.  torch.distributed is used only to line the ranks up before
-and after the timed region and to take the maximum of the per-rank times.
+Two ways to split work over ranks:
+  * whole batches (independent signals; weak scaling, no collective on the data path) -- what
+    bench.py times; torch.distributed only lines the ranks up and takes the maximum time;
+  * one transform split by order |m| (Sec. 4.4: for a fixed m the theta stage couples degrees and
+    rings, never orders).  Each rank runs the theta stage for its contiguous range of |m|, chosen
+    so that the number of (l, m) pairs is balanced; the inverse then exchanges the ring spectra
+    (one all-gather) before the phi DFT, the forward gathers the coefficients of every range.
+    Each rank computes, for its orders, the bits the whole transform computes, and the assembly
+    only copies, so the result is bitwise that of the unsharded transform.
 """
 from __future__ import annotations
 
@@ -42,3 +48,92 @@ def max_over_ranks(values, device=None):
 def weak_scaling_throughput(units_per_rank: int, world: int, ms_max: float, steps: int) -> float:
     """Whole-job units per second: every rank's units divided by the slowest rank's time."""
     return units_per_rank * world * steps / (ms_max * 1e-3)
+
+
+# ---------------------------------------------------------------------------- order sharding
+def order_work(L: int, n_abs: int = 0) -> list:
+    """Theta-stage work of each |m| = a: the (l, +-m) pairs with max(a, |n|) <= l < L."""
+    return [max(0, L - max(a, n_abs)) * (1 if a == 0 else 2) for a in range(L)]
+
+
+def order_ranges(L: int, world: int, n_abs: int = 0) -> list:
+    """Contiguous |m| ranges [lo, hi), one per rank, covering [0, L) with balanced work (the cut
+    after the prefix of work closest to k/world of the total).  A rank may get an empty range
+    when world > L."""
+    work = order_work(L, n_abs)
+    total = float(sum(work))
+    cuts = [0]
+    acc, a = 0.0, 0
+    for k in range(1, world):
+        target = total * k / world
+        while a < L and acc + work[a] / 2.0 <= target:
+            acc += work[a]
+            a += 1
+        cuts.append(max(a, cuts[-1]))
+    cuts.append(L)
+    return [(cuts[r], cuts[r + 1]) for r in range(world)]
+
+
+def column_owner(L: int, ranges, layout: str) -> list:
+    """Rank owning each of the T = 2L-1 columns: layout "mod" (column k = m mod T: ring spectra)
+    or "centered" (column m + L - 1: coefficients)."""
+    T = 2 * L - 1
+    owner = [-1] * T
+    for r, (lo, hi) in enumerate(ranges):
+        for a in range(lo, hi):
+            for m in ((0,) if a == 0 else (a, -a)):
+                owner[(m % T) if layout == "mod" else m + L - 1] = r
+    if min(owner) < 0:
+        raise ValueError("the ranges do not cover every order")
+    return owner
+
+
+def assemble_columns(parts, owner):
+    """Copy every column (last axis) from the rank that owns it: out[..., k] = parts[owner[k]][..., k]."""
+    import torch
+
+    own = torch.as_tensor(owner, device=parts[0].device)
+    out = parts[0].clone()
+    for r in range(1, len(parts)):
+        sel = (own == r).nonzero().flatten()
+        if sel.numel():
+            out.index_copy_(-1, sel, parts[r].index_select(-1, sel))
+    return out
+
+
+def all_gather_fn(group=None):
+    """x -> [x of rank 0, ..., x of rank W-1] through torch.distributed (complex tensors go as
+    their real views)."""
+    import torch
+    import torch.distributed as dist
+
+    def gather(x):
+        xr = torch.view_as_real(x) if x.is_complex() else x
+        bufs = [torch.empty_like(xr) for _ in range(dist.get_world_size(group))]
+        dist.all_gather(bufs, xr.contiguous(), group=group)
+        return [torch.view_as_complex(b) if x.is_complex() else b for b in bufs]
+
+    return gather
+
+
+def sharded_inverse(plan, flm, ranges, rank: int, gather):
+    """Inverse transform split by order: the theta stage of this rank's |m| range, the exchange
+    of ring spectra, then the phi stage (every rank ends with the whole f)."""
+    import torch
+
+    lo, hi = ranges[rank]
+    ft = torch.zeros(tuple(flm.shape), dtype=flm.dtype, device=flm.device)
+    plan.inverse_theta_mrange(flm, lo, hi, out=ft)
+    ft = assemble_columns(gather(ft), column_owner(plan.L, ranges, "mod"))
+    return plan.inverse_phi(ft)
+
+
+def sharded_forward(plan, f, ranges, rank: int, gather):
+    """Forward transform split by order: this rank's |m| range of the theta stage, then the
+    coefficients of every range gathered (every rank ends with the whole flm)."""
+    import torch
+
+    lo, hi = ranges[rank]
+    flm = torch.zeros(tuple(f.shape), dtype=f.dtype, device=f.device)
+    plan.forward_mrange(f, lo, hi, out=flm)
+    return assemble_columns(gather(flm), column_owner(plan.L, ranges, "centered"))

@@ -108,9 +108,34 @@ class Plan:
 
     def inverse_theta(self, flm, out=None):
         """Theta stage of the inverse alone (s2gb_inverse_theta): ftilde[b][t][m mod T]."""
+        return self.inverse_theta_mrange(flm, 0, self.L, out=out)
+
+    def inverse_theta_mrange(self, flm, m_lo: int, m_hi: int, out=None):
+        """Theta stage of the inverse for the orders with |m| in [m_lo, m_hi)
+        (s2gb_inverse_theta_mrange); columns of other orders in ``out`` are left as they are."""
         batch = self._check(flm, "flm")
-        out = torch.empty(self.shape(batch), dtype=self.dtype, device=self.device) if out is None else out
-        nat.inverse_theta(self._h, flm, out, batch, self._stream())
+        if out is None:
+            out = torch.empty(self.shape(batch), dtype=self.dtype, device=self.device)
+        elif self._check(out, "out") != batch:
+            raise ValueError("out must have the batch size of flm")
+        nat.inverse_theta_mrange(self._h, flm, out, batch, int(m_lo), int(m_hi), self._stream())
+        return out
+
+    def inverse_phi(self, ftilde, out=None, ws=None):
+        """The phi stage of the sphere inverse: ftilde[b][t][m mod T] -> f (s2gb_inverse_phi)."""
+        return self._run("inverse_phi", ftilde, out, ws)
+
+    def forward_mrange(self, f, m_lo: int, m_hi: int, out=None, ws=None):
+        """Forward transform whose theta stage covers the orders with |m| in [m_lo, m_hi) only
+        (s2gb_forward_mrange); flm entries of other orders in ``out`` are left as they are."""
+        batch = self._check(f, "f")
+        if out is None:
+            out = torch.empty(self.shape(batch), dtype=self.dtype, device=self.device)
+        elif self._check(out, "out") != batch:
+            raise ValueError("out must have the batch size of f")
+        if ws is None:
+            ws = self.workspace(batch)
+        nat.forward_mrange(self._h, f, out, batch, int(m_lo), int(m_hi), ws, ws.numel(), self._stream())
         return out
 
     def forward_theta(self, g, out=None):

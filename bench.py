@@ -42,10 +42,15 @@ WORKLOADS = {
     "l4096s0b1": (4096, 0, 0, 1, 0.0, "spin-0 SHT round trip, L=4096, MW 4096x8191, batch 1, FP64"),
     "l8192s0b1": (8192, 0, 0, 1, 0.0, "spin-0 SHT round trip, L=8192, MW 8192x16383, batch 1, FP64"),
     "wigner256n8": (256, 0, 8, 1, 0.0, "Wigner round trip, L=256, N=8, MW 256x511x15, batch 1, FP64"),
+    "l2048realb1": (2048, 0, 0, 1, 0.0, "real-signal SHT round trip (orders m >= 0), L=2048, MW 2048x4095, "
+                    "batch 1, FP64"),
+    "l1024realb4": (1024, 0, 0, 4, 1.0, "real-signal SHT round trip (orders m >= 0), L=1024, MW 1024x2047, "
+                    "batch 4, FP64"),
     "l2048s0b16f32grad": (2048, 0, 0, 16, 1.0, "differentiable FP32 SHT, L=2048, spin 0, batch 16: "
                           "loss = sum |inverse(flm) - target|^2 and its gradient via the adjoint"),
 }
 PRECISION = {"l2048s0b16f32grad": "fp32"}
+REAL = {"l2048realb1", "l1024realb4"}
 GRAD = {"l2048s0b16f32grad"}
 METRIC = "transforms/sec"
 FP64_LANES_PER_SM_CLK = 2      # DFMA lanes per SM per clock on GB300 (measured 1.88-1.89 at load)
@@ -80,10 +85,11 @@ def profiled_traffic(workload: str, kernel: str):
     return rec.get("dram_bytes_per_launch", {}).get(kernel)
 
 
-def algorithmic_flops(L: int, n_list, R: int, batch: int) -> float:
-    """Per launch of one theta kernel: elements (l, m, theta) x (5 + 4B) flops (FMA = 2)."""
-    elems = sum(L * L - n * n for n in n_list) * R
-    return float(elems) * (5 + 4 * batch)
+def algorithmic_flops(L: int, n_list, R: int, batch: int, real: bool = False) -> float:
+    """Per launch of one theta kernel: elements (l, m, theta) x (5 + 4B) flops (FMA = 2); real
+    signals have the orders m >= 0 only, L (L + 1) / 2 pairs (l, m)."""
+    pairs = L * (L + 1) // 2 if real else sum(L * L - n * n for n in n_list)
+    return float(pairs * R) * (5 + 4 * batch)
 
 
 class ClockSampler:
@@ -163,17 +169,21 @@ def run_ours(args, world, rank, local):
     L, spin, N, B, ellp, desc = WORKLOADS[args.workload]
     precision = PRECISION.get(args.workload, "fp64")
     grad_mode = args.workload in GRAD
-    plan = Plan(L, spin=spin, N=N, max_batch=B, device=local, precision=precision)
+    real = args.workload in REAL
+    plan = Plan(L, spin=spin, N=N, max_batch=B, device=local, precision=precision, real=real)
     cdt = plan.dtype
     from paper_2311_14670_gb300.multigpu import max_over_ranks, rank_seed, weak_scaling_throughput
     if N:
         coef = synth.flmn_gaussian(L, N, B, seed=rank_seed(3, rank))
         n_list = list(range(-(N - 1), N))
+    elif real:
+        coef = synth.flm_real_gaussian(L, B, seed=rank_seed(2, rank), ell_power=ellp)
+        n_list = [0]
     else:
         coef = synth.flm_gaussian(L, spin, B, seed=rank_seed(2, rank), ell_power=0.0 if grad_mode else ellp)
         n_list = [-spin]
     x = torch.from_numpy(coef).to(dev).to(cdt)
-    f = torch.empty(plan.shape(B), dtype=cdt, device=dev)
+    f = torch.empty(plan.shape(B), dtype=plan.signal_dtype, device=dev)
     y = torch.empty_like(x)
     ws = plan.workspace(B)
     stream = torch.cuda.current_stream(dev)
@@ -245,9 +255,9 @@ def run_ours(args, world, rank, local):
     # the theta-stage kernels alone, on the launch stream, same workload
     kern = {}
     if not N:
-        g = torch.from_numpy(synth.signal_gaussian((B, 2 * L - 1, L), seed=77)).to(dev).to(cdt)
-        ft = torch.empty(plan.shape(B), dtype=cdt, device=dev)
-        fl = torch.empty(plan.shape(B), dtype=cdt, device=dev)
+        g = torch.from_numpy(synth.signal_gaussian((B, L if real else 2 * L - 1, L), seed=77)).to(dev).to(cdt)
+        ft = torch.empty(plan.coef_shape(B), dtype=cdt, device=dev)
+        fl = torch.empty(plan.coef_shape(B), dtype=cdt, device=dev)
         xd_ = x.detach()
         stages = [("theta_inverse", lambda: plan.inverse_theta(xd_, out=ft))]
         if L <= 2048:    # above, the forward theta stage runs in ring chunks inside forward() only
@@ -263,7 +273,7 @@ def run_ours(args, world, rank, local):
             b.record(stream)
             torch.cuda.synchronize(dev)
             kms = a.elapsed_time(b) / reps
-            flops = algorithmic_flops(L, n_list, L, B)
+            flops = algorithmic_flops(L, n_list, L, B, real)
             kern[name] = {"ms": kms, "flops": flops, "tflops": flops / (kms * 1e-3) / 1e12}
 
     ms, ms_e2e = max_over_ranks([ms, ms_e2e], device=dev)

@@ -87,6 +87,23 @@ enum {
 int s2gb_plan_create(s2gb_plan* out, int L, int spin, int N, int sampling, int precision,
                      int max_batch, int device);
 
+/*
+ * Plan for real signals (spin 0 sphere transforms of real-valued f), whose coefficients obey the
+ * Hermitian symmetry flm(l, -m) = (-1)^m conj(flm(l, m)) (Sec. 2.2).  Only the orders m >= 0 are
+ * stored and computed:
+ *   f   real (double / float) [batch][L][2L-1],
+ *   flm complex [batch][L][L], flm[b][l][m] for 0 <= m < L (entries m > l ignored / written 0);
+ *       the imaginary parts of flm[b][l][0] are ignored (they are 0 for a real signal).
+ * s2gb_forward / s2gb_inverse / the adjoints / the order-range calls take these layouts; the
+ * adjoints are with respect to the real inner product Re sum conj(x) y (PyTorch's convention for
+ * gradients of real losses).  The theta stages alone use ring spectra [batch][L][L] (column m) and
+ * forward-theta input g [batch][L (m)][L (t)].  The theta recursion runs for m >= 0 only and the
+ * phi DFTs are real-to-complex / complex-to-real, so a real transform costs about half a complex
+ * one.  Arguments as in s2gb_plan_create (spin 0, N = 0 implied).  s2gb_inverse_noalloc refuses
+ * real plans (S2GB_EUNSUPPORTED).
+ */
+int s2gb_plan_create_real(s2gb_plan* out, int L, int sampling, int precision, int max_batch, int device);
+
 /* Free a plan and everything it holds (NULL is ignored).  No call on it may be in flight. */
 void s2gb_plan_destroy(s2gb_plan plan);
 

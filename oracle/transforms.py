@@ -186,6 +186,50 @@ def adjoint_forward(flm_bar: np.ndarray, L: int, spin: int) -> np.ndarray:
     return Fbar @ phi_dft_matrix(L, -1).conj().T                            # phi-DFT^H
 
 
+# ----------------------------------------------------------------------------- real signals (Sec. 2.2)
+# A real spin-0 signal has Hermitian coefficients flm_{l,-m} = (-1)^m conj(flm_{lm}) (Sec. 2.2), so
+# the orders m >= 0 carry everything: flm_pos[..., l, m] for 0 <= m < L.  The real transforms are
+# the complex ones restricted to such signals; as maps between real vector spaces their adjoints
+# are taken with respect to the real inner product Re sum conj(x) y.
+def hermitian_expand(flm_pos: np.ndarray, L: int) -> np.ndarray:
+    """Full coefficients [..., l, m+L-1] from the orders m >= 0 (the real part of m = 0 is used)."""
+    flm_pos = np.asarray(flm_pos, dtype=np.complex128)
+    out = np.zeros(flm_pos.shape[:-1] + (2 * L - 1,), dtype=np.complex128)
+    m = np.arange(1, L)
+    out[..., L - 1] = flm_pos[..., 0].real
+    out[..., L - 1 + m] = flm_pos[..., m]
+    out[..., L - 1 - m] = ((-1.0) ** m) * np.conj(flm_pos[..., m])
+    return np.where(coeff_mask(L, 0), out, 0)
+
+
+def inverse_real(flm_pos: np.ndarray, L: int) -> np.ndarray:
+    """Real signal f[..., t, p] with coefficients hermitian_expand(flm_pos)."""
+    return inverse(hermitian_expand(flm_pos, L), L, 0).real
+
+
+def forward_real(f: np.ndarray, L: int) -> np.ndarray:
+    """Orders m >= 0 of the coefficients of a real signal: flm_pos[..., l, m]."""
+    return forward(np.asarray(f, dtype=np.float64).astype(np.complex128), L, 0)[..., L - 1:]
+
+
+def adjoint_inverse_real(fbar: np.ndarray, L: int) -> np.ndarray:
+    """Adjoint of inverse_real: the adjoint of hermitian_expand applied to adjoint_inverse."""
+    w = adjoint_inverse(np.asarray(fbar, dtype=np.float64).astype(np.complex128), L, 0)
+    m = np.arange(1, L)
+    out = np.zeros(w.shape[:-1] + (L,), dtype=np.complex128)
+    out[..., 0] = w[..., L - 1].real
+    out[..., m] = w[..., L - 1 + m] + ((-1.0) ** m) * np.conj(w[..., L - 1 - m])
+    return np.where(coeff_mask(L, 0)[:, L - 1:], out, 0)
+
+
+def adjoint_forward_real(flm_bar_pos: np.ndarray, L: int) -> np.ndarray:
+    """Adjoint of forward_real: the real part of adjoint_forward of the zero-padded orders."""
+    flm_bar_pos = np.asarray(flm_bar_pos, dtype=np.complex128)
+    full = np.zeros(flm_bar_pos.shape[:-1] + (2 * L - 1,), dtype=np.complex128)
+    full[..., L - 1:] = flm_bar_pos
+    return adjoint_forward(full, L, 0).real
+
+
 # ----------------------------------------------------------------------------- Wigner (Sec. 2.3, 4.5)
 def _gamma_matrix(N: int, sign: int) -> np.ndarray:
     """E[k, j] = exp(sign i n_j gamma_k), n_j = j-(N-1), gamma_k = 2 pi k/(2N-1)."""

@@ -45,6 +45,8 @@ def lib() -> ctypes.CDLL:
         vp, i, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
         L.s2gb_plan_create.argtypes = [ctypes.POINTER(vp), i, i, i, i, i, i, i]
         L.s2gb_plan_create.restype = i
+        L.s2gb_plan_create_real.argtypes = [ctypes.POINTER(vp), i, i, i, i, i]
+        L.s2gb_plan_create_real.restype = i
         L.s2gb_plan_destroy.argtypes = [vp]
         L.s2gb_plan_destroy.restype = None
         L.s2gb_workspace_bytes.argtypes = [vp, i]
@@ -88,6 +90,13 @@ def plan_create(L: int, spin: int, N: int, sampling: int, precision: int, max_ba
     h = ctypes.c_void_p()
     _check(lib().s2gb_plan_create(ctypes.byref(h), L, spin, N, sampling, precision, max_batch, device),
            "s2gb_plan_create")
+    return h.value
+
+
+def plan_create_real(L: int, sampling: int, precision: int, max_batch: int, device: int) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().s2gb_plan_create_real(ctypes.byref(h), L, sampling, precision, max_batch, device),
+           "s2gb_plan_create_real")
     return h.value
 
 

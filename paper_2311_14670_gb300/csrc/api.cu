@@ -67,10 +67,10 @@ struct Workspace {
 Workspace carve(const Plan& p, void* ws, int batch) {
   const size_t es = p.precision == S2GB_FP64 ? 16 : 8;
   const size_t S = (size_t)batch * p.nN;
-  const size_t a = align256(S * p.T * (size_t)(p.Nfft > p.L ? p.Nfft : p.L) * es);
-  const size_t b = align256(S * p.T * (size_t)p.T * es);
+  const size_t a = align256(S * p.MR * (size_t)(p.Nfft > p.L ? p.Nfft : p.L) * es);
+  const size_t b = align256(S * p.MR * (size_t)p.T * es);
   const size_t c = align256(p.wigner ? S * p.L * (size_t)p.T * es : 0);
-  const size_t d = align256(p.fwd_parts > 1 ? (size_t)p.fwd_parts * S * p.L * (size_t)p.T * es : 0);
+  const size_t d = align256(p.fwd_parts > 1 ? (size_t)p.fwd_parts * S * p.L * (size_t)p.MR * es : 0);
   char* base = reinterpret_cast<char*>(((uintptr_t)ws + 255) & ~(uintptr_t)255);
   Workspace w = {base, base + a, base + a + b, base + a + b + c + d};
   w.D = d ? base + a + b + c : nullptr;
@@ -105,6 +105,30 @@ struct FftRunner {
     }
     return S2GB_OK;
   }
+  // Real-signal plans: rings of T real samples -> orders 0..L-1 (dir > 0) or back (dir < 0);
+  // in_elems / out_elems are one signal's element counts (real or complex as the direction says).
+  int run_real(cufftHandle* hs, const void* in, void* out, size_t in_elems, size_t out_elems, int dir) {
+    const bool whole = (batch == p.max_batch);
+    cufftHandle h = hs[whole ? 1 : 0];
+    if (cufftSetStream(h, st) != CUFFT_SUCCESS) return S2GB_ECUFFT;
+    if (cufftSetWorkArea(h, work) != CUFFT_SUCCESS) return S2GB_ECUFFT;
+    const int reps = whole ? 1 : batch;
+    const size_t rs = p.precision == S2GB_FP64 ? 8 : 4;       // bytes of one real
+    const size_t ies = dir > 0 ? rs : 2 * rs, oes = dir > 0 ? 2 * rs : rs;
+    for (int r = 0; r < reps; ++r) {
+      const char* i = reinterpret_cast<const char*>(in) + r * in_elems * ies;
+      char* o = reinterpret_cast<char*>(out) + r * out_elems * oes;
+      cufftResult res;
+      if (p.precision == S2GB_FP64)
+        res = dir > 0 ? cufftExecD2Z(h, (cufftDoubleReal*)i, (cufftDoubleComplex*)o)
+                      : cufftExecZ2D(h, (cufftDoubleComplex*)i, (cufftDoubleReal*)o);
+      else
+        res = dir > 0 ? cufftExecR2C(h, (cufftReal*)i, (cufftComplex*)o)
+                      : cufftExecC2R(h, (cufftComplex*)i, (cufftReal*)o);
+      if (res != CUFFT_SUCCESS) return S2GB_ECUFFT;
+    }
+    return S2GB_OK;
+  }
 };
 
 #define S2GB_TRY(expr)            \
@@ -119,8 +143,20 @@ InvArgs inv_args(const Plan& p, const void* flm, void* out, int batch, const dou
   a.flm = flm; a.out = out; a.s_sig = s_sig; a.s_t = s_t; a.s_m = s_m; a.m_mod = m_mod;
   a.nsig = batch; a.nN = p.nN; a.L = p.L; a.coef = p.coef; a.ring = p.ring; a.seed = p.seed;
   a.scale = scale; a.coef32 = p.coef32; a.v32 = p.v32;
-  a.rank0 = 0; a.nrank = p.T;
+  a.rank0 = 0; a.nrank = p.MR;
+  a.mpos = p.real ? 1 : 0; a.flm_ld = p.MR; a.flm_c0 = p.real ? 0 : p.L - 1;
   return a;
+}
+
+// CTAs of the orders |m| in [lo, hi): m-ranks of the 0, -1, 1, ... order, or m itself for
+// real-signal plans (m >= 0 only).
+void order_ranks(const Plan& p, int lo, int hi, int& rank0, int& nrank) {
+  if (p.real) {
+    rank0 = lo;
+    nrank = hi > lo ? hi - lo : 0;
+  } else {
+    mrange_ranks(lo, hi, rank0, nrank);
+  }
 }
 
 FwdArgs fwd_args(const Plan& p, const void* g, void* flm, int batch, const double* scale,
@@ -130,14 +166,15 @@ FwdArgs fwd_args(const Plan& p, const void* g, void* flm, int batch, const doubl
   a.nsig = batch; a.nN = p.nN; a.L = p.L; a.coef = p.coef; a.ring = p.ring; a.seed = p.seed;
   a.scale = scale; a.nu = p.nu; a.coef32 = p.coef32; a.v32 = p.v32;
   a.row0 = 0; a.nrows = p.L; a.part = nullptr; a.part_off = 0;
-  a.rank0 = 0; a.nrank = p.T;
+  a.rank0 = 0; a.nrank = p.MR;
+  a.mpos = p.real ? 1 : 0; a.flm_ld = p.MR; a.flm_c0 = p.real ? 0 : p.L - 1;
   return a;
 }
 
 // G (rows of length T, S*T rows, in B) -> H in B, using A as the fine-grid buffer.
 int theta_weight_operator(Plan& p, FftRunner& fr, char* A, char* B, int S) {
-  const size_t rows_item = (size_t)p.nN * p.T;
-  const int rows = S * p.T;
+  const size_t rows_item = (size_t)p.nN * p.MR;
+  const int rows = S * p.MR;
   cudaStream_t st = fr.st;
   S2GB_TRY(fr.run(p.fft_T, B, B, rows_item * p.T, CUFFT_FORWARD));
   S2GB_TRY(cuda_rc(launch_pad(p, B, A, rows, st)));
@@ -179,7 +216,7 @@ int do_forward(Plan& p, const void* f, void* flm, int batch, const Workspace& w,
   S2GB_TRY(theta_weight_operator(p, fr, w.A, w.B, S));
   FwdArgs a = fwd_args(p, w.B, flm, batch, p.scale_fwd, (long long)p.T * p.T, 1, p.T, 0, 1);
   a.part = w.D;
-  mrange_ranks(mlo, mhi, a.rank0, a.nrank);
+  order_ranks(p, mlo, mhi, a.rank0, a.nrank);
   return cuda_rc(launch_theta_forward(p, a, st));
 }
 
@@ -264,10 +301,71 @@ int do_adjoint_forward(Plan& p, const void* flmbar, void* fbar, int batch, const
   return S2GB_OK;
 }
 
-bool overlaps(const void* a, const void* b, size_t bytes) {
-  const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
-  return x < y + bytes && y < x + bytes;
+// ---- real signals (spin 0, Sec. 2.2 Hermitian symmetry flm(l, -m) = (-1)^m conj(flm(l, m))) ----
+// f real [b][L][T]; flm [b][L][L] holds the orders m = 0..L-1; ring spectra [b][t][m] with L
+// columns.  Every stage runs on the orders m >= 0 only; the phi DFTs are real-to-complex and
+// complex-to-real (the C2R sum is Re X_0 + 2 Re sum_{m>=1} X_m e^{i m phi}).
+
+int do_forward_real(Plan& p, const void* f, void* flm, int batch, const Workspace& w, cudaStream_t st,
+                    int mlo, int mhi) {
+  FftRunner fr{p, st, w.fft, batch};
+  const size_t L = p.L, T = p.T;
+  S2GB_TRY(fr.run_real(p.fft_phi, f, w.A, L * T, L * L, +1));
+  S2GB_TRY(cuda_rc(launch_extend(p, w.A, w.B, batch, st)));
+  S2GB_TRY(theta_weight_operator(p, fr, w.A, w.B, batch));
+  FwdArgs a = fwd_args(p, w.B, flm, batch, p.scale_fwd, (long long)(L * T), 1, (long long)T, 1, 1);
+  a.part = w.D;
+  order_ranks(p, mlo, mhi, a.rank0, a.nrank);
+  return cuda_rc(launch_theta_forward(p, a, st));
 }
+
+int do_inverse_real(Plan& p, const void* flm, void* f, int batch, const Workspace& w, cudaStream_t st) {
+  FftRunner fr{p, st, w.fft, batch};
+  const size_t L = p.L, T = p.T;
+  InvArgs a = inv_args(p, flm, w.A, batch, p.scale_inv, (long long)(L * L), (long long)L, 1, 1);
+  S2GB_TRY(cuda_rc(launch_theta_inverse(p, a, st)));
+  return fr.run_real(p.fft_phi_c2r, w.A, f, L * L, L * T, -1);
+}
+
+// Adjoint (real inner product) of f = C2R(theta(flm)): R2C, columns m >= 1 doubled, then the
+// forward-shaped theta contraction without weights.
+int do_adjoint_inverse_real(Plan& p, const void* fbar, void* flmbar, int batch, const Workspace& w,
+                            cudaStream_t st) {
+  FftRunner fr{p, st, w.fft, batch};
+  const size_t L = p.L, T = p.T;
+  S2GB_TRY(fr.run_real(p.fft_phi, fbar, w.A, L * T, L * L, +1));
+  S2GB_TRY(cuda_rc(launch_scale_nonzero_orders(p, w.A, (size_t)batch * L, 2.0, st)));
+  FwdArgs a = fwd_args(p, w.A, flmbar, batch, p.scale_inv, (long long)(L * L), (long long)L, 1, 1, 0);
+  a.part = w.D;
+  return cuda_rc(launch_theta_forward(p, a, st));
+}
+
+// Adjoint of the real forward: the complex adjoint's stages on the orders m >= 0, then the
+// adjoint of R2C, which is C2R of the spectrum with columns m >= 1 halved (and Im X_0 dropped).
+int do_adjoint_forward_real(Plan& p, const void* flmbar, void* fbar, int batch, const Workspace& w,
+                            cudaStream_t st) {
+  FftRunner fr{p, st, w.fft, batch};
+  const size_t L = p.L, T = p.T;
+  InvArgs a = inv_args(p, flmbar, w.B, batch, p.scale_fwd, (long long)(L * T), 1, (long long)T, 1);
+  S2GB_TRY(cuda_rc(launch_theta_inverse(p, a, st)));
+  S2GB_TRY(cuda_rc(launch_nu_extend(p, w.B, batch * p.MR, st)));
+  S2GB_TRY(theta_weight_operator(p, fr, w.A, w.B, batch));
+  S2GB_TRY(cuda_rc(launch_extend_adjoint(p, w.B, w.A, batch, st)));
+  S2GB_TRY(cuda_rc(launch_scale_nonzero_orders(p, w.A, (size_t)batch * L, 0.5, st)));
+  return fr.run_real(p.fft_phi_c2r, w.A, fbar, L * L, L * T, -1);
+}
+
+int do_inverse_phi_real(Plan& p, const void* ftilde, void* f, int batch, const Workspace& w, cudaStream_t st) {
+  FftRunner fr{p, st, w.fft, batch};
+  return fr.run_real(p.fft_phi_c2r, ftilde, f, (size_t)p.L * p.L, (size_t)p.L * p.T, -1);
+}
+
+bool overlaps(const void* a, size_t abytes, const void* b, size_t bbytes) {
+  const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+  return x < y + bbytes && y < x + abytes;
+}
+
+bool overlaps(const void* a, const void* b, size_t bytes) { return overlaps(a, bytes, b, bytes); }
 
 enum class Op { Forward, Inverse, AdjForward, AdjInverse, InversePhi };
 
@@ -280,13 +378,27 @@ int run(s2gb_plan plan, Op op, const void* in, void* out, int batch, void* ws, s
   if (mlo < 0 || mlo > mhi || mhi > p.L) return S2GB_EINVAL;
   if (op == Op::InversePhi && p.wigner) return S2GB_EUNSUPPORTED;
   const size_t es = p.precision == S2GB_FP64 ? 16 : 8;
-  const size_t bytes = (size_t)batch * p.nN * p.L * p.T * es;
-  if (overlaps(in, out, bytes)) return S2GB_EINVAL;
+  // element counts of the signal side and of the coefficient (or spectrum) side
+  const size_t sig_bytes = (size_t)batch * p.nN * p.L * p.T * (p.real ? es / 2 : es);
+  const size_t coef_bytes = (size_t)batch * p.nN * p.L * p.MR * es;
+  const bool in_is_signal = (op == Op::Forward || op == Op::AdjInverse);
+  if (overlaps(in, in_is_signal ? sig_bytes : coef_bytes, out, in_is_signal ? coef_bytes : sig_bytes))
+    return S2GB_EINVAL;
   if (!ws || ws_bytes < workspace_bytes(p, batch)) return S2GB_EWORKSPACE;
   DeviceGuard g(p.device);
   std::lock_guard<std::mutex> lock(p.fft_mutex);
   const Workspace w = carve(p, ws, batch);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (p.real) {
+    switch (op) {
+      case Op::Forward: return do_forward_real(p, in, out, batch, w, st, mlo, mhi);
+      case Op::InversePhi: return do_inverse_phi_real(p, in, out, batch, w, st);
+      case Op::Inverse: return do_inverse_real(p, in, out, batch, w, st);
+      case Op::AdjForward: return do_adjoint_forward_real(p, in, out, batch, w, st);
+      case Op::AdjInverse: return do_adjoint_inverse_real(p, in, out, batch, w, st);
+    }
+    return S2GB_EINVAL;
+  }
   switch (op) {
     case Op::Forward: return do_forward(p, in, out, batch, w, st, mlo, mhi);
     case Op::InversePhi: return do_inverse_phi(p, in, out, batch, w, st);
@@ -304,8 +416,9 @@ using s2gb::Op;
 
 extern "C" {
 
-int s2gb_plan_create(s2gb_plan* out, int L, int spin, int N, int sampling, int precision,
-                     int max_batch, int device) {
+namespace {
+int plan_create_impl(s2gb_plan* out, int L, int spin, int N, int sampling, int precision, int max_batch,
+                     int device, bool real) {
   if (!out) return S2GB_EINVAL;
   *out = nullptr;
   if (L < 1 || L > 8192 || N < 0 || N > L || max_batch < 1 || sampling != S2GB_MW) return S2GB_EINVAL;
@@ -319,6 +432,7 @@ int s2gb_plan_create(s2gb_plan* out, int L, int spin, int N, int sampling, int p
   s2gb::Plan& p = h->p;
   p.L = L; p.spin = N == 0 ? spin : 0; p.N = N; p.precision = precision; p.max_batch = max_batch;
   p.device = device;
+  p.real = real;
   int rc;
   {
     s2gb::DeviceGuard g(device);
@@ -331,6 +445,17 @@ int s2gb_plan_create(s2gb_plan* out, int L, int spin, int N, int sampling, int p
   }
   *out = h;
   return S2GB_OK;
+}
+
+}  // namespace
+
+int s2gb_plan_create(s2gb_plan* out, int L, int spin, int N, int sampling, int precision,
+                     int max_batch, int device) {
+  return plan_create_impl(out, L, spin, N, sampling, precision, max_batch, device, false);
+}
+
+int s2gb_plan_create_real(s2gb_plan* out, int L, int sampling, int precision, int max_batch, int device) {
+  return plan_create_impl(out, L, 0, 0, sampling, precision, max_batch, device, true);
 }
 
 void s2gb_plan_destroy(s2gb_plan plan) {
@@ -372,10 +497,10 @@ int s2gb_inverse_theta_mrange(s2gb_plan plan, const void* flm, void* ftilde, int
   if (batch < 1 || batch > p.max_batch) return S2GB_EINVAL;
   if (m_lo < 0 || m_lo > m_hi || m_hi > p.L) return S2GB_EINVAL;
   const size_t es = p.precision == S2GB_FP64 ? 16 : 8;
-  if (s2gb::overlaps(flm, ftilde, (size_t)batch * p.L * p.T * es)) return S2GB_EINVAL;
+  if (s2gb::overlaps(flm, ftilde, (size_t)batch * p.L * p.MR * es)) return S2GB_EINVAL;
   s2gb::DeviceGuard g(p.device);
-  s2gb::InvArgs a = s2gb::inv_args(p, flm, ftilde, batch, p.scale_inv, (long long)p.L * p.T, p.T, 1, 1);
-  s2gb::mrange_ranks(m_lo, m_hi, a.rank0, a.nrank);
+  s2gb::InvArgs a = s2gb::inv_args(p, flm, ftilde, batch, p.scale_inv, (long long)p.L * p.MR, p.MR, 1, 1);
+  s2gb::order_ranks(p, m_lo, m_hi, a.rank0, a.nrank);
   return s2gb::cuda_rc(s2gb::launch_theta_inverse(p, a, reinterpret_cast<cudaStream_t>(stream)));
 }
 
@@ -399,9 +524,10 @@ int s2gb_forward_theta(s2gb_plan plan, const void* gin, void* flm, int batch, vo
   if (p.wigner || p.fwd_parts > 1) return S2GB_EUNSUPPORTED;   // L > 2048 needs a workspace
   if (batch < 1 || batch > p.max_batch) return S2GB_EINVAL;
   const size_t es = p.precision == S2GB_FP64 ? 16 : 8;
-  if (s2gb::overlaps(gin, flm, (size_t)batch * p.L * p.T * es)) return S2GB_EINVAL;
+  if (s2gb::overlaps(gin, flm, (size_t)batch * p.L * p.MR * es)) return S2GB_EINVAL;
   s2gb::DeviceGuard g(p.device);
-  s2gb::FwdArgs a = s2gb::fwd_args(p, gin, flm, batch, p.scale_fwd, (long long)p.T * p.L, 1, p.L, 0, 0);
+  s2gb::FwdArgs a = s2gb::fwd_args(p, gin, flm, batch, p.scale_fwd, (long long)p.MR * p.L, 1, p.L,
+                                   p.real ? 1 : 0, 0);
   return s2gb::cuda_rc(s2gb::launch_theta_forward(p, a, reinterpret_cast<cudaStream_t>(stream)));
 }
 
@@ -460,6 +586,7 @@ int noalloc_scratch(int device, void** out) {
 extern "C" int s2gb_inverse_noalloc(s2gb_plan plan, const void* flm, void* f, int batch, void* stream) {
   if (!plan || !flm || !f) return S2GB_EINVAL;
   s2gb::Plan& p = plan->p;
+  if (p.real) return S2GB_EUNSUPPORTED;
   if (batch < 1 || batch > p.max_batch) return S2GB_EINVAL;
   const size_t es = p.precision == S2GB_FP64 ? 16 : 8;
   const size_t sig_bytes = (size_t)batch * p.nN * p.L * p.T * es;

@@ -23,52 +23,54 @@ inline unsigned grid_for(size_t n) {
   return (unsigned)(g ? g : 1);
 }
 
-// G[s][mi][t'] (t' < T) from F[s][t][k]:  t' < L-1: F[t'];  t' = L-1: (1+sigma)/2 F[L-1];
-// t' >= L: sigma F[2L-2-t'];  sigma = (-1)^{m-n},  k = m mod T.
+// G[s][r][t'] (t' < T) from F[s][t][k]:  t' < L-1: F[t'];  t' = L-1: (1+sigma)/2 F[L-1];
+// t' >= L: sigma F[2L-2-t'];  sigma = (-1)^{m-n}.  Row r of G is order m = r - mo (MR rows); F has
+// rows of FW columns with column k = m mod T (complex signals: MR = FW = T, mo = L-1; real
+// signals, m >= 0 only: MR = FW = L, mo = 0).
 template <typename C>
 __global__ void extend_kernel(const C* __restrict__ F, C* __restrict__ G, int S, int L, int nN,
-                              const int* __restrict__ n_of) {
+                              const int* __restrict__ n_of, int MR, int mo, int FW) {
   const int T = 2 * L - 1;
-  const size_t total = (size_t)S * T * T;
+  const size_t total = (size_t)S * MR * T;
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
        idx += (size_t)gridDim.x * blockDim.x) {
     const int tp = (int)(idx % T);
-    const int mi = (int)((idx / T) % T);
-    const int s = (int)(idx / ((size_t)T * T));
-    const int m = mi - (L - 1);
+    const int r = (int)((idx / T) % MR);
+    const int s = (int)(idx / ((size_t)T * MR));
+    const int m = r - mo;
     const int k = m >= 0 ? m : m + T;
     const int n = n_of[s % nN];
     const bool odd = ((m - n) & 1) != 0;
     C out;
     if (tp < L - 1) {
-      out = F[((size_t)s * L + tp) * T + k];
+      out = F[((size_t)s * L + tp) * FW + k];
     } else if (tp == L - 1) {
-      out = odd ? C{0, 0} : F[((size_t)s * L + tp) * T + k];
+      out = odd ? C{0, 0} : F[((size_t)s * L + tp) * FW + k];
     } else {
-      C v = F[((size_t)s * L + (2 * L - 2 - tp)) * T + k];
+      C v = F[((size_t)s * L + (2 * L - 2 - tp)) * FW + k];
       out = odd ? C{-v.x, -v.y} : v;
     }
     G[idx] = out;
   }
 }
 
-// Adjoint of extend_kernel: F[s][t][k] = G[s][mi][t] + sigma G[s][mi][2L-2-t] (t < L-1),
-// F[s][L-1][k] = (1+sigma)/2 G[s][mi][L-1].
+// Adjoint of extend_kernel: F[s][t][k] = G[s][r][t] + sigma G[s][r][2L-2-t] (t < L-1),
+// F[s][L-1][k] = (1+sigma)/2 G[s][r][L-1], for every column k of F (FW = MR columns).
 template <typename C>
 __global__ void extend_adjoint_kernel(const C* __restrict__ G, C* __restrict__ F, int S, int L, int nN,
-                                      const int* __restrict__ n_of) {
+                                      const int* __restrict__ n_of, int MR, int mo) {
   const int T = 2 * L - 1;
-  const size_t total = (size_t)S * L * T;
+  const size_t total = (size_t)S * L * MR;
   for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
        idx += (size_t)gridDim.x * blockDim.x) {
-    const int k = (int)(idx % T);
-    const int t = (int)((idx / T) % L);
-    const int s = (int)(idx / ((size_t)T * L));
+    const int k = (int)(idx % MR);
+    const int t = (int)((idx / MR) % L);
+    const int s = (int)(idx / ((size_t)MR * L));
     const int m = k <= L - 1 ? k : k - T;
-    const int mi = m + L - 1;
+    const int r = m + mo;
     const int n = n_of[s % nN];
     const bool odd = ((m - n) & 1) != 0;
-    const C* row = G + ((size_t)s * T + mi) * T;
+    const C* row = G + ((size_t)s * MR + r) * T;
     C out;
     if (t < L - 1) {
       C a = row[t], b = row[2 * L - 2 - t];
@@ -165,13 +167,26 @@ __global__ void gamma_reorder_kernel(const C* __restrict__ in, C* __restrict__ o
   }
 }
 
-// out[i] = sum_{p < nparts} parts[p * n + i], in the order of p.
+// Real-signal spectra (columns m = 0 .. W-1): X[r][m] *= s for m >= 1; X[r][0] keeps its real
+// part only (the m = 0 term of a real signal's spectrum is real).
+template <typename C>
+__global__ void scale_nonzero_orders_kernel(C* __restrict__ X, size_t rows, int W, double s) {
+  using R = typename RealOf<C>::type;
+  const size_t total = rows * W;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    C v = X[idx];
+    X[idx] = (idx % W == 0) ? C{v.x, (R)0} : C{(R)(v.x * s), (R)(v.y * s)};
+  }
+}
+
+// out[i] = sum_{p < nparts} parts[p * n + i], in the order of p, for the columns (rows of ld,
+// column c0 + m) of the orders |m| in [mlo, mhi).
 template <typename C>
 __global__ void sum_parts_kernel(const C* __restrict__ parts, C* __restrict__ out, size_t n, int nparts,
-                                 int L, int mlo, int mhi) {
-  const int T = 2 * L - 1;
+                                 int ld, int c0, int mlo, int mhi) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    const int am = abs((int)(i % T) - (L - 1));
+    const int am = abs((int)(i % ld) - c0);
     if (am < mlo || am >= mhi) continue;
     C acc = parts[i];
     for (int q = 1; q < nparts; ++q) {
@@ -186,30 +201,45 @@ __global__ void sum_parts_kernel(const C* __restrict__ parts, C* __restrict__ ou
 }  // namespace
 
 cudaError_t launch_sum_parts(const Plan& p, const void* parts, void* out, int nsig, int nparts,
-                             int mlo, int mhi, cudaStream_t st) {
-  const size_t n = (size_t)nsig * p.nN * p.L * p.T;
+                             int mlo, int mhi, int ld, int c0, cudaStream_t st) {
+  const size_t n = (size_t)nsig * p.nN * p.L * ld;
   if (p.precision == S2GB_FP64)
-    sum_parts_kernel<double2><<<grid_for(n), 256, 0, st>>>((const double2*)parts, (double2*)out, n, nparts, p.L, mlo, mhi);
+    sum_parts_kernel<double2><<<grid_for(n), 256, 0, st>>>((const double2*)parts, (double2*)out, n, nparts, ld, c0, mlo, mhi);
   else
-    sum_parts_kernel<float2><<<grid_for(n), 256, 0, st>>>((const float2*)parts, (float2*)out, n, nparts, p.L, mlo, mhi);
+    sum_parts_kernel<float2><<<grid_for(n), 256, 0, st>>>((const float2*)parts, (float2*)out, n, nparts, ld, c0, mlo, mhi);
   return launched();
 }
 
 cudaError_t launch_extend(const Plan& p, const void* F, void* G, int nsig, cudaStream_t st) {
-  const size_t n = (size_t)nsig * p.T * p.T;
+  const size_t n = (size_t)nsig * p.MR * p.T;
+  const int mo = p.real ? 0 : p.L - 1;
   if (p.precision == S2GB_FP64)
-    extend_kernel<double2><<<grid_for(n), 256, 0, st>>>((const double2*)F, (double2*)G, nsig, p.L, p.nN, p.n_of);
+    extend_kernel<double2><<<grid_for(n), 256, 0, st>>>((const double2*)F, (double2*)G, nsig, p.L, p.nN, p.n_of,
+                                                        p.MR, mo, p.MR);
   else
-    extend_kernel<float2><<<grid_for(n), 256, 0, st>>>((const float2*)F, (float2*)G, nsig, p.L, p.nN, p.n_of);
+    extend_kernel<float2><<<grid_for(n), 256, 0, st>>>((const float2*)F, (float2*)G, nsig, p.L, p.nN, p.n_of,
+                                                       p.MR, mo, p.MR);
   return launched();
 }
 
 cudaError_t launch_extend_adjoint(const Plan& p, const void* G, void* F, int nsig, cudaStream_t st) {
-  const size_t n = (size_t)nsig * p.L * p.T;
+  const size_t n = (size_t)nsig * p.L * p.MR;
+  const int mo = p.real ? 0 : p.L - 1;
   if (p.precision == S2GB_FP64)
-    extend_adjoint_kernel<double2><<<grid_for(n), 256, 0, st>>>((const double2*)G, (double2*)F, nsig, p.L, p.nN, p.n_of);
+    extend_adjoint_kernel<double2><<<grid_for(n), 256, 0, st>>>((const double2*)G, (double2*)F, nsig, p.L, p.nN,
+                                                                p.n_of, p.MR, mo);
   else
-    extend_adjoint_kernel<float2><<<grid_for(n), 256, 0, st>>>((const float2*)G, (float2*)F, nsig, p.L, p.nN, p.n_of);
+    extend_adjoint_kernel<float2><<<grid_for(n), 256, 0, st>>>((const float2*)G, (float2*)F, nsig, p.L, p.nN,
+                                                               p.n_of, p.MR, mo);
+  return launched();
+}
+
+cudaError_t launch_scale_nonzero_orders(const Plan& p, void* X, size_t rows, double s, cudaStream_t st) {
+  const size_t n = rows * p.L;
+  if (p.precision == S2GB_FP64)
+    scale_nonzero_orders_kernel<double2><<<grid_for(n), 256, 0, st>>>((double2*)X, rows, p.L, s);
+  else
+    scale_nonzero_orders_kernel<float2><<<grid_for(n), 256, 0, st>>>((float2*)X, rows, p.L, s);
   return launched();
 }
 

@@ -188,13 +188,15 @@ int upload(T** dst, const std::vector<T>& src, size_t* counter) {
   return S2GB_OK;
 }
 
-int make_fft(cufftHandle* h, int n, int batch, int istride, int idist, cufftType type, size_t* work) {
+int make_fft(cufftHandle* h, int n, int batch, int istride, int idist, cufftType type, size_t* work,
+             int odist = 0) {
   if (cufftCreate(h) != CUFFT_SUCCESS) return S2GB_ECUFFT;
   if (cufftSetAutoAllocation(*h, 0) != CUFFT_SUCCESS) return S2GB_ECUFFT;
   int nn[1] = {n};
   int emb[1] = {n};
   size_t ws = 0;
-  cufftResult r = cufftMakePlanMany(*h, 1, nn, emb, istride, idist, emb, istride, idist, type, batch, &ws);
+  cufftResult r = cufftMakePlanMany(*h, 1, nn, emb, istride, idist, emb, istride, odist ? odist : idist,
+                                    type, batch, &ws);
   if (r != CUFFT_SUCCESS) return S2GB_ECUFFT;
   if (ws > *work) *work = ws;
   return S2GB_OK;
@@ -208,6 +210,7 @@ int make_plan(Plan* p) {
   p->T = T;
   p->wigner = p->N >= 1;
   p->nN = p->wigner ? 2 * p->N - 1 : 1;
+  p->MR = p->real ? L : T;
   p->Nfft = good_fft_size(4 * L - 3 > 2 * L - 1 ? 4 * L - 3 : 2 * L - 1);
   const int nN = p->nN;
 
@@ -344,18 +347,26 @@ int make_plan(Plan* p) {
   }
 
   // ---- cuFFT plans ----
-  const cufftType ty = p->precision == S2GB_FP64 ? CUFFT_Z2Z : CUFFT_C2C;
+  const bool f64 = p->precision == S2GB_FP64;
+  const cufftType ty = f64 ? CUFFT_Z2Z : CUFFT_C2C;
   const int S[2] = {nN, p->max_batch * nN};
+  const int MR = p->MR;
   for (int q = 0; q < 2; ++q) {
     if (q == 1 && S[1] == S[0]) {
       p->fft_phi[1] = p->fft_phi[0];
+      p->fft_phi_c2r[1] = p->fft_phi_c2r[0];
       p->fft_T[1] = p->fft_T[0];
       p->fft_N[1] = p->fft_N[0];
       continue;
     }
-    if ((rc = make_fft(&p->fft_phi[q], T, S[q] * L, 1, T, ty, &p->fft_work))) return rc;
-    if ((rc = make_fft(&p->fft_T[q], T, S[q] * T, 1, T, ty, &p->fft_work))) return rc;
-    if ((rc = make_fft(&p->fft_N[q], NF, S[q] * T, 1, NF, ty, &p->fft_work))) return rc;
+    if (p->real) {   // rings of T real samples <-> orders m = 0 .. L-1
+      if ((rc = make_fft(&p->fft_phi[q], T, S[q] * L, 1, T, f64 ? CUFFT_D2Z : CUFFT_R2C, &p->fft_work, L))) return rc;
+      if ((rc = make_fft(&p->fft_phi_c2r[q], T, S[q] * L, 1, L, f64 ? CUFFT_Z2D : CUFFT_C2R, &p->fft_work, T))) return rc;
+    } else {
+      if ((rc = make_fft(&p->fft_phi[q], T, S[q] * L, 1, T, ty, &p->fft_work))) return rc;
+    }
+    if ((rc = make_fft(&p->fft_T[q], T, S[q] * MR, 1, T, ty, &p->fft_work))) return rc;
+    if ((rc = make_fft(&p->fft_N[q], NF, S[q] * MR, 1, NF, ty, &p->fft_work))) return rc;
     p->fft_made[q] = true;
   }
   if (p->wigner) {
@@ -380,6 +391,7 @@ void free_plan(Plan* p) {
   for (int q = 0; q < 2; ++q)
     if (p->fft_made[q]) {
       cufftDestroy(p->fft_phi[q]);
+      if (p->real) cufftDestroy(p->fft_phi_c2r[q]);
       cufftDestroy(p->fft_T[q]);
       cufftDestroy(p->fft_N[q]);
     }
@@ -392,10 +404,10 @@ size_t workspace_bytes(const Plan& p, int batch) {
   if (batch < 1 || batch > p.max_batch) return 0;
   const size_t es = p.precision == S2GB_FP64 ? 16 : 8;
   const size_t S = (size_t)batch * p.nN;
-  const size_t bufA = S * p.T * (size_t)(p.Nfft > p.L ? p.Nfft : p.L) * es;
-  const size_t bufB = S * p.T * (size_t)p.T * es;
+  const size_t bufA = S * p.MR * (size_t)(p.Nfft > p.L ? p.Nfft : p.L) * es;
+  const size_t bufB = S * p.MR * (size_t)p.T * es;
   const size_t bufC = p.wigner ? S * p.L * (size_t)p.T * es : 0;
-  const size_t bufD = p.fwd_parts > 1 ? (size_t)p.fwd_parts * S * p.L * (size_t)p.T * es : 0;
+  const size_t bufD = p.fwd_parts > 1 ? (size_t)p.fwd_parts * S * p.L * (size_t)p.MR * es : 0;
   return align256(bufA) + align256(bufB) + align256(bufC) + align256(bufD) + align256(p.fft_work) + 256;
 }
 

@@ -59,6 +59,8 @@ struct Plan {
   int cap_s = 0;
   int fwd_parts = 1;  // forward theta stage in one launch (L <= 2048) or in ring chunks
   bool wigner = false;
+  bool real = false;  // real signals (spin 0): orders m >= 0 only, f real, flm [L][L]
+  int MR = 0;         // order rows of the theta-direction buffers: T (complex) or L (real)
 
   // device tables
   double* coef = nullptr;      // [nN][T][L][kCoefPerStepN] (m index = m + L - 1, step j); FP64 plans
@@ -74,7 +76,8 @@ struct Plan {
   size_t device_bytes = 0;
 
   // cuFFT plans: index 0 = one signal, 1 = max_batch signals (rows of the whole batch)
-  cufftHandle fft_phi[2] = {0, 0};   // length T along rows of length T, S*L rows
+  cufftHandle fft_phi[2] = {0, 0};   // length T along rows of length T, S*L rows (real: R2C)
+  cufftHandle fft_phi_c2r[2] = {0, 0};   // real plans: the inverse direction (C2R)
   cufftHandle fft_T[2] = {0, 0};     // length T, S*T rows
   cufftHandle fft_N[2] = {0, 0};     // length Nfft, S*T rows
   cufftHandle fft_gam[1] = {0};      // length 2N-1, stride L*T, L*T rows (one signal)
@@ -103,6 +106,9 @@ struct InvArgs {
   const float* v32;
   int rank0;            // orders of this launch: m-ranks [rank0, rank0 + nrank) (m_of_rank order
   int nrank;            // 0, -1, 1, -2, 2, ...: |m| in [lo, hi) is ranks [max(0, 2lo-1), 2hi-1))
+  int mpos;             // 1: rank r is order m = r (real-signal plans: m >= 0 only)
+  int flm_ld;           // row length of flm (T; L for real-signal plans)
+  int flm_c0;           // column of m = 0 in flm (L - 1; 0 for real-signal plans)
 };
 
 struct FwdArgs {
@@ -127,6 +133,9 @@ struct FwdArgs {
   long long part_off;   // (elements) instead of flm; a fixed-order sum of the parts gives flm
   int rank0;            // orders of this launch (as in InvArgs)
   int nrank;
+  int mpos;             // flm layout and order mapping as in InvArgs
+  int flm_ld;
+  int flm_c0;
 };
 
 // m-ranks of the orders with |m| in [lo, hi), 0 <= lo <= hi <= L (empty: count 0)
@@ -152,9 +161,11 @@ cudaError_t launch_pad(const Plan& p, const void* X, void* Y, int rows, cudaStre
 cudaError_t launch_truncate(const Plan& p, const void* Y, void* X, int rows, cudaStream_t st);
 cudaError_t launch_weight_fine(const Plan& p, void* Y, int rows, cudaStream_t st);
 cudaError_t launch_nu_extend(const Plan& p, void* X, int rows, cudaStream_t st);
-// out[i] = sum of the parts in order, for the columns (m + L - 1) of orders with |m| in [mlo, mhi)
+// out[i] = sum of the parts in order, for the columns (c0 + m, rows of ld) of orders |m| in [mlo, mhi)
 cudaError_t launch_sum_parts(const Plan& p, const void* parts, void* out, int nsig, int nparts,
-                             int mlo, int mhi, cudaStream_t st);
+                             int mlo, int mhi, int ld, int c0, cudaStream_t st);
+// real-signal spectra [rows][L]: columns m >= 1 times s, imaginary part of column 0 dropped
+cudaError_t launch_scale_nonzero_orders(const Plan& p, void* X, size_t rows, double s, cudaStream_t st);
 cudaError_t launch_gamma_reorder(const Plan& p, const void* in, void* out, int batch, int to_signal,
                                  double scale, cudaStream_t st);
 

@@ -146,7 +146,8 @@ __device__ __forceinline__ void inverse_body(const InvArgs& a, int m, int ni, in
       const Slot sl = slot_of<NB, PAIR>(b, sig0, a.nsig, a.nN, ni, m, n, L);
       double2 h = make_double2(0.0, 0.0);
       if (j < L && sl.sig_off >= 0) {
-        h = reinterpret_cast<const double2*>(a.flm)[((size_t)sl.sig_off * L + j) * T + sl.mi];
+        h = reinterpret_cast<const double2*>(a.flm)[((size_t)sl.sig_off * L + j) * a.flm_ld + sl.m + a.flm_c0];
+        if (a.mpos && m == 0) h.y = 0.0;      // real signals: flm(l, 0) is real
         // plain chains carry u^j = d^j / gamma_j: fold gamma_j into the coefficient
         const double s = sl.sign * (DIFF ? scale[j] : scale[j] * coef_m[(size_t)j * kCoefPerStepN + 3]);
         h.x *= s; h.y *= s;
@@ -221,7 +222,7 @@ __global__ void __launch_bounds__(128) theta_inverse_kernel(InvArgs a, int ntile
   __shared__ double cs[kChunk * kCoefPerStepN];
   const int L = a.L;
   const int rank = a.rank0 + (int)(blockIdx.x / ntiles), tile = blockIdx.x % ntiles;
-  const int m = m_of_rank(rank);
+  const int m = a.mpos ? rank : m_of_rank(rank);
   const int ni = PAIR ? (a.nN - 1) / 2 + (int)blockIdx.y : (int)blockIdx.y;
   const int n = ni - (a.nN - 1) / 2;          // used only with pairing (n-set symmetric about 0)
   if (PAIR && n == 0 && m < 0) return;        // produced by the CTA of -m
@@ -275,7 +276,7 @@ __global__ void __launch_bounds__(128) theta_forward_kernel(FwdArgs a) {
   double* red = reinterpret_cast<double*>(gs + NBX * rows);   // [2][nwarps][32]
   double* vs = red + 2 * nwarps * 32;                          // [rows]
 
-  const int m = m_of_rank(a.rank0 + (int)blockIdx.x);
+  const int m = a.mpos ? a.rank0 + (int)blockIdx.x : m_of_rank(a.rank0 + (int)blockIdx.x);
   const int mi = m + L - 1;
   const int ni = PAIR ? (a.nN - 1) / 2 + (int)blockIdx.y : (int)blockIdx.y;
   const int n = ni - (a.nN - 1) / 2;          // used only with pairing
@@ -290,7 +291,7 @@ __global__ void __launch_bounds__(128) theta_forward_kernel(FwdArgs a) {
   for (int q = tid; q < NBX * lz; q += nt) {
     const int b = q / lz, j = q % lz;
     const Slot sl = slot_of<NB, PAIR>(b, sig0, a.nsig, a.nN, ni, m, n, L);
-    if (sl.sig_off >= 0) outb[((size_t)sl.sig_off * L + j) * T + sl.mi] = make_double2(0.0, 0.0);
+    if (sl.sig_off >= 0) outb[((size_t)sl.sig_off * L + j) * a.flm_ld + sl.m + a.flm_c0] = make_double2(0.0, 0.0);
   }
   if (l0 >= L) return;
 
@@ -402,7 +403,7 @@ __global__ void __launch_bounds__(128) theta_forward_kernel(FwdArgs a) {
       const int j = j0 + jr;
       const Slot sl = slot_of<NB, PAIR>(b, sig0, a.nsig, a.nN, ni, m, n, L);
       if (j < L && sl.sig_off >= 0) {
-        double* o = reinterpret_cast<double*>(outb + ((size_t)sl.sig_off * L + j) * T + sl.mi);
+        double* o = reinterpret_cast<double*>(outb + ((size_t)sl.sig_off * L + j) * a.flm_ld + sl.m + a.flm_c0);
         o[reim] = tot * (scale[j] * coef_m[(size_t)j * kCoefPerStepN + 3]);   // * gamma_j
       }
     }
@@ -463,7 +464,7 @@ cudaError_t launch_fwd_nb(const Plan& p, const FwdArgs& a0, cudaStream_t st) {
   // interior chunks of at most kFwdChunk rings (plain form); each launch writes a partial result
   // that a fixed-order sum turns into flm.
   if (!a0.part) return cudaErrorInvalidValue;
-  const long long part_elems = (long long)a.nsig * a.nN * L * p.T;
+  const long long part_elems = (long long)a.nsig * a.nN * L * a.flm_ld;
   int q = 0;
   cudaError_t e;
   // threads per CTA: KT * nt >= rows and nt <= rows (the last slot holds the last nt rings)
@@ -482,13 +483,15 @@ cudaError_t launch_fwd_nb(const Plan& p, const FwdArgs& a0, cudaStream_t st) {
     if ((e = launch_fwd<16, NB, 2, PAIR>(p, a, nt_for(a.nrows, 16), st)) != cudaSuccess) return e;
   }
   if (q != p.fwd_parts) return cudaErrorInvalidValue;
-  // the orders of this launch: |m| in [(rank0 + 1) / 2, (rank0 + nrank + 1) / 2)
-  return launch_sum_parts(p, a0.part, a0.flm, a.nsig, q, (a.rank0 + 1) / 2,
-                          (a.rank0 + a.nrank + 1) / 2, st);
+  // the orders of this launch: |m| in [(rank0 + 1) / 2, (rank0 + nrank + 1) / 2), or
+  // m in [rank0, rank0 + nrank) for real-signal plans
+  const int mlo = a.mpos ? a.rank0 : (a.rank0 + 1) / 2;
+  const int mhi = a.mpos ? a.rank0 + a.nrank : (a.rank0 + a.nrank + 1) / 2;
+  return launch_sum_parts(p, a0.part, a0.flm, a.nsig, q, mlo, mhi, a.flm_ld, a.flm_c0, st);
 }
 
 // Pairing (m, n) with (-m, -n) needs the set of n to be symmetric: spin-0 sphere plans and Wigner.
-bool paired(const Plan& p) { return p.wigner || p.spin == 0; }
+bool paired(const Plan& p) { return !p.real && (p.wigner || p.spin == 0); }
 
 }  // namespace
 

@@ -125,7 +125,8 @@ __device__ __forceinline__ void inverse_body_f32(const InvArgs& a, int m, int ni
       const int jj = q / NB, b = q % NB, j = jc + jj, sig = sig0 + b;
       float2 h = make_float2(0.f, 0.f);
       if (j < L && sig < a.nsig) {
-        h = reinterpret_cast<const float2*>(a.flm)[((size_t)(sig * a.nN + ni) * L + j) * T + mi];
+        h = reinterpret_cast<const float2*>(a.flm)[((size_t)(sig * a.nN + ni) * L + j) * a.flm_ld + m + a.flm_c0];
+        if (a.mpos && m == 0) h.y = 0.f;      // real signals: flm(l, 0) is real
         const float s = (float)scale[j];
         h.x *= s; h.y *= s;
       }
@@ -211,7 +212,7 @@ __global__ void __launch_bounds__(128) theta_inverse_kernel_f32(InvArgs a, int n
   __shared__ float cs[kChunk32 * kCoefPerStep];
   const int L = a.L;
   const int rank = a.rank0 + (int)(blockIdx.x / ntiles), tile = blockIdx.x % ntiles;
-  const int m = m_of_rank(rank);
+  const int m = a.mpos ? rank : m_of_rank(rank);
   const int ni = blockIdx.y;
   const int l0 = a.seed[(size_t)ni * (2 * L - 1) + m + L - 1].l0;
   const int t_lo = tile * KT * blockDim.x, t_hi = min(L, t_lo + KT * (int)blockDim.x) - 1;
@@ -257,7 +258,7 @@ __global__ void __launch_bounds__(128) theta_forward_kernel_f32(FwdArgs a) {
   float2* gs = reinterpret_cast<float2*>(red + 2 * nwarps * 32);  // [NB][rows]
   float* vs = reinterpret_cast<float*>(gs + NB * rows);           // [rows]
 
-  const int m = m_of_rank(a.rank0 + (int)blockIdx.x);
+  const int m = a.mpos ? a.rank0 + (int)blockIdx.x : m_of_rank(a.rank0 + (int)blockIdx.x);
   const int mi = m + L - 1;
   const int ni = blockIdx.y;
   const int sig0 = blockIdx.z * NB;
@@ -268,7 +269,7 @@ __global__ void __launch_bounds__(128) theta_forward_kernel_f32(FwdArgs a) {
   for (int q = tid; q < NB * min(l0, L); q += nt) {
     const int b = q / min(l0, L), j = q % min(l0, L), sig = sig0 + b;
     if (sig < a.nsig)
-      reinterpret_cast<float2*>(a.flm)[((size_t)(sig * a.nN + ni) * L + j) * T + mi] = make_float2(0.f, 0.f);
+      reinterpret_cast<float2*>(a.flm)[((size_t)(sig * a.nN + ni) * L + j) * a.flm_ld + m + a.flm_c0] = make_float2(0.f, 0.f);
   }
   if (l0 >= L) return;
 
@@ -371,7 +372,7 @@ __global__ void __launch_bounds__(128) theta_forward_kernel_f32(FwdArgs a) {
       const int j = j0 + jr, sig = sig0 + b;
       if (j < L && sig < a.nsig) {
         float* o = reinterpret_cast<float*>(
-            reinterpret_cast<float2*>(a.flm) + ((size_t)(sig * a.nN + ni) * L + j) * T + mi);
+            reinterpret_cast<float2*>(a.flm) + ((size_t)(sig * a.nN + ni) * L + j) * a.flm_ld + m + a.flm_c0);
         o[reim] = (float)(tot * scale[j]);
       }
     }

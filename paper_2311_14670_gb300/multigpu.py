@@ -51,16 +51,17 @@ def weak_scaling_throughput(units_per_rank: int, world: int, ms_max: float, step
 
 
 # ---------------------------------------------------------------------------- order sharding
-def order_work(L: int, n_abs: int = 0) -> list:
-    """Theta-stage work of each |m| = a: the (l, +-m) pairs with max(a, |n|) <= l < L."""
-    return [max(0, L - max(a, n_abs)) * (1 if a == 0 else 2) for a in range(L)]
+def order_work(L: int, n_abs: int = 0, real: bool = False) -> list:
+    """Theta-stage work of each |m| = a: the (l, +-m) pairs with max(a, |n|) <= l < L (real
+    signals: the order m = a alone)."""
+    return [max(0, L - max(a, n_abs)) * (1 if (a == 0 or real) else 2) for a in range(L)]
 
 
-def order_ranges(L: int, world: int, n_abs: int = 0) -> list:
+def order_ranges(L: int, world: int, n_abs: int = 0, real: bool = False) -> list:
     """Contiguous |m| ranges [lo, hi), one per rank, covering [0, L) with balanced work (the cut
     after the prefix of work closest to k/world of the total).  A rank may get an empty range
     when world > L."""
-    work = order_work(L, n_abs)
+    work = order_work(L, n_abs, real)
     total = float(sum(work))
     cuts = [0]
     acc, a = 0.0, 0
@@ -75,12 +76,16 @@ def order_ranges(L: int, world: int, n_abs: int = 0) -> list:
 
 
 def column_owner(L: int, ranges, layout: str) -> list:
-    """Rank owning each of the T = 2L-1 columns: layout "mod" (column k = m mod T: ring spectra)
-    or "centered" (column m + L - 1: coefficients)."""
+    """Rank owning each column: layout "mod" (T = 2L-1 columns, k = m mod T: ring spectra),
+    "centered" (T columns, m + L - 1: coefficients) or "real" (L columns, m >= 0: both arrays of
+    real-signal plans)."""
     T = 2 * L - 1
-    owner = [-1] * T
+    owner = [-1] * (L if layout == "real" else T)
     for r, (lo, hi) in enumerate(ranges):
         for a in range(lo, hi):
+            if layout == "real":
+                owner[a] = r
+                continue
             for m in ((0,) if a == 0 else (a, -a)):
                 owner[(m % T) if layout == "mod" else m + L - 1] = r
     if min(owner) < 0:
@@ -124,7 +129,8 @@ def sharded_inverse(plan, flm, ranges, rank: int, gather):
     lo, hi = ranges[rank]
     ft = torch.zeros(tuple(flm.shape), dtype=flm.dtype, device=flm.device)
     plan.inverse_theta_mrange(flm, lo, hi, out=ft)
-    ft = assemble_columns(gather(ft), column_owner(plan.L, ranges, "mod"))
+    real = getattr(plan, "real", False)
+    ft = assemble_columns(gather(ft), column_owner(plan.L, ranges, "real" if real else "mod"))
     return plan.inverse_phi(ft)
 
 
@@ -134,6 +140,7 @@ def sharded_forward(plan, f, ranges, rank: int, gather):
     import torch
 
     lo, hi = ranges[rank]
-    flm = torch.zeros(tuple(f.shape), dtype=f.dtype, device=f.device)
+    flm = torch.zeros(plan.coef_shape(f.shape[0]), dtype=plan.dtype, device=f.device)
     plan.forward_mrange(f, lo, hi, out=flm)
-    return assemble_columns(gather(flm), column_owner(plan.L, ranges, "centered"))
+    real = getattr(plan, "real", False)
+    return assemble_columns(gather(flm), column_owner(plan.L, ranges, "real" if real else "centered"))

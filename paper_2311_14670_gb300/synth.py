@@ -33,6 +33,22 @@ def flm_gaussian(L: int, spin: int, batch: int, seed: int, ell_power: float = 0.
     return a
 
 
+def flm_real_gaussian(L: int, batch: int, seed: int, ell_power: float = 0.0) -> np.ndarray:
+    """Coefficients of a real signal, orders m >= 0 (batch, L, L): complex Gaussian times
+    (l+1)^-ell_power where m <= l, real at m = 0."""
+    rng = np.random.default_rng(seed)
+    a = complex_gaussian(rng, (batch, L, L))
+    a *= (np.arange(L) + 1.0)[:, None] ** (-ell_power)
+    a = np.where(np.arange(L)[None, :] <= np.arange(L)[:, None], a, 0)
+    a[..., 0] = a[..., 0].real
+    return a
+
+
+def signal_real_gaussian(shape, seed: int) -> np.ndarray:
+    """Arbitrary real samples, standard Gaussian."""
+    return np.random.default_rng(seed).standard_normal(shape)
+
+
 def flmn_gaussian(L: int, N: int, batch: int, seed: int) -> np.ndarray:
     """Wigner coefficients (batch, 2N-1, L, 2L-1), complex Gaussian where l >= max(|m|, |n|)."""
     rng = np.random.default_rng(seed)

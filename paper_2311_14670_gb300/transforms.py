@@ -1,9 +1,11 @@
 """PyTorch-facing wrappers of libs2gb.so: plans, transforms on CUDA tensors, autograd.
 
-Tensors are complex CUDA tensors laid out as in ``include/s2gb.h``:
-  sphere:  f, flm of shape (batch, L, 2L-1)
-  Wigner:  f, flmn of shape (batch, 2N-1, L, 2L-1)
-complex128 for ``precision="fp64"`` plans, complex64 for ``"fp32"``.  Every call enqueues on
+Tensors are CUDA tensors laid out as in ``include/s2gb.h``:
+  sphere:  f, flm of shape (batch, L, 2L-1), complex
+  Wigner:  f, flmn of shape (batch, 2N-1, L, 2L-1), complex
+  real signals (``real=True``, spin 0): f real of shape (batch, L, 2L-1), flm complex of shape
+           (batch, L, L) holding the orders m >= 0
+complex128 / float64 for ``precision="fp64"`` plans, complex64 / float32 for ``"fp32"``.  Every call enqueues on
 PyTorch's current stream of the plan's device.  The autograd functions use the hand-written adjoint
 transforms for the backward pass (Sec. 5.2), which recompute the Wigner d-functions instead of
 storing anything.
@@ -17,13 +19,14 @@ import torch
 from . import _native as nat
 
 _PRECISIONS = {"fp64": (nat.S2GB_FP64, torch.complex128), "fp32": (nat.S2GB_FP32, torch.complex64)}
+_REAL_OF = {torch.complex128: torch.float64, torch.complex64: torch.float32}
 
 
 class Plan:
     """A transform plan (``s2gb_plan_create``) plus a per-batch-size workspace cache."""
 
     def __init__(self, L: int, spin: int = 0, N: int = 0, precision: str = "fp64", max_batch: int = 1,
-                 device: int | torch.device | None = None, sampling: str = "mw"):
+                 device: int | torch.device | None = None, sampling: str = "mw", real: bool = False):
         if sampling != "mw":
             raise ValueError("only MW sampling is implemented")
         if precision not in _PRECISIONS:
@@ -34,9 +37,17 @@ class Plan:
             device = device.index if device.index is not None else torch.cuda.current_device()
         self.L, self.spin, self.N, self.precision, self.max_batch = int(L), int(spin), int(N), precision, int(max_batch)
         self.device = torch.device("cuda", int(device))
-        self.dtype = _PRECISIONS[precision][1]
-        self._h = nat.plan_create(self.L, self.spin, self.N, nat.S2GB_MW, _PRECISIONS[precision][0],
-                                  self.max_batch, int(device))
+        self.dtype = _PRECISIONS[precision][1]          # coefficients (and complex signals)
+        self.real = bool(real)
+        if self.real:
+            if self.spin != 0 or self.N != 0:
+                raise ValueError("real-signal plans are spin-0 sphere transforms (spin = 0, N = 0)")
+            self._h = nat.plan_create_real(self.L, nat.S2GB_MW, _PRECISIONS[precision][0], self.max_batch,
+                                           int(device))
+        else:
+            self._h = nat.plan_create(self.L, self.spin, self.N, nat.S2GB_MW, _PRECISIONS[precision][0],
+                                      self.max_batch, int(device))
+        self.signal_dtype = _REAL_OF[self.dtype] if self.real else self.dtype
         self._ws = {}
         self._lock = threading.Lock()
 
@@ -46,8 +57,18 @@ class Plan:
         return self.N >= 1
 
     def shape(self, batch: int) -> tuple:
+        """Shape of f (and of flm, for complex plans)."""
         T = 2 * self.L - 1
         return (batch, 2 * self.N - 1, self.L, T) if self.wigner else (batch, self.L, T)
+
+    def coef_shape(self, batch: int) -> tuple:
+        """Shape of flm (and of the theta stage's ring spectra)."""
+        return (batch, self.L, self.L) if self.real else self.shape(batch)
+
+    def _spec(self, kind: str):
+        if kind == "signal":
+            return self.shape, self.signal_dtype
+        return self.coef_shape, self.dtype
 
     def workspace_bytes(self, batch: int) -> int:
         return nat.workspace_bytes(self._h, batch)
@@ -63,29 +84,36 @@ class Plan:
                 self._ws[batch] = ws
             return ws
 
-    def _check(self, x: torch.Tensor, name: str) -> int:
+    def _check(self, x: torch.Tensor, name: str, kind: str = "coef") -> int:
+        shape_of, dtype = self._spec(kind)
         if not isinstance(x, torch.Tensor) or x.device != self.device:
             raise ValueError(f"{name} must be a tensor on {self.device}")
-        if x.dtype != self.dtype:
-            raise TypeError(f"{name} must have dtype {self.dtype}, got {x.dtype}")
+        if x.dtype != dtype:
+            raise TypeError(f"{name} must have dtype {dtype}, got {x.dtype}")
         if not x.is_contiguous():
             raise ValueError(f"{name} must be contiguous")
-        batch = x.shape[0] if x.dim() == len(self.shape(1)) else None
-        if batch is None or tuple(x.shape) != self.shape(batch):
-            raise ValueError(f"{name} has shape {tuple(x.shape)}, expected {self.shape(batch or 1)}")
+        batch = x.shape[0] if x.dim() == len(shape_of(1)) else None
+        if batch is None or tuple(x.shape) != shape_of(batch):
+            raise ValueError(f"{name} has shape {tuple(x.shape)}, expected {shape_of(batch or 1)}")
         if not 1 <= batch <= self.max_batch:
             raise ValueError(f"batch {batch} outside [1, {self.max_batch}]")
         return batch
 
+    def _out(self, out, batch: int, kind: str):
+        shape_of, dtype = self._spec(kind)
+        if out is None:
+            return torch.empty(shape_of(batch), dtype=dtype, device=self.device)
+        if self._check(out, "out", kind) != batch:
+            raise ValueError("out must have the batch size of the input")
+        return out
+
     def _stream(self) -> int:
         return torch.cuda.current_stream(self.device).cuda_stream
 
-    def _run(self, name: str, x: torch.Tensor, out: torch.Tensor | None, ws: torch.Tensor | None):
-        batch = self._check(x, "input")
-        if out is None:
-            out = torch.empty(self.shape(batch), dtype=self.dtype, device=self.device)
-        else:
-            self._check(out, "out")
+    def _run(self, name: str, x: torch.Tensor, out: torch.Tensor | None, ws: torch.Tensor | None,
+             src: str, dst: str):
+        batch = self._check(x, "input", src)
+        out = self._out(out, batch, dst)
         if ws is None:
             ws = self.workspace(batch)
         getattr(nat, name)(self._h, x, out, batch, ws, ws.numel(), self._stream())
@@ -94,58 +122,55 @@ class Plan:
     # ---------------------------------------------------------------- transforms (no autograd)
     def forward(self, f, out=None, ws=None):
         """Forward transform f -> flm (s2gb_forward)."""
-        return self._run("forward", f, out, ws)
+        return self._run("forward", f, out, ws, "signal", "coef")
 
     def inverse(self, flm, out=None, ws=None):
         """Inverse transform flm -> f (s2gb_inverse)."""
-        return self._run("inverse", flm, out, ws)
+        return self._run("inverse", flm, out, ws, "coef", "signal")
 
     def adjoint_forward(self, flm_bar, out=None, ws=None):
-        return self._run("adjoint_forward", flm_bar, out, ws)
+        return self._run("adjoint_forward", flm_bar, out, ws, "coef", "signal")
 
     def adjoint_inverse(self, f_bar, out=None, ws=None):
-        return self._run("adjoint_inverse", f_bar, out, ws)
+        return self._run("adjoint_inverse", f_bar, out, ws, "signal", "coef")
 
     def inverse_theta(self, flm, out=None):
-        """Theta stage of the inverse alone (s2gb_inverse_theta): ftilde[b][t][m mod T]."""
+        """Theta stage of the inverse alone (s2gb_inverse_theta): ring spectra ftilde[b][t][k],
+        k = m mod T (real plans: k = m >= 0)."""
         return self.inverse_theta_mrange(flm, 0, self.L, out=out)
 
     def inverse_theta_mrange(self, flm, m_lo: int, m_hi: int, out=None):
         """Theta stage of the inverse for the orders with |m| in [m_lo, m_hi)
         (s2gb_inverse_theta_mrange); columns of other orders in ``out`` are left as they are."""
         batch = self._check(flm, "flm")
-        if out is None:
-            out = torch.empty(self.shape(batch), dtype=self.dtype, device=self.device)
-        elif self._check(out, "out") != batch:
-            raise ValueError("out must have the batch size of flm")
+        out = self._out(out, batch, "coef")
         nat.inverse_theta_mrange(self._h, flm, out, batch, int(m_lo), int(m_hi), self._stream())
         return out
 
     def inverse_phi(self, ftilde, out=None, ws=None):
-        """The phi stage of the sphere inverse: ftilde[b][t][m mod T] -> f (s2gb_inverse_phi)."""
-        return self._run("inverse_phi", ftilde, out, ws)
+        """The phi stage of the sphere inverse: ring spectra -> f (s2gb_inverse_phi)."""
+        return self._run("inverse_phi", ftilde, out, ws, "coef", "signal")
 
     def forward_mrange(self, f, m_lo: int, m_hi: int, out=None, ws=None):
         """Forward transform whose theta stage covers the orders with |m| in [m_lo, m_hi) only
         (s2gb_forward_mrange); flm entries of other orders in ``out`` are left as they are."""
-        batch = self._check(f, "f")
-        if out is None:
-            out = torch.empty(self.shape(batch), dtype=self.dtype, device=self.device)
-        elif self._check(out, "out") != batch:
-            raise ValueError("out must have the batch size of f")
+        batch = self._check(f, "f", "signal")
+        out = self._out(out, batch, "coef")
         if ws is None:
             ws = self.workspace(batch)
         nat.forward_mrange(self._h, f, out, batch, int(m_lo), int(m_hi), ws, ws.numel(), self._stream())
         return out
 
     def forward_theta(self, g, out=None):
-        """Theta stage of the forward alone (s2gb_forward_theta): g[b][m+L-1][t] -> flm."""
-        if g.dim() != 3 or tuple(g.shape[1:]) != (2 * self.L - 1, self.L):
-            raise ValueError("g must have shape (batch, 2L-1, L)")
+        """Theta stage of the forward alone (s2gb_forward_theta): g[b][r][t] -> flm, r = m + L - 1
+        (real plans: r = m >= 0)."""
+        rows = self.L if self.real else 2 * self.L - 1
+        if g.dim() != 3 or tuple(g.shape[1:]) != (rows, self.L):
+            raise ValueError(f"g must have shape (batch, {rows}, L)")
         if g.dtype != self.dtype or g.device != self.device or not g.is_contiguous():
             raise ValueError("g must be a contiguous tensor of the plan's dtype and device")
         batch = g.shape[0]
-        out = torch.empty(self.shape(batch), dtype=self.dtype, device=self.device) if out is None else out
+        out = self._out(out, batch, "coef")
         nat.forward_theta(self._h, g, out, batch, self._stream())
         return out
 

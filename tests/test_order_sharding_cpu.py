@@ -30,6 +30,17 @@ def test_order_ranges_cover_and_balance(L, world, n_abs):
         assert max(loads) - sum(work) / world <= max(work)
 
 
+def test_real_signal_ranges_and_owner():
+    L, world = 50, 4
+    ranges = order_ranges(L, world, real=True)
+    work = order_work(L, real=True)
+    assert sum(work) == L * (L + 1) // 2
+    loads = [sum(work[a:b]) for a, b in ranges]
+    assert max(loads) - sum(work) / world <= max(work)
+    owner = column_owner(L, ranges, "real")
+    assert len(owner) == L and owner == sorted(owner)
+
+
 def test_column_owner_layouts():
     L, ranges = 4, [(0, 2), (2, 4)]                 # rank 0: m in {0, +-1}; rank 1: m in {+-2, +-3}
     T = 2 * L - 1
@@ -46,6 +57,10 @@ class _OraclePlan:
 
     def __init__(self, L, spin):
         self.L, self.spin = L, spin
+        self.dtype = torch.complex128
+
+    def coef_shape(self, batch):
+        return (batch, self.L, 2 * self.L - 1)
 
     def _mask(self, lo, hi):
         m = np.arange(-(self.L - 1), self.L)

@@ -46,11 +46,20 @@ WORKLOADS = {
                     "batch 1, FP64"),
     "l1024realb4": (1024, 0, 0, 4, 1.0, "real-signal SHT round trip (orders m >= 0), L=1024, MW 1024x2047, "
                     "batch 4, FP64"),
+    "l1024s2b4pre": (1024, 2, 0, 4, 1.0, "spin-2 SHT round trip, L=1024, batch 4, FP64, precompute mode "
+                     "(d-table 8.6 GB in HBM)"),
+    "l1024s0b1pre": (1024, 0, 0, 1, 0.0, "spin-0 SHT round trip, L=1024, batch 1, FP64, precompute mode "
+                     "(d-table 4.3 GB in HBM)"),
+    "l2048s0b1pre": (2048, 0, 0, 1, 0.0, "spin-0 SHT round trip, L=2048, batch 1, FP64, precompute mode "
+                     "(d-table 34 GB in HBM)"),
+    "l2048realb1pre": (2048, 0, 0, 1, 0.0, "real-signal SHT round trip, L=2048, batch 1, FP64, precompute "
+                       "mode (d-table 34 GB in HBM)"),
     "l2048s0b16f32grad": (2048, 0, 0, 16, 1.0, "differentiable FP32 SHT, L=2048, spin 0, batch 16: "
                           "loss = sum |inverse(flm) - target|^2 and its gradient via the adjoint"),
 }
 PRECISION = {"l2048s0b16f32grad": "fp32"}
-REAL = {"l2048realb1", "l1024realb4"}
+REAL = {"l2048realb1", "l1024realb4", "l2048realb1pre"}
+PRECOMPUTE = {"l1024s2b4pre", "l1024s0b1pre", "l2048s0b1pre", "l2048realb1pre"}
 GRAD = {"l2048s0b16f32grad"}
 METRIC = "transforms/sec"
 FP64_LANES_PER_SM_CLK = 2      # DFMA lanes per SM per clock on GB300 (measured 1.88-1.89 at load)
@@ -170,7 +179,11 @@ def run_ours(args, world, rank, local):
     precision = PRECISION.get(args.workload, "fp64")
     grad_mode = args.workload in GRAD
     real = args.workload in REAL
-    plan = Plan(L, spin=spin, N=N, max_batch=B, device=local, precision=precision, real=real)
+    tp0 = time.perf_counter()
+    plan = Plan(L, spin=spin, N=N, max_batch=B, device=local, precision=precision, real=real,
+                precompute=args.workload in PRECOMPUTE)
+    torch.cuda.synchronize(dev)
+    plan_ms = (time.perf_counter() - tp0) * 1e3
     cdt = plan.dtype
     from paper_2311_14670_gb300.multigpu import max_over_ranks, rank_seed, weak_scaling_throughput
     if N:
@@ -310,7 +323,8 @@ def run_ours(args, world, rank, local):
                             else "inverse + forward of every signal in the batch"),
                    "l2": "working set > L2 (coefficients %.0f MB, workspace %.0f MB per step)"
                          % (in_bytes / 1e6, ws.numel() / 1e6),
-                   "parallelism": f"dp{world} (independent batches, no data-path collective)"},
+                   "parallelism": f"dp{world} (independent batches, no data-path collective)",
+                   "plan_ms": round(plan_ms, 1), "plan_device_bytes": plan.device_bytes()},
         "roundtrip_rel_max_err": err,
         "e2e": {"value": round(weak_scaling_throughput(transforms_per_step // world, world, ms_e2e, args.steps), 3),
                 "unit": "transforms/s",

@@ -104,6 +104,25 @@ int s2gb_plan_create(s2gb_plan* out, int L, int spin, int N, int sampling, int p
  */
 int s2gb_plan_create_real(s2gb_plan* out, int L, int sampling, int precision, int max_batch, int device);
 
+/*
+ * Plan with options (bitwise OR of the flags below; other bits: S2GB_EINVAL).  flags = 0 is
+ * s2gb_plan_create; S2GB_PLAN_REAL is s2gb_plan_create_real (spin and N must be 0).
+ *
+ * S2GB_PLAN_PRECOMPUTE: precompute mode (Sec. 4.4's precompute variant).  At plan creation the
+ * Wigner d-functions d^l_{m,n}(theta_t) on the L MW rings are generated by the plan's recursion
+ * and kept in device memory; every transform (and adjoint, order-range and theta-only call) then
+ * reads them instead of recomputing them.  Same results to rounding (|d| < 2^-400 is stored as 0,
+ * as the on-the-fly kernels skip such values).  Memory: 8 bytes x L rings x the (l, m, n) triples
+ * the theta kernels run -- with the +-m pairing of spin-0 and Wigner plans only m >= 0 at n = 0
+ * (L = 1024 spin 0: 4.3 GB; spin 2: 8.6 GB; L = 2048 spin 0: 34 GB; real plans as spin 0);
+ * s2gb_plan_device_bytes includes it.  FP64 plans with L <= 2048 only (else S2GB_EUNSUPPORTED);
+ * S2GB_ENOMEM when the table does not fit.
+ */
+#define S2GB_PLAN_REAL 1u
+#define S2GB_PLAN_PRECOMPUTE 2u
+int s2gb_plan_create_flags(s2gb_plan* out, int L, int spin, int N, int sampling, int precision,
+                           int max_batch, int device, unsigned flags);
+
 /* Free a plan and everything it holds (NULL is ignored).  No call on it may be in flight. */
 void s2gb_plan_destroy(s2gb_plan plan);
 

@@ -24,6 +24,8 @@ S2GB_EWORKSPACE = -6
 S2GB_MW = 0
 S2GB_FP64 = 0
 S2GB_FP32 = 1
+S2GB_PLAN_REAL = 1
+S2GB_PLAN_PRECOMPUTE = 2
 
 _lib = None
 
@@ -47,6 +49,8 @@ def lib() -> ctypes.CDLL:
         L.s2gb_plan_create.restype = i
         L.s2gb_plan_create_real.argtypes = [ctypes.POINTER(vp), i, i, i, i, i]
         L.s2gb_plan_create_real.restype = i
+        L.s2gb_plan_create_flags.argtypes = [ctypes.POINTER(vp), i, i, i, i, i, i, i, ctypes.c_uint]
+        L.s2gb_plan_create_flags.restype = i
         L.s2gb_plan_destroy.argtypes = [vp]
         L.s2gb_plan_destroy.restype = None
         L.s2gb_workspace_bytes.argtypes = [vp, i]
@@ -97,6 +101,14 @@ def plan_create_real(L: int, sampling: int, precision: int, max_batch: int, devi
     h = ctypes.c_void_p()
     _check(lib().s2gb_plan_create_real(ctypes.byref(h), L, sampling, precision, max_batch, device),
            "s2gb_plan_create_real")
+    return h.value
+
+
+def plan_create_flags(L: int, spin: int, N: int, sampling: int, precision: int, max_batch: int,
+                      device: int, flags: int) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().s2gb_plan_create_flags(ctypes.byref(h), L, spin, N, sampling, precision, max_batch, device,
+                                        flags), "s2gb_plan_create_flags")
     return h.value
 
 

@@ -143,6 +143,7 @@ InvArgs inv_args(const Plan& p, const void* flm, void* out, int batch, const dou
   a.flm = flm; a.out = out; a.s_sig = s_sig; a.s_t = s_t; a.s_m = s_m; a.m_mod = m_mod;
   a.nsig = batch; a.nN = p.nN; a.L = p.L; a.coef = p.coef; a.ring = p.ring; a.seed = p.seed;
   a.scale = scale; a.coef32 = p.coef32; a.v32 = p.v32;
+  a.dtab = p.dtab; a.tab_off = p.tab_off; a.live0 = p.live0;
   a.rank0 = 0; a.nrank = p.MR;
   a.mpos = p.real ? 1 : 0; a.flm_ld = p.MR; a.flm_c0 = p.real ? 0 : p.L - 1;
   return a;
@@ -166,6 +167,7 @@ FwdArgs fwd_args(const Plan& p, const void* g, void* flm, int batch, const doubl
   a.nsig = batch; a.nN = p.nN; a.L = p.L; a.coef = p.coef; a.ring = p.ring; a.seed = p.seed;
   a.scale = scale; a.nu = p.nu; a.coef32 = p.coef32; a.v32 = p.v32;
   a.row0 = 0; a.nrows = p.L; a.part = nullptr; a.part_off = 0;
+  a.dtab = p.dtab; a.tab_off = p.tab_off; a.live0 = p.live0;
   a.rank0 = 0; a.nrank = p.MR;
   a.mpos = p.real ? 1 : 0; a.flm_ld = p.MR; a.flm_c0 = p.real ? 0 : p.L - 1;
   return a;
@@ -418,13 +420,14 @@ extern "C" {
 
 namespace {
 int plan_create_impl(s2gb_plan* out, int L, int spin, int N, int sampling, int precision, int max_batch,
-                     int device, bool real) {
+                     int device, bool real, bool precompute = false) {
   if (!out) return S2GB_EINVAL;
   *out = nullptr;
   if (L < 1 || L > 8192 || N < 0 || N > L || max_batch < 1 || sampling != S2GB_MW) return S2GB_EINVAL;
   if (precision != S2GB_FP64 && precision != S2GB_FP32) return S2GB_EINVAL;
   if (N == 0 && (spin <= -L || spin >= L)) return S2GB_EINVAL;
   if (precision == S2GB_FP32 && L > 2048) return S2GB_EUNSUPPORTED;
+  if (precompute && (precision != S2GB_FP64 || L > s2gb::kFwdChunk)) return S2GB_EUNSUPPORTED;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return S2GB_EINVAL;
   s2gb_plan h = new (std::nothrow) s2gb_plan_s;
@@ -433,6 +436,7 @@ int plan_create_impl(s2gb_plan* out, int L, int spin, int N, int sampling, int p
   p.L = L; p.spin = N == 0 ? spin : 0; p.N = N; p.precision = precision; p.max_batch = max_batch;
   p.device = device;
   p.real = real;
+  p.precompute = precompute;
   int rc;
   {
     s2gb::DeviceGuard g(device);
@@ -456,6 +460,16 @@ int s2gb_plan_create(s2gb_plan* out, int L, int spin, int N, int sampling, int p
 
 int s2gb_plan_create_real(s2gb_plan* out, int L, int sampling, int precision, int max_batch, int device) {
   return plan_create_impl(out, L, 0, 0, sampling, precision, max_batch, device, true);
+}
+
+int s2gb_plan_create_flags(s2gb_plan* out, int L, int spin, int N, int sampling, int precision,
+                           int max_batch, int device, unsigned flags) {
+  if (out) *out = nullptr;
+  if (flags & ~(unsigned)(S2GB_PLAN_REAL | S2GB_PLAN_PRECOMPUTE)) return S2GB_EINVAL;
+  const bool real = (flags & S2GB_PLAN_REAL) != 0;
+  if (real && (spin != 0 || N != 0)) return S2GB_EINVAL;
+  return plan_create_impl(out, L, spin, N, sampling, precision, max_batch, device, real,
+                          (flags & S2GB_PLAN_PRECOMPUTE) != 0);
 }
 
 void s2gb_plan_destroy(s2gb_plan plan) {

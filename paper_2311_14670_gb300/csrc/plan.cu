@@ -329,6 +329,10 @@ int make_plan(Plan* p) {
     coef_kernel<<<1024, 256>>>(p->coef, p->n_of, nN, L);
   if (launched() != cudaSuccess) return S2GB_ECUDA;
   if (cudaDeviceSynchronize() != cudaSuccess) return S2GB_ECUDA;
+  if (p->precompute) {
+    if ((rc = build_dtable(p, &bytes))) return rc;
+    p->device_bytes = bytes;
+  }
   if (p->precision == S2GB_FP32) {
     // float32 plans keep the coefficient table rounded once to float, and v per ring
     const size_t n = (size_t)nN * T * L * kCoefPerStep;
@@ -378,6 +382,9 @@ int make_plan(Plan* p) {
 }
 
 void free_plan(Plan* p) {
+  cudaFree(p->dtab);
+  cudaFree(p->tab_off);
+  cudaFree(p->live0);
   cudaFree(p->coef);
   cudaFree(p->coef32);
   cudaFree(p->v32);

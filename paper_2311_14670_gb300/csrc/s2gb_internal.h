@@ -75,6 +75,14 @@ struct Plan {
   int* n_of = nullptr;         // [nN] n for each n index
   size_t device_bytes = 0;
 
+  // precompute mode (FP64, L <= kFwdChunk): d^l_{m,n}(theta_t) of every (n, m) theta kernels run,
+  // rows l = l0 .. L-1 of L doubles (t fastest), zero where the on-the-fly kernels would skip a
+  // chain as dead (|d| < 2^-kLiveThr)
+  bool precompute = false;
+  double* dtab = nullptr;
+  size_t* tab_off = nullptr;   // [nN][T] offset (doubles) of the rows of (n, m), kNoTable if none
+  int* live0 = nullptr;        // [nN][T][ceil(L/32)] first degree with a live chain in 32 rings
+
   // cuFFT plans: index 0 = one signal, 1 = max_batch signals (rows of the whole batch)
   cufftHandle fft_phi[2] = {0, 0};   // length T along rows of length T, S*L rows (real: R2C)
   cufftHandle fft_phi_c2r[2] = {0, 0};   // real plans: the inverse direction (C2R)
@@ -104,6 +112,9 @@ struct InvArgs {
   const double* scale;  // [nN][L]
   const float* coef32;  // FP32 plans
   const float* v32;
+  const double* dtab;   // precompute mode (else null): the d table, its offsets, live starts
+  const size_t* tab_off;
+  const int* live0;
   int rank0;            // orders of this launch: m-ranks [rank0, rank0 + nrank) (m_of_rank order
   int nrank;            // 0, -1, 1, -2, 2, ...: |m| in [lo, hi) is ranks [max(0, 2lo-1), 2hi-1))
   int mpos;             // 1: rank r is order m = r (real-signal plans: m >= 0 only)
@@ -127,6 +138,9 @@ struct FwdArgs {
   const double* nu;
   const float* coef32;  // FP32 plans
   const float* v32;
+  const double* dtab;   // precompute mode (as in InvArgs)
+  const size_t* tab_off;
+  const int* live0;
   int row0;             // ring range of this launch: [row0, row0 + nrows)
   int nrows;
   void* part;           // non-null: write this launch's partial result at part + part_off
@@ -150,6 +164,15 @@ inline void mrange_ranks(int lo, int hi, int& rank0, int& nrank) {
 cudaError_t launched();
 
 cudaError_t launch_theta_inverse(const Plan& p, const InvArgs& a, cudaStream_t st);
+// precompute mode (theta_precompute.cu): table construction at plan creation, and the theta stages
+// reading it
+constexpr size_t kNoTable = ~(size_t)0;
+// Pairing (m, n) with (-m, -n) needs the set of n to be symmetric: spin-0 sphere plans and Wigner
+// (real-signal plans have the orders m >= 0 only and need no partner).
+inline bool paired_plan(const Plan& p) { return !p.real && (p.wigner || p.spin == 0); }
+int build_dtable(Plan* p, size_t* bytes);
+cudaError_t launch_theta_inverse_pre(const Plan& p, const InvArgs& a, cudaStream_t st);
+cudaError_t launch_theta_forward_pre(const Plan& p, const FwdArgs& a, cudaStream_t st);
 cudaError_t launch_theta_forward(const Plan& p, const FwdArgs& a, cudaStream_t st);
 cudaError_t launch_theta_inverse_f32(const Plan& p, const InvArgs& a, cudaStream_t st);
 cudaError_t launch_theta_forward_f32(const Plan& p, const FwdArgs& a, cudaStream_t st);

@@ -64,6 +64,68 @@ __device__ __forceinline__ void renorm(double& x, double& y, int& E) {
   }
 }
 
+// Coefficients of one step of the block-normalised recursion (layout of plan.cu's coefn_kernel).
+struct StepN {
+  double Ap, Knp, Ksp, g, gn, App, Kdnp, Kdsp, en, ig;
+};
+
+__device__ __forceinline__ StepN stepn_at(const double* c) {
+  return {c[0], c[1], c[2], c[3], c[4], c[5], c[6], c[7], c[8], c[9]};
+}
+
+// One step of the block-normalised recursion (2 FP64 instructions plain, 3 in the difference
+// form); x, y are (u^j, u^{j-1}) plain or (d^j, ehat^j) in the difference form.
+template <bool DIFF>
+__device__ __forceinline__ void stepn(double& x, double& y, double v, unsigned nmask, bool north, const StepN& c) {
+  if (!DIFF) {
+    const double P = fma(flip_sign(c.Ap, nmask), v, north ? c.Knp : c.Ksp);
+    const double xn = fma(P, x, -y);
+    y = x;
+    x = xn;
+  } else {
+    const unsigned smask = nmask ^ 0x80000000u;          // sign of sigma: + north, - south
+    const double Q = fma(flip_sign(c.App, nmask), v, north ? c.Kdnp : c.Kdsp);
+    const double en = fma(Q, x, flip_sign(y, smask));     // Q' d + sigma ehat
+    x = fma(c.en, en, flip_sign(x, smask));                // sigma d + eta ehat'
+    y = en;
+  }
+}
+
+// End of a normalisation block (after the step j -> j+1): back to (d^{j+1}, d^j) / (d^{j+1}, e^{j+1}).
+template <bool DIFF>
+__device__ __forceinline__ void unnormalise(double& x, double& y, const StepN& c) {
+  if (!DIFF) {
+    x *= c.gn;
+    y *= c.g;
+  } else {
+    y *= c.en;
+  }
+}
+
+// Signal slots of a CTA.  Slot b < NB is signal sig0 + b at (m, n); with pairing (PAIR), slot
+// NB + b is the same signal at (-m, -n), whose d-functions are d^l_{-m,-n} = (-1)^{m-n} d^l_{m,n}
+// (Sec. 3.3 symmetry): the partner column reuses the recursion of (m, n), scaled by that sign.
+struct Slot {
+  long long sig_off;   // signal offset (sig * nN + ni) or -1 if inactive
+  int mi;              // column index m + L - 1 of the slot
+  int m;
+  double sign;
+};
+
+template <int NB, bool PAIR>
+__device__ __forceinline__ Slot slot_of(int b, int sig0, int nsig, int nN, int ni, int m, int n, int L) {
+  Slot sl;
+  const bool partner = PAIR && b >= NB;
+  const int sig = sig0 + (partner ? b - NB : b);
+  const bool active = sig < nsig && !(partner && m == 0 && n == 0);
+  const int nis = partner ? (nN - 1 - ni) : ni;
+  sl.m = partner ? -m : m;
+  sl.mi = sl.m + L - 1;
+  sl.sig_off = active ? (long long)sig * nN + nis : -1;
+  sl.sign = (partner && ((m - n) & 1)) ? -1.0 : 1.0;
+  return sl;
+}
+
 struct StepCoef {
   double A, C, Kn, Ks, Kdn, Kds;
 };

@@ -26,7 +26,8 @@ class Plan:
     """A transform plan (``s2gb_plan_create``) plus a per-batch-size workspace cache."""
 
     def __init__(self, L: int, spin: int = 0, N: int = 0, precision: str = "fp64", max_batch: int = 1,
-                 device: int | torch.device | None = None, sampling: str = "mw", real: bool = False):
+                 device: int | torch.device | None = None, sampling: str = "mw", real: bool = False,
+                 precompute: bool = False):
         if sampling != "mw":
             raise ValueError("only MW sampling is implemented")
         if precision not in _PRECISIONS:
@@ -39,14 +40,12 @@ class Plan:
         self.device = torch.device("cuda", int(device))
         self.dtype = _PRECISIONS[precision][1]          # coefficients (and complex signals)
         self.real = bool(real)
-        if self.real:
-            if self.spin != 0 or self.N != 0:
-                raise ValueError("real-signal plans are spin-0 sphere transforms (spin = 0, N = 0)")
-            self._h = nat.plan_create_real(self.L, nat.S2GB_MW, _PRECISIONS[precision][0], self.max_batch,
-                                           int(device))
-        else:
-            self._h = nat.plan_create(self.L, self.spin, self.N, nat.S2GB_MW, _PRECISIONS[precision][0],
-                                      self.max_batch, int(device))
+        self.precompute = bool(precompute)
+        if self.real and (self.spin != 0 or self.N != 0):
+            raise ValueError("real-signal plans are spin-0 sphere transforms (spin = 0, N = 0)")
+        flags = (nat.S2GB_PLAN_REAL if self.real else 0) | (nat.S2GB_PLAN_PRECOMPUTE if self.precompute else 0)
+        self._h = nat.plan_create_flags(self.L, self.spin, self.N, nat.S2GB_MW, _PRECISIONS[precision][0],
+                                        self.max_batch, int(device), flags)
         self.signal_dtype = _REAL_OF[self.dtype] if self.real else self.dtype
         self._ws = {}
         self._lock = threading.Lock()

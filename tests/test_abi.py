@@ -64,3 +64,19 @@ def test_kernel_launch_counter_starts_at_zero_without_gpu(libpath):
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         assert n == 0                       # nothing in the CPU suite launches a kernel
+
+
+def test_plan_flags_are_checked_before_any_device_work(libpath):
+    from paper_2311_14670_gb300 import _native as nat
+    lib = nat.lib()
+    h = ctypes.c_void_p(1)
+    # unknown flag bits, a real plan with spin or N, precompute in FP32 or above L = 2048
+    assert lib.s2gb_plan_create_flags(ctypes.byref(h), 8, 0, 0, 0, 0, 1, 0, 4) == nat.S2GB_EINVAL
+    assert h.value is None
+    assert lib.s2gb_plan_create_flags(ctypes.byref(h), 8, 1, 0, 0, 0, 1, 0, nat.S2GB_PLAN_REAL) == nat.S2GB_EINVAL
+    assert lib.s2gb_plan_create_flags(ctypes.byref(h), 8, 0, 2, 0, 0, 1, 0, nat.S2GB_PLAN_REAL) == nat.S2GB_EINVAL
+    assert lib.s2gb_plan_create_flags(ctypes.byref(h), 8, 0, 0, 0, nat.S2GB_FP32, 1, 0,
+                                      nat.S2GB_PLAN_PRECOMPUTE) == nat.S2GB_EUNSUPPORTED
+    assert lib.s2gb_plan_create_flags(ctypes.byref(h), 4096, 0, 0, 0, 0, 1, 0,
+                                      nat.S2GB_PLAN_PRECOMPUTE) == nat.S2GB_EUNSUPPORTED
+    assert h.value is None

@@ -1,4 +1,5 @@
-"""McEwen-Wiaux (MW) sampling and quadrature for the oracle (test infrastructure only).
+"""Sampling schemes and quadratures of the oracle (test infrastructure only): McEwen-Wiaux (MW),
+its symmetric variant (MWSS) and Driscoll-Healy (DH).
 
 Sec. 4.2.2 of the paper:
 * MW positions: theta_t = (2t+1) pi / (2L-1), t = 0..L-1;  phi_p = 2 pi p / (2L-1), p = 0..2L-2.
@@ -81,3 +82,53 @@ def mw_theta_weights(Lp: int) -> np.ndarray:
         q[t] = (w[t] + zeta * w[2 * Lp - 2 - t]) / T      # reflect: theta_{2L'-2-t} = 2 pi - theta_t
     assert np.max(np.abs(q.imag)) < 1e-12 * np.max(np.abs(q.real))
     return q.real.copy()
+
+
+# ----------------------------------------------------------------------------- MWSS (Sec. 4.2.2)
+# theta_t = 2 pi t / (2L), t = 0..L (both poles are rings); phi_p = 2 pi p / (2L), p < 2L.  The same
+# torus construction as MW with T = 2L torus points: the reflection of theta_t is theta_{2L-t} and
+# the rings t = 0 and t = L are their own reflections (zeta = 0 there).  Readings as for MW.
+def mwss_thetas(L: int, dtype=np.longdouble) -> np.ndarray:
+    """MWSS colatitudes theta_t = pi t / L, t = 0..L (exactly 0 and pi at the ends)."""
+    th = np.arange(L + 1).astype(np.longdouble) * PI_LD / np.longdouble(L)
+    th[0], th[-1] = 0, PI_LD
+    return th.astype(dtype)
+
+
+def mwss_phis(L: int) -> np.ndarray:
+    """MWSS longitudes phi_p = 2 pi p / (2L), p < 2L (extended precision)."""
+    return np.arange(2 * L).astype(np.longdouble) * PI_LD / np.longdouble(L)
+
+
+def mwss_theta_weights(Lp: int) -> np.ndarray:
+    """Theta quadrature weights q_t, t = 0..Lp, of the MWSS sampling theorem at bandlimit Lp:
+    sum_t q_t g(theta_t) = int_0^pi g sin(theta) dtheta for every g whose torus extension is even
+    about pi and has frequencies |k| <= Lp-1 (trapezoid on the 2Lp torus points, exact for the
+    product of g with the degree-(Lp-1) truncation of the weight function)."""
+    T = 2 * Lp
+    th = (np.arange(T).astype(np.longdouble) * PI_LD / np.longdouble(Lp)).astype(np.float64)
+    k = np.arange(-(Lp - 1), Lp)
+    w = np.exp(-1j * np.outer(th, k)) @ w_hat(k)
+    q = np.empty(Lp + 1, dtype=np.complex128)
+    for t in range(Lp + 1):
+        zeta = 0.0 if t in (0, Lp) else 1.0
+        q[t] = (w[t] + zeta * w[(T - t) % T]) / T
+    assert np.max(np.abs(q.imag)) < 1e-12 * np.max(np.abs(q.real))
+    return q.real.copy()
+
+
+# ----------------------------------------------------------------------------- DH (Sec. 4.2.1)
+def dh_thetas(L: int, dtype=np.longdouble) -> np.ndarray:
+    """DH colatitudes theta_t = (2t+1) pi / (4L), t < 2L."""
+    t = np.arange(2 * L)
+    return ((2 * t + 1).astype(np.longdouble) * PI_LD / np.longdouble(4 * L)).astype(dtype)
+
+
+def dh_theta_weights(L: int) -> np.ndarray:
+    """The theta part of the DH weights, (2/L) sin(theta_t) sum_{k<L} sin((2k+1) theta_t)/(2k+1),
+    t < 2L (the paper's q(theta, phi) is this times the phi step 2 pi/(2L-1)); evaluated in
+    extended precision."""
+    th = dh_thetas(L)
+    k = np.arange(L).astype(np.longdouble)
+    S = (np.sin(np.outer(th, 2 * k + 1)) / (2 * k + 1)).sum(axis=1)
+    return (np.longdouble(2) / L * np.sin(th) * S).astype(np.float64)

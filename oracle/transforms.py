@@ -26,7 +26,8 @@ from __future__ import annotations
 
 import numpy as np
 
-from .sampling import mw_theta_weights, mw_thetas
+from .sampling import (dh_theta_weights, dh_thetas, mw_theta_weights, mw_thetas, mwss_theta_weights,
+                       mwss_thetas)
 from .wigner import PI_LD, wigner_d_table
 
 _CHUNK_BYTES = 256 << 20
@@ -186,6 +187,97 @@ def adjoint_forward(flm_bar: np.ndarray, L: int, spin: int) -> np.ndarray:
     return Fbar @ phi_dft_matrix(L, -1).conj().T                            # phi-DFT^H
 
 
+# ----------------------------------------------------------------------------- MWSS and DH (Sec. 4.2)
+# Signals on the MWSS grid are f[..., t, p] with t = 0..L (L+1 rings, both poles) and p < 2L; on the
+# DH grid t < 2L and p < 2L-1.  Coefficients as for MW.
+SAMPLINGS = ("mw", "mwss", "dh")
+
+
+def sampling_shape(L: int, sampling: str) -> tuple:
+    """(rings, phi samples) of a sampling scheme."""
+    return {"mw": (L, 2 * L - 1), "mwss": (L + 1, 2 * L), "dh": (2 * L, 2 * L - 1)}[sampling]
+
+
+def sampling_thetas(L: int, sampling: str):
+    return {"mw": mw_thetas, "mwss": mwss_thetas, "dh": dh_thetas}[sampling](L)
+
+
+def _phi_matrix(L: int, Tp: int, sign: int) -> np.ndarray:
+    """E[p, j] = exp(sign i m_j phi_p), m_j = j - (L-1), phi_p = 2 pi p / Tp."""
+    p = np.arange(Tp)[:, None]
+    m = np.arange(-(L - 1), L)[None, :]
+    return _expi_pi(sign * 2 * p * m, Tp)
+
+
+def inverse_s(flm: np.ndarray, L: int, spin: int, sampling: str = "mw", rings=None) -> np.ndarray:
+    """Inverse spin-s SHT on any of the samplings: the direct sums of Eqs. disc_ish_expanded and
+    disc_ish_fft at that grid's theta_t and phi_p."""
+    if sampling == "mw":
+        return inverse(flm, L, spin, rings)
+    th = sampling_thetas(L, sampling)
+    if rings is not None:
+        th = th[np.asarray(rings)]
+    ft = _theta_inverse(np.asarray(flm, dtype=np.complex128), L, -spin, ell_factor(L, spin), th)
+    return ft @ _phi_matrix(L, sampling_shape(L, sampling)[1], +1).T
+
+
+def _mwss_extend(F: np.ndarray, L: int, n: int) -> np.ndarray:
+    """MWSS torus extension G[..., t', m], t' < 2L: G[t'] = F[t'] (t' <= L), G[2L-t] = sigma F[t]
+    (0 < t < L), and at the two self-reflected rings (the poles) the average (1 + sigma)/2 F, as for
+    MW's theta = pi ring (same reading)."""
+    m = np.arange(-(L - 1), L)
+    sigma = (-1.0) ** ((m - n) % 2)
+    G = np.zeros(F.shape[:-2] + (2 * L, F.shape[-1]), dtype=np.complex128)
+    G[..., :L + 1, :] = F
+    G[..., 0, :] = F[..., 0, :] * (1 + sigma) / 2
+    G[..., L, :] = F[..., L, :] * (1 + sigma) / 2
+    G[..., L + 1:, :] = (F[..., 1:L, :] * sigma)[..., ::-1, :]
+    return G
+
+
+def forward_s(f: np.ndarray, L: int, spin: int, sampling: str = "mw", ells=None) -> np.ndarray:
+    """Forward spin-s SHT on any of the samplings.
+    DH: the quadrature sum with the explicit DH weights (Sec. 4.2.1).
+    MWSS: the route of Sec. 4.2.2 -- torus extension, Fourier coefficients |k| <= L-1 on the 2L
+    torus points, evaluation on the MWSS grid of bandlimit 2L, MWSS weights at bandlimit 2L."""
+    if sampling == "mw":
+        return forward(f, L, spin, ells)
+    if ells is None:
+        ells = np.arange(L)
+    ells = np.asarray(ells)
+    n = -spin
+    Tp = sampling_shape(L, sampling)[1]
+    F = np.asarray(f, dtype=np.complex128) @ _phi_matrix(L, Tp, -1)          # [t, m]
+    qphi = 2 * np.pi / Tp
+    if sampling == "dh":
+        th = dh_thetas(L)
+        W = F * (dh_theta_weights(L) * qphi)[:, None]
+    else:
+        G = _mwss_extend(F, L, n)                                            # [t', m], t' < 2L
+        k = np.arange(-(L - 1), L)
+        coef = _expi_pi(-np.outer(k, 2 * np.arange(2 * L)), 2 * L) / (2 * L)  # e^{-ik pi t'/L}/2L
+        u = np.arange(2 * L + 1)
+        up = _expi_pi(np.outer(u, k), 2 * L)                                 # e^{+ik pi u/(2L)}
+        Gu = up @ (coef @ G)
+        th = mwss_thetas(2 * L)
+        W = Gu * (mwss_theta_weights(2 * L) * qphi)[:, None]
+    D = wigner_d_table(ells, n, th)                                          # [i, m', u]
+    M = int(ells.max())
+    D = D[:, M - (L - 1):M + L, :] if M >= L - 1 else np.pad(D, ((0, 0), (L - 1 - M, L - 1 - M), (0, 0)))
+    out = np.einsum("...um,imu->...im", W, D) * ell_factor(L, spin)[ells][:, None]
+    return np.where(coeff_mask(L, n)[ells], out, 0)
+
+
+def adjoint_dense(fn, x_shape, y: np.ndarray) -> np.ndarray:
+    """A^H y for the linear map x -> fn(x) (complex-linear), by building A column by column from
+    unit vectors: the definition of the adjoint, for small sizes."""
+    size = int(np.prod(x_shape))
+    cols = [np.asarray(fn(np.eye(1, size, i, dtype=np.complex128).reshape(x_shape))).ravel()
+            for i in range(size)]
+    A = np.stack(cols, axis=1)
+    return (A.conj().T @ np.asarray(y).ravel()).reshape(x_shape)
+
+
 # ----------------------------------------------------------------------------- real signals (Sec. 2.2)
 # A real spin-0 signal has Hermitian coefficients flm_{l,-m} = (-1)^m conj(flm_{lm}) (Sec. 2.2), so
 # the orders m >= 0 carry everything: flm_pos[..., l, m] for 0 <= m < L.  The real transforms are
@@ -202,14 +294,14 @@ def hermitian_expand(flm_pos: np.ndarray, L: int) -> np.ndarray:
     return np.where(coeff_mask(L, 0), out, 0)
 
 
-def inverse_real(flm_pos: np.ndarray, L: int) -> np.ndarray:
+def inverse_real(flm_pos: np.ndarray, L: int, sampling: str = "mw") -> np.ndarray:
     """Real signal f[..., t, p] with coefficients hermitian_expand(flm_pos)."""
-    return inverse(hermitian_expand(flm_pos, L), L, 0).real
+    return inverse_s(hermitian_expand(flm_pos, L), L, 0, sampling).real
 
 
-def forward_real(f: np.ndarray, L: int) -> np.ndarray:
+def forward_real(f: np.ndarray, L: int, sampling: str = "mw") -> np.ndarray:
     """Orders m >= 0 of the coefficients of a real signal: flm_pos[..., l, m]."""
-    return forward(np.asarray(f, dtype=np.float64).astype(np.complex128), L, 0)[..., L - 1:]
+    return forward_s(np.asarray(f, dtype=np.float64).astype(np.complex128), L, 0, sampling)[..., L - 1:]
 
 
 def adjoint_inverse_real(fbar: np.ndarray, L: int) -> np.ndarray:

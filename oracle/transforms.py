@@ -235,17 +235,13 @@ def _mwss_extend(F: np.ndarray, L: int, n: int) -> np.ndarray:
     return G
 
 
-def forward_s(f: np.ndarray, L: int, spin: int, sampling: str = "mw", ells=None) -> np.ndarray:
-    """Forward spin-s SHT on any of the samplings.
-    DH: the quadrature sum with the explicit DH weights (Sec. 4.2.1).
-    MWSS: the route of Sec. 4.2.2 -- torus extension, Fourier coefficients |k| <= L-1 on the 2L
-    torus points, evaluation on the MWSS grid of bandlimit 2L, MWSS weights at bandlimit 2L."""
-    if sampling == "mw":
-        return forward(f, L, spin, ells)
-    if ells is None:
-        ells = np.arange(L)
+def _forward_sampled(f: np.ndarray, L: int, n: int, scale: np.ndarray, sampling: str, ells) -> np.ndarray:
+    """flm[..., i, m] = scale_l int f(theta, phi) d^l_{m,n}(theta) e^{-i m phi} sin(theta), l = ells[i],
+    on the MWSS or DH grid (f[..., t, p]): the phi DFT, then the theta quadrature of the sampling.
+    DH: the explicit DH weights (Sec. 4.2.1).  MWSS: the route of Sec. 4.2.2 -- torus extension,
+    Fourier coefficients |k| <= L-1 on the 2L torus points, evaluation on the MWSS grid of
+    bandlimit 2L, MWSS weights at bandlimit 2L."""
     ells = np.asarray(ells)
-    n = -spin
     Tp = sampling_shape(L, sampling)[1]
     F = np.asarray(f, dtype=np.complex128) @ _phi_matrix(L, Tp, -1)          # [t, m]
     qphi = 2 * np.pi / Tp
@@ -264,8 +260,18 @@ def forward_s(f: np.ndarray, L: int, spin: int, sampling: str = "mw", ells=None)
     D = wigner_d_table(ells, n, th)                                          # [i, m', u]
     M = int(ells.max())
     D = D[:, M - (L - 1):M + L, :] if M >= L - 1 else np.pad(D, ((0, 0), (L - 1 - M, L - 1 - M), (0, 0)))
-    out = np.einsum("...um,imu->...im", W, D) * ell_factor(L, spin)[ells][:, None]
+    out = np.einsum("...um,imu->...im", W, D) * scale[ells][:, None]
     return np.where(coeff_mask(L, n)[ells], out, 0)
+
+
+def forward_s(f: np.ndarray, L: int, spin: int, sampling: str = "mw", ells=None) -> np.ndarray:
+    """Forward spin-s SHT on any of the samplings (MW: ``forward``; MWSS, DH: _forward_sampled
+    with d^l_{m,-s} and c_l)."""
+    if sampling == "mw":
+        return forward(f, L, spin, ells)
+    if ells is None:
+        ells = np.arange(L)
+    return _forward_sampled(f, L, -spin, ell_factor(L, spin), sampling, ells)
 
 
 def adjoint_dense(fn, x_shape, y: np.ndarray) -> np.ndarray:
@@ -358,3 +364,31 @@ def wigner_forward(f: np.ndarray, L: int, N: int, ells=None) -> np.ndarray:
         G = _extend(_phi_forward(fn[..., j, :, :], L), L, n)
         out.append(_theta_forward_upsampled(up @ (coef @ G), L, n, ones, ells))
     return np.stack(out, axis=-3)
+
+
+def wigner_inverse_s(flmn: np.ndarray, L: int, N: int, sampling: str = "mw") -> np.ndarray:
+    """Inverse Wigner transform on any of the samplings: for each n the spin-(-n) inverse theta
+    and phi sums at that grid's (beta_t, alpha_p) with the factor (2l+1)/(8 pi^2), then the sum
+    over n against e^{i n gamma_k}."""
+    if sampling == "mw":
+        return wigner_inverse(flmn, L, N)
+    flmn = np.asarray(flmn, dtype=np.complex128)
+    th = sampling_thetas(L, sampling)
+    E = _phi_matrix(L, sampling_shape(L, sampling)[1], +1)
+    scale = (2 * np.arange(L) + 1) / (8 * np.pi ** 2)
+    fn = np.stack([_theta_inverse(flmn[..., j, :, :], L, n, scale, th) @ E.T
+                   for j, n in enumerate(range(-(N - 1), N))], axis=-3)
+    return np.einsum("kn,...ntp->...ktp", _gamma_matrix(N, +1), fn)
+
+
+def wigner_forward_s(f: np.ndarray, L: int, N: int, sampling: str = "mw") -> np.ndarray:
+    """Forward Wigner transform on any of the samplings: the gamma DFT (times 2 pi/(2N-1)), then
+    for each n the theta quadrature of the sampling with d^l_{m,n} and factor 1."""
+    if sampling == "mw":
+        return wigner_forward(f, L, N)
+    f = np.asarray(f, dtype=np.complex128)
+    qgam = 2 * np.pi / (2 * N - 1)
+    fn = np.einsum("kn,...ktp->...ntp", _gamma_matrix(N, -1), f) * qgam
+    ones = np.ones(L)
+    return np.stack([_forward_sampled(fn[..., j, :, :], L, n, ones, sampling, np.arange(L))
+                     for j, n in enumerate(range(-(N - 1), N))], axis=-3)

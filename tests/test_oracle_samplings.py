@@ -74,3 +74,30 @@ def test_dense_adjoint_equals_the_mw_adjoints():
     c = synth.flm_gaussian(L, spin, 1, seed=2)[0]
     got = OT.adjoint_dense(lambda x: OT.forward(x, L, spin), (L, 2 * L - 1), c)
     assert np.abs(got - OT.adjoint_forward(c, L, spin)).max() <= 1e-13
+
+
+@pytest.mark.parametrize("sampling", ["mwss", "dh"])
+@pytest.mark.parametrize("L,N", [(1, 1), (3, 2), (6, 3), (9, 2)])
+def test_wigner_round_trip_and_agreement_with_mw(sampling, L, N):
+    """Bandlimited SO(3) signals: forward(inverse(a)) = a on every sampling, and the Wigner
+    coefficients of the same function sampled on MW and on this grid agree."""
+    a = synth.flmn_gaussian(L, N, 2, seed=L * N + 5)
+    f = OT.wigner_inverse_s(a, L, N, sampling)
+    R, P = OT.sampling_shape(L, sampling)
+    assert f.shape == (2, 2 * N - 1, R, P)
+    b = OT.wigner_forward_s(f, L, N, sampling)
+    assert np.abs(b - a).max() <= 1e-13 * np.abs(a).max()
+    assert np.abs(b - OT.wigner_forward(OT.wigner_inverse(a, L, N), L, N)).max() <= 1e-13 * np.abs(a).max()
+
+
+@pytest.mark.parametrize("sampling", ["mwss", "dh"])
+def test_wigner_n1_is_the_scaled_spin0_transform(sampling):
+    """N = 1: the Wigner inverse is the spin-0 inverse with (2l+1)/(8 pi^2) in place of
+    sqrt((2l+1)/(4 pi)) (Sec. 2.3: D^l_{m0} is proportional to Y_lm), and it is constant in gamma."""
+    L = 7
+    a = synth.flmn_gaussian(L, 1, 1, seed=3)[0, 0]                       # [l, m]
+    ell = np.arange(L)
+    ratio = ((2 * ell + 1) / (8 * np.pi ** 2)) / np.sqrt((2 * ell + 1) / (4 * np.pi))
+    f_w = OT.wigner_inverse_s(a[None], L, 1, sampling)[0]
+    f_s = OT.inverse_s(a * ratio[:, None], L, 0, sampling)
+    assert np.abs(f_w - f_s).max() <= 1e-14 * np.abs(f_s).max()

@@ -56,11 +56,18 @@ WORKLOADS = {
                        "mode (d-table 34 GB in HBM)"),
     "l2048s0b16f32grad": (2048, 0, 0, 16, 1.0, "differentiable FP32 SHT, L=2048, spin 0, batch 16: "
                           "loss = sum |inverse(flm) - target|^2 and its gradient via the adjoint"),
+    "l1024s0b1dh": (1024, 0, 0, 1, 0.0, "spin-0 SHT round trip, L=1024, DH 2048x2047, batch 1, FP64"),
+    "l2048s0b1dh": (2048, 0, 0, 1, 0.0, "spin-0 SHT round trip, L=2048, DH 4096x4095, batch 1, FP64"),
+    "l1024s0b1mwss": (1024, 0, 0, 1, 0.0, "spin-0 SHT round trip, L=1024, MWSS 1025x2048, batch 1, FP64"),
+    "l2048s0b1mwss": (2048, 0, 0, 1, 0.0, "spin-0 SHT round trip, L=2048, MWSS 2049x4096, batch 1, FP64"),
+    "l1024s2b4dh": (1024, 2, 0, 4, 1.0, "spin-2 SHT round trip, L=1024, DH 2048x2047, batch 4, FP64"),
 }
 PRECISION = {"l2048s0b16f32grad": "fp32"}
 REAL = {"l2048realb1", "l1024realb4", "l2048realb1pre"}
 PRECOMPUTE = {"l1024s2b4pre", "l1024s0b1pre", "l2048s0b1pre", "l2048realb1pre"}
 GRAD = {"l2048s0b16f32grad"}
+SAMPLING = {"l1024s0b1dh": "dh", "l2048s0b1dh": "dh", "l1024s0b1mwss": "mwss", "l2048s0b1mwss": "mwss",
+            "l1024s2b4dh": "dh"}
 METRIC = "transforms/sec"
 FP64_LANES_PER_SM_CLK = 2      # DFMA lanes per SM per clock on GB300 (measured 1.88-1.89 at load)
 FP32_LANES_PER_SM_CLK = 128    # FFMA lanes per SM per clock (measured 118.5 at load)
@@ -180,8 +187,9 @@ def run_ours(args, world, rank, local):
     grad_mode = args.workload in GRAD
     real = args.workload in REAL
     tp0 = time.perf_counter()
+    sampling = SAMPLING.get(args.workload, "mw")
     plan = Plan(L, spin=spin, N=N, max_batch=B, device=local, precision=precision, real=real,
-                precompute=args.workload in PRECOMPUTE)
+                precompute=args.workload in PRECOMPUTE, sampling=sampling)
     torch.cuda.synchronize(dev)
     plan_ms = (time.perf_counter() - tp0) * 1e3
     cdt = plan.dtype
@@ -268,12 +276,13 @@ def run_ours(args, world, rank, local):
     # the theta-stage kernels alone, on the launch stream, same workload
     kern = {}
     if not N:
-        g = torch.from_numpy(synth.signal_gaussian((B, L if real else 2 * L - 1, L), seed=77)).to(dev).to(cdt)
-        ft = torch.empty(plan.coef_shape(B), dtype=cdt, device=dev)
+        R = plan.R
+        g = torch.from_numpy(synth.signal_gaussian((B, L if real else 2 * L - 1, R), seed=77)).to(dev).to(cdt)
+        ft = torch.empty(plan.spectra_shape(B), dtype=cdt, device=dev)
         fl = torch.empty(plan.coef_shape(B), dtype=cdt, device=dev)
         xd_ = x.detach()
         stages = [("theta_inverse", lambda: plan.inverse_theta(xd_, out=ft))]
-        if L <= 2048:    # above, the forward theta stage runs in ring chunks inside forward() only
+        if R <= 2048:    # above, the forward theta stage runs in ring chunks inside forward() only
             stages.append(("theta_forward", lambda: plan.forward_theta(g, out=fl)))
         for name, fn in stages:
             fn()
@@ -286,7 +295,7 @@ def run_ours(args, world, rank, local):
             b.record(stream)
             torch.cuda.synchronize(dev)
             kms = a.elapsed_time(b) / reps
-            flops = algorithmic_flops(L, n_list, L, B, real)
+            flops = algorithmic_flops(L, n_list, R, B, real)
             kern[name] = {"ms": kms, "flops": flops, "tflops": flops / (kms * 1e-3) / 1e12}
 
     ms, ms_e2e = max_over_ranks([ms, ms_e2e], device=dev)
@@ -318,7 +327,7 @@ def run_ours(args, world, rank, local):
         "dtype": "f64" if precision == "fp64" else "f32 (f64 starting values)",
         "data": "synthetic (seeded complex Gaussian coefficients)",
         "config": {"workload": args.workload, "description": desc, "L": L, "spin": spin, "N": N,
-                   "batch_per_gpu": B, "transforms_per_step": transforms_per_step,
+                   "sampling": sampling, "batch_per_gpu": B, "transforms_per_step": transforms_per_step,
                    "step": ("loss forward (inverse) + backward (adjoint inverse) of the batch" if grad_mode
                             else "inverse + forward of every signal in the batch"),
                    "l2": "working set > L2 (coefficients %.0f MB, workspace %.0f MB per step)"
@@ -335,7 +344,8 @@ def run_ours(args, world, rank, local):
         "clocks": {k: ck[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
     }
     if not args.no_cpu_baseline and world == 1 and not grad_mode:
-        out["cpu_baseline"] = cpu_baseline(args.workload, rings=args.cpu_rings)
+        out["cpu_baseline"] = (cpu_baseline_sampled(args.workload, sampling, rings=args.cpu_rings)
+                               if sampling != "mw" else cpu_baseline(args.workload, rings=args.cpu_rings))
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
@@ -446,17 +456,82 @@ def cpu_baseline(workload: str, rings: int = 8) -> dict:
             "seconds_full_round_trip_est": round(total, 1)}
 
 
+def cpu_baseline_sampled(workload: str, sampling: str, rings: int = 8) -> dict:
+    """cpu_baseline for the MWSS and DH workloads (spin-s sphere transforms): the oracle's inverse
+    timed per ring, its forward phi DFT (and, on MWSS, theta upsampling) per order and its
+    quadrature per degree, each on two slice sizes and extrapolated as overhead + linear cost."""
+    from oracle import transforms as OT
+    from paper_2311_14670_gb300 import synth
+
+    L, spin, N, B, ellp, _ = WORKLOADS[workload]
+    R, P = OT.sampling_shape(L, sampling)
+    T = 2 * L - 1
+    coef = synth.flm_gaussian(L, spin, B, seed=1, ell_power=ellp)
+    f = synth.signal_gaussian((B, R, P), seed=2)
+    k = max(4, min(L, rings))
+    k2 = k // 2
+
+    def fit(fn, full):
+        t0 = time.perf_counter()
+        fn(k2)
+        ta = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        fn(k)
+        tb = time.perf_counter() - t0
+        b = max(0.0, (tb - ta) / (k - k2))
+        return max(0.0, tb - b * k) + b * full
+
+    t_start = time.perf_counter()
+    scale = OT.ell_factor(L, spin)
+
+    def inv(j):                                                # inverse: per ring
+        OT.inverse_s(coef, L, spin, sampling, rings=np.linspace(0, R - 1, j).astype(int))
+
+    E = OT._phi_matrix(L, P, -1)
+    up = cm = None
+    if sampling == "mwss":
+        kk = np.arange(-(L - 1), L)
+        cm = OT._expi_pi(-np.outer(kk, 2 * np.arange(2 * L)), 2 * L) / (2 * L)
+        up = OT._expi_pi(np.outer(np.arange(2 * L + 1), kk), 2 * L)
+
+    def dft(j):                                                # phi DFT (+ upsampling): per order
+        F = f @ E[:, np.linspace(0, T - 1, j).astype(int)]
+        if up is not None:
+            up @ (cm @ np.concatenate([F, F[..., 1:L, :]], axis=-2))
+
+    Rq = 2 * L + 1 if sampling == "mwss" else R
+    W = synth.signal_gaussian((B, Rq, T), seed=3)                # stand-in of the weighted spectra
+    thq = OT.mwss_thetas(2 * L) if sampling == "mwss" else OT.dh_thetas(L)
+
+    def quad(j):                                               # quadrature: per degree
+        OT._quadrature(W, thq, L, -spin, scale, np.linspace(abs(spin), L - 1, j).astype(int))
+
+    total = fit(inv, R) + fit(dft, T) + fit(quad, L)
+    return {"value": round(2 * B / total, 6), "unit": "transforms/s", "cores": 1, "kind": "oracle",
+            "sample": f"{workload}: oracle stages timed on {k2} and {k} of {R} rings / {T} orders / {L} "
+                      f"degrees (all {B} signals), single thread, extrapolated as overhead + linear cost",
+            "seconds_measured": round(time.perf_counter() - t_start, 2),
+            "seconds_full_round_trip_est": round(total, 1)}
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return None
     L, spin, N, B, ellp, desc = WORKLOADS[args.workload]
     k = 4
     samples = []
+    sampling = SAMPLING.get(args.workload, "mw")
+
+    def sample():
+        if sampling != "mw":
+            return cpu_baseline_sampled(args.workload, sampling, rings=k)
+        return cpu_baseline(args.workload, rings=k)
+
     for _ in range(args.warmup):
-        cpu_baseline(args.workload, rings=k)
+        sample()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        samples.append(cpu_baseline(args.workload, rings=k)["value"])
+        samples.append(sample()["value"])
     wall = time.perf_counter() - t0
     value = statistics.median(samples)
     per = 2 * B * (2 * N - 1 if N else 1)

@@ -1,12 +1,12 @@
 /*
- * s2gb -- spin spherical-harmonic and Wigner transforms on McEwen-Wiaux sampling for NVIDIA
+ * s2gb -- spin spherical-harmonic and Wigner transforms on equiangular samplings for NVIDIA
  * GB300 (sm_103a).  C ABI of libs2gb.so.
  *
  * The operations are those of Price & McEwen, "Differentiable and accelerated spherical harmonic
  * and Wigner transforms" (arXiv:2311.14670):
  *   - forward / inverse spin-s spherical-harmonic transform, separated into a phi-DFT and a theta
  *     stage (Sec. 4.1, Eqs. disc_sh_expanded, disc_sh_fft, disc_ish_fft, disc_ish_expanded),
- *     on MW sampling (Sec. 4.2.2);
+ *     on MW, MWSS and DH sampling (Sec. 4.2);
  *   - forward / inverse Wigner transform as a gamma-DFT plus spin-(-n) transforms (Sec. 2.3, 4.5);
  *   - the adjoints of both directions (Sec. 5.2).
  * The Wigner d-functions of the theta stage are generated on the fly by a three-term recursion
@@ -15,12 +15,13 @@
  * Conventions shared by every entry point
  * ---------------------------------------
  *   L      bandlimit (l < L), L >= 1.
- *   T      2L - 1 (number of phi samples; number of orders m).
- *   theta_t = (2t+1) pi / (2L-1), t < L;  phi_p = 2 pi p / (2L-1), p < T.
+ *   T      2L - 1 (number of orders m; number of phi samples on MW and DH).
+ *   R, P   rings and phi samples of the plan's sampling (see S2GB_MW below); on MW R = L and
+ *          P = T, theta_t = (2t+1) pi / (2L-1), t < L;  phi_p = 2 pi p / (2L-1), p < T.
  *   sY_lm(theta, phi) = (-1)^s sqrt((2l+1)/(4 pi)) d^l_{m,-s}(theta) e^{i m phi}.
- *   Sphere signal      f  [batch][L][T]              (ring t, sample p), row-major.
+ *   Sphere signal      f  [batch][R][P]              (ring t, sample p), row-major.
  *   Sphere coefficients flm[batch][L][T]             (degree l, index m+L-1).
- *   SO(3) signal       f  [batch][2N-1][L][T]        (gamma_k = 2 pi k/(2N-1), beta_t, alpha_p).
+ *   SO(3) signal       f  [batch][2N-1][R][P]        (gamma_k = 2 pi k/(2N-1), beta_t, alpha_p).
  *   Wigner coefficients flmn[batch][2N-1][L][T]      (index n+N-1, degree l, index m+L-1).
  *   Coefficient entries with |m| > l, or l < |s| (sphere) / l < |n| (Wigner), are ignored on
  *   input and written as 0 on output.
@@ -62,8 +63,16 @@ enum {
   S2GB_EWORKSPACE = -6     /* ws is NULL or smaller than s2gb_workspace_bytes() */
 };
 
-/* Sampling schemes.  Only McEwen-Wiaux (Sec. 4.2.2) is implemented. */
-enum { S2GB_MW = 0 };
+/*
+ * Sampling schemes (Sec. 4.2).  R theta rings by P phi samples, phi_p = 2 pi p / P:
+ *   S2GB_MW   McEwen-Wiaux (Sec. 4.2.2): R = L, theta_t = (2t+1) pi/(2L-1), P = 2L-1.
+ *   S2GB_MWSS its symmetric variant (Sec. 4.2.2): R = L+1, theta_t = pi t/L (both poles are
+ *             rings), P = 2L.
+ *   S2GB_DH   Driscoll-Healy (Sec. 4.2.1): R = 2L, theta_t = (2t+1) pi/(4L), P = 2L-1.
+ * Every scheme has an exact forward quadrature for bandlimited signals: MW and MWSS through the
+ * torus extension of Sec. 4.2.2, DH through its explicit weights.
+ */
+enum { S2GB_MW = 0, S2GB_MWSS = 1, S2GB_DH = 2 };
 
 /* Arithmetic of the theta stage. */
 enum {
@@ -80,7 +89,8 @@ enum {
  * recursion coefficient tables (Sec. 3.3 readings, O(L^2) per spin), the per-ring and per-order
  * log-space seed data (Eq. "initial_values") and the FFT weights; it creates cuFFT plans.
  * Returns S2GB_EINVAL for L < 1 or L > 8192, |spin| >= L (sphere), N < 0 or N > L, max_batch < 1,
- * an unknown sampling or precision; S2GB_EUNSUPPORTED for S2GB_FP32 with L > 2048;
+ * an unknown sampling or precision; S2GB_EUNSUPPORTED for S2GB_FP32 with L > 2048 or more than
+ * 2048 rings (MWSS at L = 2048, DH above L = 1024);
  * S2GB_ENOMEM / S2GB_ECUDA / S2GB_ECUFFT on device failures.  On failure *out is set to NULL.  The
  * calling thread's current device is restored on return.
  */
@@ -91,13 +101,13 @@ int s2gb_plan_create(s2gb_plan* out, int L, int spin, int N, int sampling, int p
  * Plan for real signals (spin 0 sphere transforms of real-valued f), whose coefficients obey the
  * Hermitian symmetry flm(l, -m) = (-1)^m conj(flm(l, m)) (Sec. 2.2).  Only the orders m >= 0 are
  * stored and computed:
- *   f   real (double / float) [batch][L][2L-1],
+ *   f   real (double / float) [batch][R][P] (MW and DH sampling; MWSS: S2GB_EUNSUPPORTED),
  *   flm complex [batch][L][L], flm[b][l][m] for 0 <= m < L (entries m > l ignored / written 0);
  *       the imaginary parts of flm[b][l][0] are ignored (they are 0 for a real signal).
  * s2gb_forward / s2gb_inverse / the adjoints / the order-range calls take these layouts; the
  * adjoints are with respect to the real inner product Re sum conj(x) y (PyTorch's convention for
- * gradients of real losses).  The theta stages alone use ring spectra [batch][L][L] (column m) and
- * forward-theta input g [batch][L (m)][L (t)].  The theta recursion runs for m >= 0 only and the
+ * gradients of real losses).  The theta stages alone use ring spectra [batch][R][L] (column m) and
+ * forward-theta input g [batch][L (m)][R (t)].  The theta recursion runs for m >= 0 only and the
  * phi DFTs are real-to-complex / complex-to-real, so a real transform costs about half a complex
  * one.  Arguments as in s2gb_plan_create (spin 0, N = 0 implied).  s2gb_inverse_noalloc refuses
  * real plans (S2GB_EUNSUPPORTED).
@@ -115,7 +125,7 @@ int s2gb_plan_create_real(s2gb_plan* out, int L, int sampling, int precision, in
  * as the on-the-fly kernels skip such values).  Memory: 8 bytes x L rings x the (l, m, n) triples
  * the theta kernels run -- with the +-m pairing of spin-0 and Wigner plans only m >= 0 at n = 0
  * (L = 1024 spin 0: 4.3 GB; spin 2: 8.6 GB; L = 2048 spin 0: 34 GB; real plans as spin 0);
- * s2gb_plan_device_bytes includes it.  FP64 plans with L <= 2048 only (else S2GB_EUNSUPPORTED);
+ * s2gb_plan_device_bytes includes it.  FP64 MW plans with L <= 2048 only (else S2GB_EUNSUPPORTED);
  * S2GB_ENOMEM when the table does not fit.
  */
 #define S2GB_PLAN_REAL 1u
@@ -134,8 +144,8 @@ size_t s2gb_plan_device_bytes(s2gb_plan plan);
 
 /*
  * Forward transform (Sec. 4.1, Eqs. disc_sh_fft + disc_sh_expanded; Wigner: Eq. wigner_sht_forward
- * with the gamma-DFT).  f -> flm.  The theta quadrature is exact for bandlimited signals (MW
- * sampling theorem).  f and flm must not overlap (else S2GB_EINVAL).
+ * with the gamma-DFT).  f -> flm.  The theta quadrature is exact for bandlimited signals (the
+ * sampling theorems of Sec. 4.2).  f and flm must not overlap (else S2GB_EINVAL).
  */
 int s2gb_forward(s2gb_plan plan, const void* f, void* flm, int batch, void* ws, size_t ws_bytes,
                  void* stream);
@@ -157,13 +167,15 @@ int s2gb_adjoint_inverse(s2gb_plan plan, const void* f_bar, void* flm_bar, int b
  *
  * s2gb_inverse_theta: Eq. disc_ish_expanded,
  *     ftilde[b][t][k] = sum_l (-1)^s sqrt((2l+1)/(4 pi)) flm[b][l][m+L-1] d^l_{m,-s}(theta_t),
- *   k = m mod T (the layout a length-T inverse DFT along the last axis turns into f).
- * s2gb_forward_theta: Eq. disc_sh_expanded on the L MW rings with ring weights already applied,
+ *   ftilde of shape [batch][R][P], k = m mod P (the layout a length-P inverse DFT along the last
+ *   axis turns into f); on MWSS the column k = L (no order) is written 0.
+ * s2gb_forward_theta: Eq. disc_sh_expanded on the R rings of the sampling with ring weights
+ *   already applied,
  *     flm[b][l][m+L-1] = (-1)^s sqrt((2l+1)/(4 pi)) sum_t d^l_{m,-s}(theta_t) g[b][m+L-1][t],
- *   g of shape [batch][T][L] (order-major).
+ *   g of shape [batch][T][R] (order-major).
  * Same pointer, batch and stream rules as the transforms; no workspace is needed.  For N >= 1
- * plans these return S2GB_EUNSUPPORTED, and so does s2gb_forward_theta for L > 2048 (its ring
- * chunks need the transforms' workspace).
+ * plans these return S2GB_EUNSUPPORTED, and so does s2gb_forward_theta for more than 2048 rings
+ * (its ring chunks need the transforms' workspace).
  */
 int s2gb_inverse_theta(s2gb_plan plan, const void* flm, void* ftilde, int batch, void* stream);
 int s2gb_forward_theta(s2gb_plan plan, const void* g, void* flm, int batch, void* stream);
@@ -177,12 +189,12 @@ int s2gb_forward_theta(s2gb_plan plan, const void* g, void* flm, int batch, void
  * transform computes for those orders, bit for bit.
  *
  * s2gb_inverse_theta_mrange: s2gb_inverse_theta for the orders in range only (sphere plans).
- *   Columns of ftilde for other orders are not written.
- * s2gb_inverse_phi: the rest of the sphere inverse transform, ftilde [b][t][m mod T] -> f
- *   (Eq. disc_ish_fft, a length-T inverse DFT along phi).  Sphere plans (Wigner:
+ *   Columns of ftilde for other orders are not written (on MWSS the column k = L is written 0).
+ * s2gb_inverse_phi: the rest of the sphere inverse transform, ftilde [b][t][m mod P] -> f
+ *   (Eq. disc_ish_fft, a length-P inverse DFT along phi).  Sphere plans (Wigner:
  *   S2GB_EUNSUPPORTED); workspace as for s2gb_inverse.  s2gb_inverse = s2gb_inverse_theta +
  *   s2gb_inverse_phi; an order-sharded inverse assembles ftilde from every shard (one exchange of
- *   16 * batch * L * (2L-1) bytes in FP64) before s2gb_inverse_phi.
+ *   16 * batch * R * P bytes in FP64) before s2gb_inverse_phi.
  * s2gb_forward_mrange: s2gb_forward whose theta stage runs for the orders in range only; every
  *   stage before it (the phi DFT and the theta-direction quadrature operator) runs in full.
  *   flm entries of other orders are not written.  Any plan (sphere or Wigner); workspace as for
@@ -206,7 +218,7 @@ int s2gb_forward_mrange(s2gb_plan plan, const void* f, void* flm, int batch, int
  * libs2gb.so, which every GPU that loads the library holds until the process exits.  It calls no
  * cudaMalloc / cudaFree and no allocating library routine (the plan must already exist).
  *   - Returns S2GB_EWORKSPACE when the call needs more scratch than the array holds: the
- *     theta-stage output (batch * L * (2L-1) elements; three such buffers for Wigner plans) plus
+ *     theta-stage output (batch * R * P elements; three such buffers for Wigner plans) plus
  *     the cuFFT work area of the phi (and gamma) DFT.  With complex128 data, 64 MiB covers for
  *     example L = 1024 with batch 1 or L = 512 with batch 4.
  *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress) with

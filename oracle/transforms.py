@@ -235,33 +235,41 @@ def _mwss_extend(F: np.ndarray, L: int, n: int) -> np.ndarray:
     return G
 
 
-def _forward_sampled(f: np.ndarray, L: int, n: int, scale: np.ndarray, sampling: str, ells) -> np.ndarray:
-    """flm[..., i, m] = scale_l int f(theta, phi) d^l_{m,n}(theta) e^{-i m phi} sin(theta), l = ells[i],
-    on the MWSS or DH grid (f[..., t, p]): the phi DFT, then the theta quadrature of the sampling.
+def _sampled_weighted_spectra(f: np.ndarray, L: int, n: int, sampling: str):
+    """W[..., u, m] and theta_u such that flm = scale_l sum_u W[u, m] d^l_{m,n}(theta_u) on the MWSS
+    or DH grid (f[..., t, p]): the phi DFT, then the theta quadrature of the sampling.
     DH: the explicit DH weights (Sec. 4.2.1).  MWSS: the route of Sec. 4.2.2 -- torus extension,
     Fourier coefficients |k| <= L-1 on the 2L torus points, evaluation on the MWSS grid of
     bandlimit 2L, MWSS weights at bandlimit 2L."""
-    ells = np.asarray(ells)
     Tp = sampling_shape(L, sampling)[1]
     F = np.asarray(f, dtype=np.complex128) @ _phi_matrix(L, Tp, -1)          # [t, m]
     qphi = 2 * np.pi / Tp
     if sampling == "dh":
-        th = dh_thetas(L)
-        W = F * (dh_theta_weights(L) * qphi)[:, None]
-    else:
-        G = _mwss_extend(F, L, n)                                            # [t', m], t' < 2L
-        k = np.arange(-(L - 1), L)
-        coef = _expi_pi(-np.outer(k, 2 * np.arange(2 * L)), 2 * L) / (2 * L)  # e^{-ik pi t'/L}/2L
-        u = np.arange(2 * L + 1)
-        up = _expi_pi(np.outer(u, k), 2 * L)                                 # e^{+ik pi u/(2L)}
-        Gu = up @ (coef @ G)
-        th = mwss_thetas(2 * L)
-        W = Gu * (mwss_theta_weights(2 * L) * qphi)[:, None]
-    D = wigner_d_table(ells, n, th)                                          # [i, m', u]
+        return F * (dh_theta_weights(L) * qphi)[:, None], dh_thetas(L)
+    G = _mwss_extend(F, L, n)                                                # [t', m], t' < 2L
+    k = np.arange(-(L - 1), L)
+    coef = _expi_pi(-np.outer(k, 2 * np.arange(2 * L)), 2 * L) / (2 * L)      # e^{-ik pi t'/L}/2L
+    u = np.arange(2 * L + 1)
+    up = _expi_pi(np.outer(u, k), 2 * L)                                     # e^{+ik pi u/(2L)}
+    Gu = up @ (coef @ G)
+    return Gu * (mwss_theta_weights(2 * L) * qphi)[:, None], mwss_thetas(2 * L)
+
+
+def _quadrature(W: np.ndarray, thetas, L: int, n: int, scale: np.ndarray, ells) -> np.ndarray:
+    """flm[..., i, m] = scale_l sum_u W[..., u, m] d^l_{m,n}(theta_u), l = ells[i] (Eq. disc_sh_expanded)."""
+    ells = np.asarray(ells)
+    D = wigner_d_table(ells, n, thetas)                                      # [i, m', u]
     M = int(ells.max())
     D = D[:, M - (L - 1):M + L, :] if M >= L - 1 else np.pad(D, ((0, 0), (L - 1 - M, L - 1 - M), (0, 0)))
     out = np.einsum("...um,imu->...im", W, D) * scale[ells][:, None]
     return np.where(coeff_mask(L, n)[ells], out, 0)
+
+
+def _forward_sampled(f: np.ndarray, L: int, n: int, scale: np.ndarray, sampling: str, ells) -> np.ndarray:
+    """flm[..., i, m] = scale_l int f(theta, phi) d^l_{m,n}(theta) e^{-i m phi} sin(theta), l = ells[i],
+    on the MWSS or DH grid."""
+    W, th = _sampled_weighted_spectra(f, L, n, sampling)
+    return _quadrature(W, th, L, n, scale, ells)
 
 
 def forward_s(f: np.ndarray, L: int, spin: int, sampling: str = "mw", ells=None) -> np.ndarray:

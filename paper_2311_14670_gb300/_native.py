@@ -22,6 +22,8 @@ S2GB_ECUDA = -4
 S2GB_ECUFFT = -5
 S2GB_EWORKSPACE = -6
 S2GB_MW = 0
+S2GB_MWSS = 1
+S2GB_DH = 2
 S2GB_FP64 = 0
 S2GB_FP32 = 1
 S2GB_PLAN_REAL = 1

@@ -65,12 +65,9 @@ struct Workspace {
 };
 
 Workspace carve(const Plan& p, void* ws, int batch) {
-  const size_t es = p.precision == S2GB_FP64 ? 16 : 8;
-  const size_t S = (size_t)batch * p.nN;
-  const size_t a = align256(S * p.MR * (size_t)(p.Nfft > p.L ? p.Nfft : p.L) * es);
-  const size_t b = align256(S * p.MR * (size_t)p.T * es);
-  const size_t c = align256(p.wigner ? S * p.L * (size_t)p.T * es : 0);
-  const size_t d = align256(p.fwd_parts > 1 ? (size_t)p.fwd_parts * S * p.L * (size_t)p.MR * es : 0);
+  size_t r[4];
+  workspace_regions(p, batch, r);
+  const size_t a = align256(r[0]), b = align256(r[1]), c = align256(r[2]), d = align256(r[3]);
   char* base = reinterpret_cast<char*>(((uintptr_t)ws + 255) & ~(uintptr_t)255);
   Workspace w = {base, base + a, base + a + b, base + a + b + c + d};
   w.D = d ? base + a + b + c : nullptr;
@@ -141,7 +138,8 @@ InvArgs inv_args(const Plan& p, const void* flm, void* out, int batch, const dou
                  long long s_sig, long long s_t, long long s_m, int m_mod) {
   InvArgs a;
   a.flm = flm; a.out = out; a.s_sig = s_sig; a.s_t = s_t; a.s_m = s_m; a.m_mod = m_mod;
-  a.nsig = batch; a.nN = p.nN; a.L = p.L; a.coef = p.coef; a.ring = p.ring; a.seed = p.seed;
+  a.mmod = p.P;
+  a.nsig = batch; a.nN = p.nN; a.L = p.L; a.nring = p.R; a.coef = p.coef; a.ring = p.ring; a.seed = p.seed;
   a.scale = scale; a.coef32 = p.coef32; a.v32 = p.v32;
   a.dtab = p.dtab; a.tab_off = p.tab_off; a.live0 = p.live0;
   a.rank0 = 0; a.nrank = p.MR;
@@ -164,114 +162,111 @@ FwdArgs fwd_args(const Plan& p, const void* g, void* flm, int batch, const doubl
                  long long s_sig, long long s_t, long long s_m, int m_mod, int use_nu) {
   FwdArgs a;
   a.g = g; a.flm = flm; a.s_sig = s_sig; a.s_t = s_t; a.s_m = s_m; a.m_mod = m_mod; a.use_nu = use_nu;
+  a.mmod = p.P;
   a.nsig = batch; a.nN = p.nN; a.L = p.L; a.coef = p.coef; a.ring = p.ring; a.seed = p.seed;
   a.scale = scale; a.nu = p.nu; a.coef32 = p.coef32; a.v32 = p.v32;
-  a.row0 = 0; a.nrows = p.L; a.part = nullptr; a.part_off = 0;
+  a.row0 = 0; a.nrows = p.R; a.part = nullptr; a.part_off = 0;
   a.dtab = p.dtab; a.tab_off = p.tab_off; a.live0 = p.live0;
   a.rank0 = 0; a.nrank = p.MR;
   a.mpos = p.real ? 1 : 0; a.flm_ld = p.MR; a.flm_c0 = p.real ? 0 : p.L - 1;
   return a;
 }
 
-// G (rows of length T, S*T rows, in B) -> H in B, using A as the fine-grid buffer.
+// G (theta-torus rows of length TS, S*MR rows, in B) -> H in B, using A as the fine-grid buffer
+// (MW and MWSS plans).
 int theta_weight_operator(Plan& p, FftRunner& fr, char* A, char* B, int S) {
   const size_t rows_item = (size_t)p.nN * p.MR;
   const int rows = S * p.MR;
   cudaStream_t st = fr.st;
-  S2GB_TRY(fr.run(p.fft_T, B, B, rows_item * p.T, CUFFT_FORWARD));
+  S2GB_TRY(fr.run(p.fft_T, B, B, rows_item * p.TS, CUFFT_FORWARD));
   S2GB_TRY(cuda_rc(launch_pad(p, B, A, rows, st)));
   S2GB_TRY(fr.run(p.fft_N, A, A, rows_item * p.Nfft, CUFFT_INVERSE));
   S2GB_TRY(cuda_rc(launch_weight_fine(p, A, rows, st)));
   S2GB_TRY(fr.run(p.fft_N, A, A, rows_item * p.Nfft, CUFFT_FORWARD));
   S2GB_TRY(cuda_rc(launch_truncate(p, A, B, rows, st)));
-  S2GB_TRY(fr.run(p.fft_T, B, B, rows_item * p.T, CUFFT_INVERSE));
+  S2GB_TRY(fr.run(p.fft_T, B, B, rows_item * p.TS, CUFFT_INVERSE));
   return S2GB_OK;
 }
 
 constexpr double kTwoPi = 6.283185307179586476925286766559;
 
-// Orders |m| in [mlo, mhi) of the forward transform: every stage before the theta kernel runs in
-// full, the theta kernel only for those orders (flm entries of other orders are not written).
-int do_forward(Plan& p, const void* f, void* flm, int batch, const Workspace& w, cudaStream_t st,
-               int mlo, int mhi) {
-  FftRunner fr{p, st, w.fft, batch};
-  const int S = batch * p.nN;
-  const size_t plane = (size_t)p.L * p.T;
-  const void* sig_in = f;
-  if (p.wigner) {
-    if (cufftSetStream(p.fft_gam[0], st) != CUFFT_SUCCESS) return S2GB_ECUFFT;
-    if (cufftSetWorkArea(p.fft_gam[0], w.fft) != CUFFT_SUCCESS) return S2GB_ECUFFT;
-    const size_t es = p.precision == S2GB_FP64 ? 16 : 8;
-    for (int b = 0; b < batch; ++b) {
-      const char* i = reinterpret_cast<const char*>(f) + (size_t)b * p.nN * plane * es;
-      char* o = w.C + (size_t)b * p.nN * plane * es;
-      cufftResult r = p.precision == S2GB_FP64
-          ? cufftExecZ2Z(p.fft_gam[0], (cufftDoubleComplex*)i, (cufftDoubleComplex*)o, CUFFT_FORWARD)
-          : cufftExecC2C(p.fft_gam[0], (cufftComplex*)i, (cufftComplex*)o, CUFFT_FORWARD);
-      if (r != CUFFT_SUCCESS) return S2GB_ECUFFT;
-    }
-    S2GB_TRY(cuda_rc(launch_gamma_reorder(p, w.C, w.B, batch, 1, kTwoPi / (2 * p.N - 1), st)));
-    sig_in = w.B;
-  }
-  S2GB_TRY(fr.run(p.fft_phi, sig_in, w.A, (size_t)p.nN * plane, CUFFT_FORWARD));
-  S2GB_TRY(cuda_rc(launch_extend(p, w.A, w.B, S, st)));
-  S2GB_TRY(theta_weight_operator(p, fr, w.A, w.B, S));
-  FwdArgs a = fwd_args(p, w.B, flm, batch, p.scale_fwd, (long long)p.T * p.T, 1, p.T, 0, 1);
-  a.part = w.D;
-  order_ranks(p, mlo, mhi, a.rank0, a.nrank);
-  return cuda_rc(launch_theta_forward(p, a, st));
-}
-
-// Sphere inverse after the theta stage: ring spectra [b][t][m mod T] -> f (Eq. disc_ish_fft).
-int do_inverse_phi(Plan& p, const void* ftilde, void* f, int batch, const Workspace& w, cudaStream_t st) {
-  FftRunner fr{p, st, w.fft, batch};
-  return fr.run(p.fft_phi, ftilde, f, (size_t)p.L * p.T, CUFFT_INVERSE);
-}
-
-int do_inverse(Plan& p, const void* flm, void* f, int batch, const Workspace& w, cudaStream_t st) {
-  FftRunner fr{p, st, w.fft, batch};
-  const size_t plane = (size_t)p.L * p.T;
-  InvArgs a = inv_args(p, flm, w.A, batch, p.scale_inv, (long long)plane, p.T, 1, 1);
-  S2GB_TRY(cuda_rc(launch_theta_inverse(p, a, st)));
-  if (!p.wigner) return fr.run(p.fft_phi, w.A, f, plane, CUFFT_INVERSE);
-  S2GB_TRY(fr.run(p.fft_phi, w.A, w.B, (size_t)p.nN * plane, CUFFT_INVERSE));
-  S2GB_TRY(cuda_rc(launch_gamma_reorder(p, w.B, w.C, batch, 0, 1.0, st)));
+// Gamma DFT of the Wigner transform, one signal at a time: [b][k][plane] -> [b][k'][plane] (dir
+// CUFFT_FORWARD) or back (CUFFT_INVERSE); plane = R * P.
+int gamma_dft(Plan& p, const void* in, void* out, int batch, void* work, cudaStream_t st, int dir) {
   if (cufftSetStream(p.fft_gam[0], st) != CUFFT_SUCCESS) return S2GB_ECUFFT;
-  if (cufftSetWorkArea(p.fft_gam[0], w.fft) != CUFFT_SUCCESS) return S2GB_ECUFFT;
+  if (cufftSetWorkArea(p.fft_gam[0], work) != CUFFT_SUCCESS) return S2GB_ECUFFT;
   const size_t es = p.precision == S2GB_FP64 ? 16 : 8;
+  const size_t plane = (size_t)p.R * p.P;
   for (int b = 0; b < batch; ++b) {
-    const char* i = w.C + (size_t)b * p.nN * plane * es;
-    char* o = reinterpret_cast<char*>(f) + (size_t)b * p.nN * plane * es;
+    const char* i = reinterpret_cast<const char*>(in) + (size_t)b * p.nN * plane * es;
+    char* o = reinterpret_cast<char*>(out) + (size_t)b * p.nN * plane * es;
     cufftResult r = p.precision == S2GB_FP64
-        ? cufftExecZ2Z(p.fft_gam[0], (cufftDoubleComplex*)i, (cufftDoubleComplex*)o, CUFFT_INVERSE)
-        : cufftExecC2C(p.fft_gam[0], (cufftComplex*)i, (cufftComplex*)o, CUFFT_INVERSE);
+        ? cufftExecZ2Z(p.fft_gam[0], (cufftDoubleComplex*)i, (cufftDoubleComplex*)o, dir)
+        : cufftExecC2C(p.fft_gam[0], (cufftComplex*)i, (cufftComplex*)o, dir);
     if (r != CUFFT_SUCCESS) return S2GB_ECUFFT;
   }
   return S2GB_OK;
 }
 
+// Orders |m| in [mlo, mhi) of the forward transform: every stage before the theta kernel runs in
+// full, the theta kernel only for those orders (flm entries of other orders are not written).
+// MW / MWSS: phi DFT, torus extension, theta-direction quadrature operator, theta kernel over the
+// rings with the fold factors.  DH: phi DFT, theta kernel over the rings with the DH weights.
+int do_forward(Plan& p, const void* f, void* flm, int batch, const Workspace& w, cudaStream_t st,
+               int mlo, int mhi) {
+  FftRunner fr{p, st, w.fft, batch};
+  const int S = batch * p.nN;
+  const size_t plane = (size_t)p.R * p.P;
+  const void* sig_in = f;
+  if (p.wigner) {
+    S2GB_TRY(gamma_dft(p, f, w.C, batch, w.fft, st, CUFFT_FORWARD));
+    S2GB_TRY(cuda_rc(launch_gamma_reorder(p, w.C, w.B, batch, 1, kTwoPi / (2 * p.N - 1), st)));
+    sig_in = w.B;
+  }
+  S2GB_TRY(fr.run(p.fft_phi, sig_in, w.A, (size_t)p.nN * plane, CUFFT_FORWARD));
+  FwdArgs a;
+  if (p.sampling == S2GB_DH) {
+    a = fwd_args(p, w.A, flm, batch, p.scale_fwd, (long long)plane, p.P, 1, 1, 1);
+  } else {
+    S2GB_TRY(cuda_rc(launch_extend(p, w.A, w.B, S, st)));
+    S2GB_TRY(theta_weight_operator(p, fr, w.A, w.B, S));
+    a = fwd_args(p, w.B, flm, batch, p.scale_fwd, (long long)p.MR * p.TS, 1, p.TS, 0, 1);
+  }
+  a.part = w.D;
+  order_ranks(p, mlo, mhi, a.rank0, a.nrank);
+  return cuda_rc(launch_theta_forward(p, a, st));
+}
+
+// Sphere inverse after the theta stage: ring spectra [b][t][m mod P] -> f (Eq. disc_ish_fft).
+int do_inverse_phi(Plan& p, const void* ftilde, void* f, int batch, const Workspace& w, cudaStream_t st) {
+  FftRunner fr{p, st, w.fft, batch};
+  return fr.run(p.fft_phi, ftilde, f, (size_t)p.R * p.P, CUFFT_INVERSE);
+}
+
+int do_inverse(Plan& p, const void* flm, void* f, int batch, const Workspace& w, cudaStream_t st) {
+  FftRunner fr{p, st, w.fft, batch};
+  const size_t plane = (size_t)p.R * p.P;
+  InvArgs a = inv_args(p, flm, w.A, batch, p.scale_inv, (long long)plane, p.P, 1, 1);
+  S2GB_TRY(cuda_rc(launch_theta_inverse(p, a, st)));
+  S2GB_TRY(cuda_rc(zero_nyquist(p, w.A, batch * p.nN, st)));
+  if (!p.wigner) return fr.run(p.fft_phi, w.A, f, plane, CUFFT_INVERSE);
+  S2GB_TRY(fr.run(p.fft_phi, w.A, w.B, (size_t)p.nN * plane, CUFFT_INVERSE));
+  S2GB_TRY(cuda_rc(launch_gamma_reorder(p, w.B, w.C, batch, 0, 1.0, st)));
+  return gamma_dft(p, w.C, f, batch, w.fft, st, CUFFT_INVERSE);
+}
+
 int do_adjoint_inverse(Plan& p, const void* fbar, void* flmbar, int batch, const Workspace& w,
                        cudaStream_t st) {
   FftRunner fr{p, st, w.fft, batch};
-  const size_t plane = (size_t)p.L * p.T;
+  const size_t plane = (size_t)p.R * p.P;
   const void* sig_in = fbar;
   if (p.wigner) {
-    if (cufftSetStream(p.fft_gam[0], st) != CUFFT_SUCCESS) return S2GB_ECUFFT;
-    if (cufftSetWorkArea(p.fft_gam[0], w.fft) != CUFFT_SUCCESS) return S2GB_ECUFFT;
-    const size_t es = p.precision == S2GB_FP64 ? 16 : 8;
-    for (int b = 0; b < batch; ++b) {
-      const char* i = reinterpret_cast<const char*>(fbar) + (size_t)b * p.nN * plane * es;
-      char* o = w.C + (size_t)b * p.nN * plane * es;
-      cufftResult r = p.precision == S2GB_FP64
-          ? cufftExecZ2Z(p.fft_gam[0], (cufftDoubleComplex*)i, (cufftDoubleComplex*)o, CUFFT_FORWARD)
-          : cufftExecC2C(p.fft_gam[0], (cufftComplex*)i, (cufftComplex*)o, CUFFT_FORWARD);
-      if (r != CUFFT_SUCCESS) return S2GB_ECUFFT;
-    }
+    S2GB_TRY(gamma_dft(p, fbar, w.C, batch, w.fft, st, CUFFT_FORWARD));
     S2GB_TRY(cuda_rc(launch_gamma_reorder(p, w.C, w.B, batch, 1, 1.0, st)));
     sig_in = w.B;
   }
   S2GB_TRY(fr.run(p.fft_phi, sig_in, w.A, (size_t)p.nN * plane, CUFFT_FORWARD));
-  FwdArgs a = fwd_args(p, w.A, flmbar, batch, p.scale_inv, (long long)plane, p.T, 1, 1, 0);
+  FwdArgs a = fwd_args(p, w.A, flmbar, batch, p.scale_inv, (long long)plane, p.P, 1, 1, 0);
   a.part = w.D;
   return cuda_rc(launch_theta_forward(p, a, st));
 }
@@ -280,42 +275,42 @@ int do_adjoint_forward(Plan& p, const void* flmbar, void* fbar, int batch, const
                        cudaStream_t st) {
   FftRunner fr{p, st, w.fft, batch};
   const int S = batch * p.nN;
-  const size_t plane = (size_t)p.L * p.T;
-  InvArgs a = inv_args(p, flmbar, w.B, batch, p.scale_fwd, (long long)p.T * p.T, 1, p.T, 0);
-  S2GB_TRY(cuda_rc(launch_theta_inverse(p, a, st)));
-  S2GB_TRY(cuda_rc(launch_nu_extend(p, w.B, S * p.T, st)));
-  S2GB_TRY(theta_weight_operator(p, fr, w.A, w.B, S));
-  S2GB_TRY(cuda_rc(launch_extend_adjoint(p, w.B, w.A, S, st)));
+  const size_t plane = (size_t)p.R * p.P;
+  if (p.sampling == S2GB_DH) {
+    InvArgs a = inv_args(p, flmbar, w.A, batch, p.scale_fwd, (long long)plane, p.P, 1, 1);
+    S2GB_TRY(cuda_rc(launch_theta_inverse(p, a, st)));
+    S2GB_TRY(cuda_rc(launch_ring_weight(p, w.A, S, p.P, st)));
+  } else {
+    InvArgs a = inv_args(p, flmbar, w.B, batch, p.scale_fwd, (long long)p.MR * p.TS, 1, p.TS, 0);
+    S2GB_TRY(cuda_rc(launch_theta_inverse(p, a, st)));
+    S2GB_TRY(cuda_rc(launch_nu_extend(p, w.B, S * p.MR, st)));
+    S2GB_TRY(theta_weight_operator(p, fr, w.A, w.B, S));
+    S2GB_TRY(cuda_rc(launch_extend_adjoint(p, w.B, w.A, S, st)));
+  }
   if (!p.wigner) return fr.run(p.fft_phi, w.A, fbar, plane, CUFFT_INVERSE);
   S2GB_TRY(fr.run(p.fft_phi, w.A, w.B, (size_t)p.nN * plane, CUFFT_INVERSE));
   S2GB_TRY(cuda_rc(launch_gamma_reorder(p, w.B, w.C, batch, 0, kTwoPi / (2 * p.N - 1), st)));
-  if (cufftSetStream(p.fft_gam[0], st) != CUFFT_SUCCESS) return S2GB_ECUFFT;
-  if (cufftSetWorkArea(p.fft_gam[0], w.fft) != CUFFT_SUCCESS) return S2GB_ECUFFT;
-  const size_t es = p.precision == S2GB_FP64 ? 16 : 8;
-  for (int b = 0; b < batch; ++b) {
-    const char* i = w.C + (size_t)b * p.nN * plane * es;
-    char* o = reinterpret_cast<char*>(fbar) + (size_t)b * p.nN * plane * es;
-    cufftResult r = p.precision == S2GB_FP64
-        ? cufftExecZ2Z(p.fft_gam[0], (cufftDoubleComplex*)i, (cufftDoubleComplex*)o, CUFFT_INVERSE)
-        : cufftExecC2C(p.fft_gam[0], (cufftComplex*)i, (cufftComplex*)o, CUFFT_INVERSE);
-    if (r != CUFFT_SUCCESS) return S2GB_ECUFFT;
-  }
-  return S2GB_OK;
+  return gamma_dft(p, w.C, fbar, batch, w.fft, st, CUFFT_INVERSE);
 }
 
 // ---- real signals (spin 0, Sec. 2.2 Hermitian symmetry flm(l, -m) = (-1)^m conj(flm(l, m))) ----
-// f real [b][L][T]; flm [b][L][L] holds the orders m = 0..L-1; ring spectra [b][t][m] with L
+// f real [b][R][P]; flm [b][L][L] holds the orders m = 0..L-1; ring spectra [b][t][m] with L
 // columns.  Every stage runs on the orders m >= 0 only; the phi DFTs are real-to-complex and
-// complex-to-real (the C2R sum is Re X_0 + 2 Re sum_{m>=1} X_m e^{i m phi}).
+// complex-to-real (the C2R sum is Re X_0 + 2 Re sum_{m>=1} X_m e^{i m phi}).  MW and DH (P = 2L-1).
 
 int do_forward_real(Plan& p, const void* f, void* flm, int batch, const Workspace& w, cudaStream_t st,
                     int mlo, int mhi) {
   FftRunner fr{p, st, w.fft, batch};
-  const size_t L = p.L, T = p.T;
-  S2GB_TRY(fr.run_real(p.fft_phi, f, w.A, L * T, L * L, +1));
-  S2GB_TRY(cuda_rc(launch_extend(p, w.A, w.B, batch, st)));
-  S2GB_TRY(theta_weight_operator(p, fr, w.A, w.B, batch));
-  FwdArgs a = fwd_args(p, w.B, flm, batch, p.scale_fwd, (long long)(L * T), 1, (long long)T, 1, 1);
+  const size_t L = p.L, R = p.R, P = p.P, TS = p.TS;
+  S2GB_TRY(fr.run_real(p.fft_phi, f, w.A, R * P, R * L, +1));
+  FwdArgs a;
+  if (p.sampling == S2GB_DH) {
+    a = fwd_args(p, w.A, flm, batch, p.scale_fwd, (long long)(R * L), (long long)L, 1, 1, 1);
+  } else {
+    S2GB_TRY(cuda_rc(launch_extend(p, w.A, w.B, batch, st)));
+    S2GB_TRY(theta_weight_operator(p, fr, w.A, w.B, batch));
+    a = fwd_args(p, w.B, flm, batch, p.scale_fwd, (long long)(L * TS), 1, (long long)TS, 1, 1);
+  }
   a.part = w.D;
   order_ranks(p, mlo, mhi, a.rank0, a.nrank);
   return cuda_rc(launch_theta_forward(p, a, st));
@@ -323,10 +318,10 @@ int do_forward_real(Plan& p, const void* f, void* flm, int batch, const Workspac
 
 int do_inverse_real(Plan& p, const void* flm, void* f, int batch, const Workspace& w, cudaStream_t st) {
   FftRunner fr{p, st, w.fft, batch};
-  const size_t L = p.L, T = p.T;
-  InvArgs a = inv_args(p, flm, w.A, batch, p.scale_inv, (long long)(L * L), (long long)L, 1, 1);
+  const size_t L = p.L, R = p.R, P = p.P;
+  InvArgs a = inv_args(p, flm, w.A, batch, p.scale_inv, (long long)(R * L), (long long)L, 1, 1);
   S2GB_TRY(cuda_rc(launch_theta_inverse(p, a, st)));
-  return fr.run_real(p.fft_phi_c2r, w.A, f, L * L, L * T, -1);
+  return fr.run_real(p.fft_phi_c2r, w.A, f, R * L, R * P, -1);
 }
 
 // Adjoint (real inner product) of f = C2R(theta(flm)): R2C, columns m >= 1 doubled, then the
@@ -334,10 +329,10 @@ int do_inverse_real(Plan& p, const void* flm, void* f, int batch, const Workspac
 int do_adjoint_inverse_real(Plan& p, const void* fbar, void* flmbar, int batch, const Workspace& w,
                             cudaStream_t st) {
   FftRunner fr{p, st, w.fft, batch};
-  const size_t L = p.L, T = p.T;
-  S2GB_TRY(fr.run_real(p.fft_phi, fbar, w.A, L * T, L * L, +1));
-  S2GB_TRY(cuda_rc(launch_scale_nonzero_orders(p, w.A, (size_t)batch * L, 2.0, st)));
-  FwdArgs a = fwd_args(p, w.A, flmbar, batch, p.scale_inv, (long long)(L * L), (long long)L, 1, 1, 0);
+  const size_t L = p.L, R = p.R, P = p.P;
+  S2GB_TRY(fr.run_real(p.fft_phi, fbar, w.A, R * P, R * L, +1));
+  S2GB_TRY(cuda_rc(launch_scale_nonzero_orders(p, w.A, (size_t)batch * R, 2.0, st)));
+  FwdArgs a = fwd_args(p, w.A, flmbar, batch, p.scale_inv, (long long)(R * L), (long long)L, 1, 1, 0);
   a.part = w.D;
   return cuda_rc(launch_theta_forward(p, a, st));
 }
@@ -347,19 +342,25 @@ int do_adjoint_inverse_real(Plan& p, const void* fbar, void* flmbar, int batch, 
 int do_adjoint_forward_real(Plan& p, const void* flmbar, void* fbar, int batch, const Workspace& w,
                             cudaStream_t st) {
   FftRunner fr{p, st, w.fft, batch};
-  const size_t L = p.L, T = p.T;
-  InvArgs a = inv_args(p, flmbar, w.B, batch, p.scale_fwd, (long long)(L * T), 1, (long long)T, 1);
-  S2GB_TRY(cuda_rc(launch_theta_inverse(p, a, st)));
-  S2GB_TRY(cuda_rc(launch_nu_extend(p, w.B, batch * p.MR, st)));
-  S2GB_TRY(theta_weight_operator(p, fr, w.A, w.B, batch));
-  S2GB_TRY(cuda_rc(launch_extend_adjoint(p, w.B, w.A, batch, st)));
-  S2GB_TRY(cuda_rc(launch_scale_nonzero_orders(p, w.A, (size_t)batch * L, 0.5, st)));
-  return fr.run_real(p.fft_phi_c2r, w.A, fbar, L * L, L * T, -1);
+  const size_t L = p.L, R = p.R, P = p.P, TS = p.TS;
+  if (p.sampling == S2GB_DH) {
+    InvArgs a = inv_args(p, flmbar, w.A, batch, p.scale_fwd, (long long)(R * L), (long long)L, 1, 1);
+    S2GB_TRY(cuda_rc(launch_theta_inverse(p, a, st)));
+    S2GB_TRY(cuda_rc(launch_ring_weight(p, w.A, batch, (int)L, st)));
+  } else {
+    InvArgs a = inv_args(p, flmbar, w.B, batch, p.scale_fwd, (long long)(L * TS), 1, (long long)TS, 1);
+    S2GB_TRY(cuda_rc(launch_theta_inverse(p, a, st)));
+    S2GB_TRY(cuda_rc(launch_nu_extend(p, w.B, batch * p.MR, st)));
+    S2GB_TRY(theta_weight_operator(p, fr, w.A, w.B, batch));
+    S2GB_TRY(cuda_rc(launch_extend_adjoint(p, w.B, w.A, batch, st)));
+  }
+  S2GB_TRY(cuda_rc(launch_scale_nonzero_orders(p, w.A, (size_t)batch * R, 0.5, st)));
+  return fr.run_real(p.fft_phi_c2r, w.A, fbar, R * L, R * P, -1);
 }
 
 int do_inverse_phi_real(Plan& p, const void* ftilde, void* f, int batch, const Workspace& w, cudaStream_t st) {
   FftRunner fr{p, st, w.fft, batch};
-  return fr.run_real(p.fft_phi_c2r, ftilde, f, (size_t)p.L * p.L, (size_t)p.L * p.T, -1);
+  return fr.run_real(p.fft_phi_c2r, ftilde, f, (size_t)p.R * p.L, (size_t)p.R * p.P, -1);
 }
 
 bool overlaps(const void* a, size_t abytes, const void* b, size_t bbytes) {
@@ -380,9 +381,10 @@ int run(s2gb_plan plan, Op op, const void* in, void* out, int batch, void* ws, s
   if (mlo < 0 || mlo > mhi || mhi > p.L) return S2GB_EINVAL;
   if (op == Op::InversePhi && p.wigner) return S2GB_EUNSUPPORTED;
   const size_t es = p.precision == S2GB_FP64 ? 16 : 8;
-  // element counts of the signal side and of the coefficient (or spectrum) side
-  const size_t sig_bytes = (size_t)batch * p.nN * p.L * p.T * (p.real ? es / 2 : es);
-  const size_t coef_bytes = (size_t)batch * p.nN * p.L * p.MR * es;
+  // bytes of the signal side and of the coefficient side (ring spectra for InversePhi)
+  const size_t sig_bytes = (size_t)batch * p.nN * p.R * p.P * (p.real ? es / 2 : es);
+  const size_t coef_bytes = op == Op::InversePhi ? (size_t)batch * p.R * (p.real ? p.L : p.P) * es
+                                                 : (size_t)batch * p.nN * p.L * p.MR * es;
   const bool in_is_signal = (op == Op::Forward || op == Op::AdjInverse);
   if (overlaps(in, in_is_signal ? sig_bytes : coef_bytes, out, in_is_signal ? coef_bytes : sig_bytes))
     return S2GB_EINVAL;
@@ -423,11 +425,18 @@ int plan_create_impl(s2gb_plan* out, int L, int spin, int N, int sampling, int p
                      int device, bool real, bool precompute = false) {
   if (!out) return S2GB_EINVAL;
   *out = nullptr;
-  if (L < 1 || L > 8192 || N < 0 || N > L || max_batch < 1 || sampling != S2GB_MW) return S2GB_EINVAL;
+  if (L < 1 || L > 8192 || N < 0 || N > L || max_batch < 1) return S2GB_EINVAL;
+  if (sampling != S2GB_MW && sampling != S2GB_MWSS && sampling != S2GB_DH) return S2GB_EINVAL;
   if (precision != S2GB_FP64 && precision != S2GB_FP32) return S2GB_EINVAL;
   if (N == 0 && (spin <= -L || spin >= L)) return S2GB_EINVAL;
-  if (precision == S2GB_FP32 && L > 2048) return S2GB_EUNSUPPORTED;
-  if (precompute && (precision != S2GB_FP64 || L > s2gb::kFwdChunk)) return S2GB_EUNSUPPORTED;
+  const int rings = sampling == S2GB_MWSS ? L + 1 : (sampling == S2GB_DH ? 2 * L : L);
+  // float32 forward kernels hold every ring in one CTA; the ring-chunked float64 forward keeps its
+  // polar caps (under 0.05 of the rings each) within one 512-ring launch, i.e. at most 8193 rings
+  if (precision == S2GB_FP32 && (L > 2048 || rings > s2gb::kFwdChunk)) return S2GB_EUNSUPPORTED;
+  if (rings > 8193) return S2GB_EUNSUPPORTED;
+  if (real && sampling == S2GB_MWSS) return S2GB_EUNSUPPORTED;
+  if (precompute && (precision != S2GB_FP64 || L > s2gb::kFwdChunk || sampling != S2GB_MW))
+    return S2GB_EUNSUPPORTED;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return S2GB_EINVAL;
   s2gb_plan h = new (std::nothrow) s2gb_plan_s;
@@ -435,6 +444,7 @@ int plan_create_impl(s2gb_plan* out, int L, int spin, int N, int sampling, int p
   s2gb::Plan& p = h->p;
   p.L = L; p.spin = N == 0 ? spin : 0; p.N = N; p.precision = precision; p.max_batch = max_batch;
   p.device = device;
+  p.sampling = sampling;
   p.real = real;
   p.precompute = precompute;
   int rc;
@@ -511,11 +521,16 @@ int s2gb_inverse_theta_mrange(s2gb_plan plan, const void* flm, void* ftilde, int
   if (batch < 1 || batch > p.max_batch) return S2GB_EINVAL;
   if (m_lo < 0 || m_lo > m_hi || m_hi > p.L) return S2GB_EINVAL;
   const size_t es = p.precision == S2GB_FP64 ? 16 : 8;
-  if (s2gb::overlaps(flm, ftilde, (size_t)batch * p.L * p.MR * es)) return S2GB_EINVAL;
+  const int SW = p.real ? p.L : p.P;     // ring-spectrum columns
+  if (s2gb::overlaps(flm, (size_t)batch * p.L * p.MR * es, ftilde, (size_t)batch * p.R * SW * es))
+    return S2GB_EINVAL;
   s2gb::DeviceGuard g(p.device);
-  s2gb::InvArgs a = s2gb::inv_args(p, flm, ftilde, batch, p.scale_inv, (long long)p.L * p.MR, p.MR, 1, 1);
+  s2gb::InvArgs a = s2gb::inv_args(p, flm, ftilde, batch, p.scale_inv, (long long)p.R * SW, SW, 1, 1);
   s2gb::order_ranks(p, m_lo, m_hi, a.rank0, a.nrank);
-  return s2gb::cuda_rc(s2gb::launch_theta_inverse(p, a, reinterpret_cast<cudaStream_t>(stream)));
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  int rc = s2gb::cuda_rc(s2gb::launch_theta_inverse(p, a, st));
+  if (rc != S2GB_OK) return rc;
+  return s2gb::cuda_rc(s2gb::zero_nyquist(p, ftilde, batch, st));
 }
 
 int s2gb_inverse_theta(s2gb_plan plan, const void* flm, void* ftilde, int batch, void* stream) {
@@ -538,9 +553,10 @@ int s2gb_forward_theta(s2gb_plan plan, const void* gin, void* flm, int batch, vo
   if (p.wigner || p.fwd_parts > 1) return S2GB_EUNSUPPORTED;   // L > 2048 needs a workspace
   if (batch < 1 || batch > p.max_batch) return S2GB_EINVAL;
   const size_t es = p.precision == S2GB_FP64 ? 16 : 8;
-  if (s2gb::overlaps(gin, flm, (size_t)batch * p.L * p.MR * es)) return S2GB_EINVAL;
+  if (s2gb::overlaps(gin, (size_t)batch * p.MR * p.R * es, flm, (size_t)batch * p.L * p.MR * es))
+    return S2GB_EINVAL;
   s2gb::DeviceGuard g(p.device);
-  s2gb::FwdArgs a = s2gb::fwd_args(p, gin, flm, batch, p.scale_fwd, (long long)p.MR * p.L, 1, p.L,
+  s2gb::FwdArgs a = s2gb::fwd_args(p, gin, flm, batch, p.scale_fwd, (long long)p.MR * p.R, 1, p.R,
                                    p.real ? 1 : 0, 0);
   return s2gb::cuda_rc(s2gb::launch_theta_forward(p, a, reinterpret_cast<cudaStream_t>(stream)));
 }
@@ -603,8 +619,8 @@ extern "C" int s2gb_inverse_noalloc(s2gb_plan plan, const void* flm, void* f, in
   if (p.real) return S2GB_EUNSUPPORTED;
   if (batch < 1 || batch > p.max_batch) return S2GB_EINVAL;
   const size_t es = p.precision == S2GB_FP64 ? 16 : 8;
-  const size_t sig_bytes = (size_t)batch * p.nN * p.L * p.T * es;
-  if (s2gb::overlaps(flm, f, sig_bytes)) return S2GB_EINVAL;
+  const size_t sig_bytes = (size_t)batch * p.nN * p.R * p.P * es;
+  if (s2gb::overlaps(flm, (size_t)batch * p.nN * p.L * p.T * es, f, sig_bytes)) return S2GB_EINVAL;
   // scratch: the theta-stage output (and, for Wigner, two more signal-sized buffers) + cuFFT work
   const int q = (batch == p.max_batch) ? 1 : 0;
   size_t work = 0, w2 = 0;

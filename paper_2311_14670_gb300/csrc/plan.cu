@@ -202,6 +202,30 @@ int make_fft(cufftHandle* h, int n, int batch, int istride, int idist, cufftType
   return S2GB_OK;
 }
 
+// DH theta weights (Sec. 4.2.1) times the phi step 2 pi / P: q_t = (2/L) sin(theta_t)
+// sum_{k<L} sin((2k+1) theta_t) / (2k+1) with theta_t = (2t+1) pi / (4L).  Every sine has its
+// argument reduced exactly ((2k+1)(2t+1) mod 8L, in units of pi/(4L)) and the sum is compensated
+// (Neumaier), so each weight is accurate to a few ulps.  q_{2L-1-t} = q_t (theta -> pi - theta).
+std::vector<double> dh_ring_weights(int L) {
+  std::vector<double> q(2 * L);
+  const long long M = 8LL * L;
+  const double u = kPi / (4.0 * L);
+  for (int t = 0; t < L; ++t) {
+    double s = 0.0, c = 0.0;
+    for (int k = 0; k < L; ++k) {
+      const long long num = ((2LL * k + 1) * (2LL * t + 1)) % M;
+      const double x = std::sin((double)num * u) / (double)(2 * k + 1);
+      const double ts = s + x;
+      c += std::fabs(s) >= std::fabs(x) ? (s - ts) + x : (x - ts) + s;
+      s = ts;
+    }
+    const long double th = (long double)(2 * t + 1) * kPiL / (4.0L * L);
+    const long double w = (2.0L / L) * std::sin(th) * ((long double)s + (long double)c);
+    q[t] = q[2 * L - 1 - t] = (double)(w * 2.0L * kPiL / (long double)(2 * L - 1));
+  }
+  return q;
+}
+
 }  // namespace
 
 int make_plan(Plan* p) {
@@ -211,24 +235,46 @@ int make_plan(Plan* p) {
   p->wigner = p->N >= 1;
   p->nN = p->wigner ? 2 * p->N - 1 : 1;
   p->MR = p->real ? L : T;
-  p->Nfft = good_fft_size(4 * L - 3 > 2 * L - 1 ? 4 * L - 3 : 2 * L - 1);
+  switch (p->sampling) {
+    case S2GB_MWSS: p->R = L + 1; p->P = 2 * L; p->TS = 2 * L; break;
+    case S2GB_DH: p->R = 2 * L; p->P = T; p->TS = 0; break;
+    default: p->R = L; p->P = T; p->TS = T; break;
+  }
+  p->Nfft = p->TS ? good_fft_size(4 * L - 3 > p->TS ? 4 * L - 3 : p->TS) : 0;
   const int nN = p->nN;
+  const int R = p->R;
 
   std::vector<int> n_of(nN);
   for (int i = 0; i < nN; ++i) n_of[i] = p->wigner ? i - (p->N - 1) : -p->spin;
 
-  // ---- rings (MW, Sec. 4.2.2) ----
-  std::vector<RingData> ring(L);
-  for (int t = 0; t < L; ++t) {
+  // ---- rings (Sec. 4.2) ----
+  // MW: theta_t = (2t+1) pi/(2L-1), t < L (the last ring is theta = pi);
+  // MWSS: theta_t = pi t/L, t <= L (theta = 0 and pi are rings); DH: theta_t = (2t+1) pi/(4L), t < 2L.
+  std::vector<RingData> ring(R);
+  for (int t = 0; t < R; ++t) {
     RingData r{};
-    const bool pole = (t == L - 1);
-    long double th = pole ? kPiL : (long double)(2 * t + 1) * kPiL / (long double)T;
-    long double sh = std::sin(th / 2), ch = pole ? 0.0L : std::cos(th / 2);
+    int pole = 0;
+    long double th;
+    if (p->sampling == S2GB_MWSS) {
+      pole = (t == L) ? 1 : (t == 0 ? 2 : 0);
+      th = pole == 1 ? kPiL : (long double)t * kPiL / (long double)L;
+    } else if (p->sampling == S2GB_DH) {
+      th = (long double)(2 * t + 1) * kPiL / (4.0L * L);
+    } else {
+      pole = (t == L - 1) ? 1 : 0;
+      th = pole ? kPiL : (long double)(2 * t + 1) * kPiL / (long double)T;
+    }
+    long double sh = pole == 2 ? 0.0L : std::sin(th / 2), ch = pole == 1 ? 0.0L : std::cos(th / 2);
     r.north = th < kPiL / 2;
     r.pole = pole;
     r.v = (double)(r.north ? 2 * sh * sh : 2 * ch * ch);
-    split(std::log2(sh), &r.ls_hi, &r.ls_lo);
-    if (pole) {
+    if (pole == 2) {
+      r.ls_hi = -std::numeric_limits<double>::infinity();
+      r.ls_lo = 0.0;
+    } else {
+      split(std::log2(sh), &r.ls_hi, &r.ls_lo);
+    }
+    if (pole == 1) {
       r.lc_hi = -std::numeric_limits<double>::infinity();
       r.lc_lo = 0.0;
     } else {
@@ -239,10 +285,10 @@ int make_plan(Plan* p) {
   }
 
   p->cap_n = 0;
-  while (p->cap_n < L && ring[p->cap_n].diff) ++p->cap_n;
-  p->cap_s = L;
+  while (p->cap_n < R && ring[p->cap_n].diff) ++p->cap_n;
+  p->cap_s = R;
   while (p->cap_s > p->cap_n && ring[p->cap_s - 1].diff) --p->cap_s;
-  p->fwd_parts = (L <= kFwdChunk) ? 1 : 2 + (p->cap_s - p->cap_n + kFwdChunk - 1) / kFwdChunk;
+  p->fwd_parts = (R <= kFwdChunk) ? 1 : 2 + (p->cap_s - p->cap_n + kFwdChunk - 1) / kFwdChunk;
 
   // ---- starting values d^{l0}_{m,n} (Eq. "initial_values" and Sec. 3.3 symmetries) ----
   std::vector<long double> lf2 = log2_factorials(2 * L + 2);
@@ -287,22 +333,34 @@ int make_plan(Plan* p) {
       }
     }
 
-  // ---- ring fold factors and fine-grid weights of the forward quadrature ----
-  std::vector<double> nu(L, 2.0);
-  nu[L - 1] = 1.0;
+  // ---- ring weights and fine-grid weights of the forward quadrature ----
+  // MW / MWSS: fold factors of the torus trapezoid onto the rings (1 on a ring that is its own
+  // reflection, theta = 0 or pi; 2 elsewhere).  DH: the DH weights times the phi step.
+  std::vector<double> nu(R, 2.0);
+  if (p->sampling == S2GB_DH) {
+    nu = dh_ring_weights(L);
+  } else {
+    nu[R - 1] = 1.0;
+    if (p->sampling == S2GB_MWSS) nu[0] = 1.0;
+  }
   const int NF = p->Nfft;
+  const int TS = p->TS;
   std::vector<double> wf(NF);
-  {
+  if (TS) {
     // W_B(x) = sum_{|k| <= 2L-2} What(k) e^{ikx},  What(0) = 1/pi, What(k) = 1/(pi (1-k^2)) for
     // even k != 0 and 0 for odd k: the Fourier series of |sin x|/2, truncated.  Sampled at
-    // x_j = pi/T + 2 pi j/NF; all constants of the pipeline folded in (see api.cu).
-    const long double cst = (2.0L * kPiL / T) * (2.0L * kPiL / T) / ((long double)T * NF);
-    const long long TN2 = 2LL * T * NF;
+    // x_j = x_0 + 2 pi j/NF with x_0 the first torus point (pi/TS on MW, 0 on MWSS), so that the
+    // grid's phase factors cancel; all constants of the pipeline, (2 pi/P)(2 pi/TS)/(TS NF), folded
+    // in (see api.cu).
+    const int shift = p->sampling == S2GB_MWSS ? 0 : 1;
+    const long double cst = (2.0L * kPiL / p->P) * (2.0L * kPiL / TS) / ((long double)TS * NF);
+    const long long TN2 = 2LL * TS * NF;
     for (int j = 0; j < NF; ++j) {
       long double acc = 0.0L;
       for (int k = 2; k <= 2 * L - 2; k += 2) {
-        long long num = ((long long)k * ((long long)NF + 2LL * j * T)) % TN2;   // k x_j = pi num/(T NF)
-        double ang = (double)num * (kPi / ((double)T * NF));
+        // k x_j = pi num / (TS NF)
+        long long num = ((long long)k * ((long long)shift * NF + 2LL * j * TS)) % TN2;
+        double ang = (double)num * (kPi / ((double)TS * NF));
         acc += (long double)(std::cos(ang) / (1.0 - (double)k * k));
       }
       wf[j] = (double)((1.0L / kPiL + (2.0L / kPiL) * acc) * cst);
@@ -344,8 +402,8 @@ int make_plan(Plan* p) {
     p->coef = nullptr;
     bytes += n * sizeof(float);
     bytes -= coef_bytes;
-    std::vector<float> v32(L);
-    for (int t = 0; t < L; ++t) v32[t] = (float)ring[t].v;
+    std::vector<float> v32(R);
+    for (int t = 0; t < R; ++t) v32[t] = (float)ring[t].v;
     if ((rc = upload(&p->v32, v32, &bytes))) return rc;
     p->device_bytes = bytes;
   }
@@ -355,6 +413,7 @@ int make_plan(Plan* p) {
   const cufftType ty = f64 ? CUFFT_Z2Z : CUFFT_C2C;
   const int S[2] = {nN, p->max_batch * nN};
   const int MR = p->MR;
+  const int P = p->P;
   for (int q = 0; q < 2; ++q) {
     if (q == 1 && S[1] == S[0]) {
       p->fft_phi[1] = p->fft_phi[0];
@@ -363,19 +422,22 @@ int make_plan(Plan* p) {
       p->fft_N[1] = p->fft_N[0];
       continue;
     }
-    if (p->real) {   // rings of T real samples <-> orders m = 0 .. L-1
-      if ((rc = make_fft(&p->fft_phi[q], T, S[q] * L, 1, T, f64 ? CUFFT_D2Z : CUFFT_R2C, &p->fft_work, L))) return rc;
-      if ((rc = make_fft(&p->fft_phi_c2r[q], T, S[q] * L, 1, L, f64 ? CUFFT_Z2D : CUFFT_C2R, &p->fft_work, T))) return rc;
+    if (p->real) {   // rings of P = 2L-1 real samples <-> orders m = 0 .. L-1
+      if ((rc = make_fft(&p->fft_phi[q], P, S[q] * R, 1, P, f64 ? CUFFT_D2Z : CUFFT_R2C, &p->fft_work, L))) return rc;
+      if ((rc = make_fft(&p->fft_phi_c2r[q], P, S[q] * R, 1, L, f64 ? CUFFT_Z2D : CUFFT_C2R, &p->fft_work, P))) return rc;
     } else {
-      if ((rc = make_fft(&p->fft_phi[q], T, S[q] * L, 1, T, ty, &p->fft_work))) return rc;
+      if ((rc = make_fft(&p->fft_phi[q], P, S[q] * R, 1, P, ty, &p->fft_work))) return rc;
     }
-    if ((rc = make_fft(&p->fft_T[q], T, S[q] * MR, 1, T, ty, &p->fft_work))) return rc;
-    if ((rc = make_fft(&p->fft_N[q], NF, S[q] * MR, 1, NF, ty, &p->fft_work))) return rc;
     p->fft_made[q] = true;
+    if (TS) {
+      if ((rc = make_fft(&p->fft_T[q], TS, S[q] * MR, 1, TS, ty, &p->fft_work))) return rc;
+      if ((rc = make_fft(&p->fft_N[q], NF, S[q] * MR, 1, NF, ty, &p->fft_work))) return rc;
+      p->fft_op_made[q] = true;
+    }
   }
   if (p->wigner) {
     const int K = 2 * p->N - 1;
-    if ((rc = make_fft(&p->fft_gam[0], K, L * T, L * T, 1, ty, &p->fft_work))) return rc;
+    if ((rc = make_fft(&p->fft_gam[0], K, R * P, R * P, 1, ty, &p->fft_work))) return rc;
     p->fft_gam_made = true;
   }
   return S2GB_OK;
@@ -395,27 +457,47 @@ void free_plan(Plan* p) {
   cudaFree(p->nu);
   cudaFree(p->wfine);
   cudaFree(p->n_of);
-  for (int q = 0; q < 2; ++q)
+  for (int q = 0; q < 2; ++q) {
     if (p->fft_made[q]) {
       cufftDestroy(p->fft_phi[q]);
       if (p->real) cufftDestroy(p->fft_phi_c2r[q]);
+    }
+    if (p->fft_op_made[q]) {
       cufftDestroy(p->fft_T[q]);
       cufftDestroy(p->fft_N[q]);
     }
+  }
   if (p->fft_gam_made) cufftDestroy(p->fft_gam[0]);
 }
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-size_t workspace_bytes(const Plan& p, int batch) {
-  if (batch < 1 || batch > p.max_batch) return 0;
+// Workspace regions of a call on `batch` signals (bytes, before alignment):
+//   A: phi spectra [S][R][SW] and the fine theta grid [S][MR][Nfft] (forward), ring spectra (inverse)
+//   B: theta-torus rows [S][MR][max(T, TS)], or a signal-sized buffer [S][R][SW] (Wigner, DH)
+//   C: a second signal-sized buffer (Wigner: the gamma DFT)
+//   D: partial coefficients of the ring-chunked forward theta stage (R > kFwdChunk)
+// with S = batch * nN and SW = P (complex signals) or L (real signals: orders m >= 0).
+void workspace_regions(const Plan& p, int batch, size_t out[4]) {
   const size_t es = p.precision == S2GB_FP64 ? 16 : 8;
   const size_t S = (size_t)batch * p.nN;
-  const size_t bufA = S * p.MR * (size_t)(p.Nfft > p.L ? p.Nfft : p.L) * es;
-  const size_t bufB = S * p.MR * (size_t)p.T * es;
-  const size_t bufC = p.wigner ? S * p.L * (size_t)p.T * es : 0;
-  const size_t bufD = p.fwd_parts > 1 ? (size_t)p.fwd_parts * S * p.L * (size_t)p.MR * es : 0;
-  return align256(bufA) + align256(bufB) + align256(bufC) + align256(bufD) + align256(p.fft_work) + 256;
+  const size_t SW = p.real ? (size_t)p.L : (size_t)p.P;
+  const size_t spectra = (size_t)p.R * SW;
+  size_t wA = (size_t)p.MR * (size_t)(p.Nfft > p.L ? p.Nfft : p.L);
+  if (spectra > wA) wA = spectra;
+  size_t wB = (size_t)p.MR * (size_t)(p.TS > p.T ? p.TS : p.T);
+  if (spectra > wB) wB = spectra;
+  out[0] = S * wA * es;
+  out[1] = S * wB * es;
+  out[2] = p.wigner ? S * spectra * es : 0;
+  out[3] = p.fwd_parts > 1 ? (size_t)p.fwd_parts * S * p.L * (size_t)p.MR * es : 0;
+}
+
+size_t workspace_bytes(const Plan& p, int batch) {
+  if (batch < 1 || batch > p.max_batch) return 0;
+  size_t r[4];
+  workspace_regions(p, batch, r);
+  return align256(r[0]) + align256(r[1]) + align256(r[2]) + align256(r[3]) + align256(p.fft_work) + 256;
 }
 
 }  // namespace s2gb

@@ -25,7 +25,7 @@ struct RingData {
   double lc_hi;    // log2 cos(theta/2) (lc_hi = -inf at theta = pi)
   double lc_lo;
   int north;       // theta < pi/2
-  int pole;        // theta == pi (last MW ring)
+  int pole;        // 1: theta == pi (cos(theta/2) = 0), 2: theta == 0 (sin(theta/2) = 0), else 0
   int diff;        // sin(theta) < kPoleSin: difference form of the recursion
   int pad;
 };
@@ -52,12 +52,17 @@ constexpr int kFwdChunk = 2048;  // rings per CTA of the forward theta kernel
 
 struct Plan {
   int L = 0, spin = 0, N = 0, precision = 0, max_batch = 0, device = 0;
-  int T = 0;        // 2L - 1
+  int sampling = S2GB_MW;
+  int T = 0;        // 2L - 1 (number of orders)
+  int R = 0;        // theta rings of the sampling: L (MW), L + 1 (MWSS), 2L (DH)
+  int P = 0;        // phi samples per ring: 2L - 1 (MW, DH), 2L (MWSS)
+  int TS = 0;       // theta-torus length of the forward quadrature operator: 2L - 1 (MW), 2L
+                    // (MWSS), 0 (DH: explicit ring weights, no operator)
   int nN = 1;       // number of n values (1 for the sphere, 2N-1 for Wigner)
   int Nfft = 0;     // length of the fine theta grid of the forward quadrature (>= 4L-3)
-  int cap_n = 0;    // rings [0, cap_n) and [cap_s, L) use the difference form of the recursion
+  int cap_n = 0;    // rings [0, cap_n) and [cap_s, R) use the difference form of the recursion
   int cap_s = 0;
-  int fwd_parts = 1;  // forward theta stage in one launch (L <= 2048) or in ring chunks
+  int fwd_parts = 1;  // forward theta stage in one launch (R <= kFwdChunk) or in ring chunks
   bool wigner = false;
   bool real = false;  // real signals (spin 0): orders m >= 0 only, f real, flm [L][L]
   int MR = 0;         // order rows of the theta-direction buffers: T (complex) or L (real)
@@ -65,13 +70,14 @@ struct Plan {
   // device tables
   double* coef = nullptr;      // [nN][T][L][kCoefPerStepN] (m index = m + L - 1, step j); FP64 plans
   float* coef32 = nullptr;     // the same table rounded to float (FP32 plans)
-  float* v32 = nullptr;        // [L] ring variable v rounded to float (FP32 plans)
-  RingData* ring = nullptr;    // [L]
+  float* v32 = nullptr;        // [R] ring variable v rounded to float (FP32 plans)
+  RingData* ring = nullptr;    // [R]
   SeedData* seed = nullptr;    // [nN][T]
   double* scale_inv = nullptr; // [nN][L] per-degree factor of the inverse theta stage
   double* scale_fwd = nullptr; // [nN][L] per-degree factor of the forward theta stage
   double* wfine = nullptr;     // [Nfft] weights on the fine grid (constants folded in)
-  double* nu = nullptr;        // [L] ring fold factors of the forward quadrature (2, ..., 2, 1)
+  double* nu = nullptr;        // [R] ring weights of the forward quadrature: fold factors
+                               // (MW 2, ..., 2, 1; MWSS 1, 2, ..., 2, 1) or DH weights * 2 pi/P
   int* n_of = nullptr;         // [nN] n for each n index
   size_t device_bytes = 0;
 
@@ -84,12 +90,13 @@ struct Plan {
   int* live0 = nullptr;        // [nN][T][ceil(L/32)] first degree with a live chain in 32 rings
 
   // cuFFT plans: index 0 = one signal, 1 = max_batch signals (rows of the whole batch)
-  cufftHandle fft_phi[2] = {0, 0};   // length T along rows of length T, S*L rows (real: R2C)
+  cufftHandle fft_phi[2] = {0, 0};   // length P along rows of length P, S*R rows (real: R2C)
   cufftHandle fft_phi_c2r[2] = {0, 0};   // real plans: the inverse direction (C2R)
-  cufftHandle fft_T[2] = {0, 0};     // length T, S*T rows
-  cufftHandle fft_N[2] = {0, 0};     // length Nfft, S*T rows
-  cufftHandle fft_gam[1] = {0};      // length 2N-1, stride L*T, L*T rows (one signal)
+  cufftHandle fft_T[2] = {0, 0};     // length TS, S*MR rows (MW, MWSS)
+  cufftHandle fft_N[2] = {0, 0};     // length Nfft, S*MR rows (MW, MWSS)
+  cufftHandle fft_gam[1] = {0};      // length 2N-1, stride R*P, R*P rows (one signal)
   bool fft_made[2] = {false, false};
+  bool fft_op_made[2] = {false, false};   // fft_T / fft_N exist (TS > 0)
   bool fft_gam_made = false;
   size_t fft_work = 0;               // max cuFFT work area over all plans
   std::mutex fft_mutex;
@@ -102,10 +109,12 @@ struct InvArgs {
   long long s_sig;      // stride between signals in out (elements)
   long long s_t;        // stride between rings
   long long s_m;        // stride between orders
-  int m_mod;            // 1: column = m mod T, 0: column = m + L - 1
+  int m_mod;            // 1: column = m mod mmod, 0: column = m + L - 1
+  int mmod;             // P (the phi DFT length)
   int nsig;             // number of signals per n (batch)
   int nN;
   int L;
+  int nring;            // rings t < nring (R)
   const double* coef;
   const RingData* ring;
   const SeedData* seed;
@@ -126,8 +135,9 @@ struct FwdArgs {
   const void* g;        // input with strides below
   void* flm;            // [S][L][T]
   long long s_sig, s_t, s_m;
-  int m_mod;
-  int use_nu;           // multiply g by the fold factors nu_t
+  int m_mod;            // as in InvArgs
+  int mmod;
+  int use_nu;           // multiply g by the ring weights nu_t
   int nsig;
   int nN;
   int L;
@@ -184,6 +194,10 @@ cudaError_t launch_pad(const Plan& p, const void* X, void* Y, int rows, cudaStre
 cudaError_t launch_truncate(const Plan& p, const void* Y, void* X, int rows, cudaStream_t st);
 cudaError_t launch_weight_fine(const Plan& p, void* Y, int rows, cudaStream_t st);
 cudaError_t launch_nu_extend(const Plan& p, void* X, int rows, cudaStream_t st);
+// ring spectra [nsig][R][W]: ring t times nu_t (adjoint of the DH forward's ring weights)
+cudaError_t launch_ring_weight(const Plan& p, void* X, int nsig, int W, cudaStream_t st);
+// ring spectra [nsig][R][P] of MWSS plans: column L (the phi frequency no order owns) set to 0
+cudaError_t zero_nyquist(const Plan& p, void* X, int nsig, cudaStream_t st);
 // out[i] = sum of the parts in order, for the columns (c0 + m, rows of ld) of orders |m| in [mlo, mhi)
 cudaError_t launch_sum_parts(const Plan& p, const void* parts, void* out, int nsig, int nparts,
                              int mlo, int mhi, int ld, int c0, cudaStream_t st);
@@ -196,5 +210,6 @@ cudaError_t launch_gamma_reorder(const Plan& p, const void* in, void* out, int b
 int make_plan(Plan* p);
 void free_plan(Plan* p);
 size_t workspace_bytes(const Plan& p, int batch);
+void workspace_regions(const Plan& p, int batch, size_t out[4]);   // bytes of regions A, B, C, D
 
 }  // namespace s2gb

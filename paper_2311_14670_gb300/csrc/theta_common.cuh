@@ -27,7 +27,7 @@ __device__ __forceinline__ double flip_sign(double x, unsigned mask) {
 // d^{l0}_{m,n}(theta) = sign 2^p sin(theta/2)^a cos(theta/2)^b, evaluated as 2^X with X in
 // double-double, returned as x * 2^-E (E = 0 if the value is not tiny).
 __device__ __forceinline__ void seed_value(const SeedData& sd, const RingData& rd, double& x, int& E) {
-  if ((rd.pole && sd.b > 0)) { x = 0.0; E = 0; return; }      // cos(pi/2) = 0
+  if ((rd.pole == 1 && sd.b > 0) || (rd.pole == 2 && sd.a > 0)) { x = 0.0; E = 0; return; }  // cos(pi/2), sin(0)
   dd X = {sd.p_hi, sd.p_lo};
   if (sd.a) {
     dd t = two_prod(rd.ls_hi, (double)sd.a);

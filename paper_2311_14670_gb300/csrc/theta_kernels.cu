@@ -62,7 +62,7 @@ __device__ __forceinline__ void inverse_body(const InvArgs& a, int m, int ni, in
   for (int i = 0; i < KT; ++i) {
     const int t = tile * KT * nt + i * nt + tid;
     tt[i] = t;
-    if (t < L) {
+    if (t < a.nring) {
       const RingData rd = a.ring[t];
       seed_value(sd, rd, x[i], E[i]);
       v[i] = rd.v;
@@ -141,10 +141,10 @@ __device__ __forceinline__ void inverse_body(const InvArgs& a, int m, int ni, in
   for (int b = 0; b < NBX; ++b) {
     const Slot sl = slot_of<NB, PAIR>(b, sig0, a.nsig, a.nN, ni, m, n, L);
     if (sl.sig_off < 0) continue;
-    const long long col = a.m_mod ? (sl.m >= 0 ? sl.m : sl.m + T) : sl.mi;
+    const long long col = a.m_mod ? (sl.m >= 0 ? sl.m : sl.m + a.mmod) : sl.mi;
 #pragma unroll
     for (int i = 0; i < KT; ++i) {
-      if (tt[i] < L) {
+      if (tt[i] < a.nring) {
         double2* o = reinterpret_cast<double2*>(a.out) + (size_t)sl.sig_off * a.s_sig + tt[i] * a.s_t + col * a.s_m;
         *o = acc[i][b];
       }
@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(128) theta_inverse_kernel(InvArgs a, int ntile
   if (PAIR && n == 0 && m < 0) return;        // produced by the CTA of -m
   const int l0 = a.seed[(size_t)ni * (2 * L - 1) + m + L - 1].l0;   // max(|m|, |n|)
   // Does this tile contain a ring that needs the difference form?
-  const int t_lo = tile * KT * blockDim.x, t_hi = min(L, t_lo + KT * (int)blockDim.x) - 1;
+  const int t_lo = tile * KT * blockDim.x, t_hi = min(a.nring, t_lo + KT * (int)blockDim.x) - 1;
   const bool diff = a.ring[t_lo].diff || a.ring[t_hi].diff;
   if (diff) inverse_body<KT, NB, true, PAIR>(a, m, ni, n, tile, l0, hs, cs);
   else inverse_body<KT, NB, false, PAIR>(a, m, ni, n, tile, l0, hs, cs);
@@ -241,7 +241,7 @@ __global__ void __launch_bounds__(128) theta_forward_kernel(FwdArgs a) {
     const int t = r0 + ring_of<KT>(pos / nt, pos % nt, nt, R, act);
     double2 g = make_double2(0.0, 0.0);
     if (act && sl.sig_off >= 0) {
-      const long long col = a.m_mod ? (sl.m >= 0 ? sl.m : sl.m + T) : sl.mi;
+      const long long col = a.m_mod ? (sl.m >= 0 ? sl.m : sl.m + a.mmod) : sl.mi;
       g = reinterpret_cast<const double2*>(a.g)[(size_t)sl.sig_off * a.s_sig + t * a.s_t + col * a.s_m];
       const double w = (a.use_nu ? a.nu[t] : 1.0) * sl.sign;
       g.x *= w; g.y *= w;
@@ -352,7 +352,7 @@ __global__ void __launch_bounds__(128) theta_forward_kernel(FwdArgs a) {
 template <int KT, int NB, bool PAIR>
 cudaError_t launch_inv(const Plan& p, const InvArgs& a, cudaStream_t st) {
   const int nt = 128;
-  const int ntiles = (p.L + KT * nt - 1) / (KT * nt);
+  const int ntiles = (a.nring + KT * nt - 1) / (KT * nt);
   dim3 grid(a.nrank * ntiles, PAIR ? (a.nN + 1) / 2 : a.nN, (a.nsig + NB - 1) / NB);
   theta_inverse_kernel<KT, NB, PAIR><<<grid, nt, 0, st>>>(a, ntiles);
   return launched();
@@ -360,8 +360,8 @@ cudaError_t launch_inv(const Plan& p, const InvArgs& a, cudaStream_t st) {
 
 template <int NB, bool PAIR>
 cudaError_t launch_inv_nb(const Plan& p, const InvArgs& a, cudaStream_t st) {
-  if (p.L <= 128) return launch_inv<1, NB, PAIR>(p, a, st);
-  if (p.L <= 512) return launch_inv<2, NB, PAIR>(p, a, st);
+  if (a.nring <= 128) return launch_inv<1, NB, PAIR>(p, a, st);
+  if (a.nring <= 512) return launch_inv<2, NB, PAIR>(p, a, st);
   return launch_inv<4, NB, PAIR>(p, a, st);
 }
 
@@ -380,29 +380,29 @@ cudaError_t launch_fwd(const Plan& p, const FwdArgs& a, int nt, cudaStream_t st)
 
 template <int NB, bool PAIR>
 cudaError_t launch_fwd_nb(const Plan& p, const FwdArgs& a0, cudaStream_t st) {
-  const int L = p.L;
+  const int R = p.R;       // rings of the sampling
   FwdArgs a = a0;
   a.row0 = 0;
-  a.nrows = L;
+  a.nrows = R;
   a.part = nullptr;
   a.part_off = 0;
-  if (L <= 128) return launch_fwd<1, NB, 1, PAIR>(p, a, ((L + 31) / 32) * 32, st);
-  if (L <= 256) return launch_fwd<2, NB, 1, PAIR>(p, a, 128, st);
-  if (L <= 512) return launch_fwd<4, NB, 0, PAIR>(p, a, 128, st);
+  if (R <= 128) return launch_fwd<1, NB, 1, PAIR>(p, a, ((R + 31) / 32) * 32, st);
+  if (R <= 256) return launch_fwd<2, NB, 1, PAIR>(p, a, 128, st);
+  if (R <= 512) return launch_fwd<4, NB, 0, PAIR>(p, a, 128, st);
   // Unpaired: 16 rings per thread (64 threads) halve the cross-thread reduction; paired CTAs carry
   // twice the signal slots and run better with 8 rings per thread (measured on GB300).
-  if (L <= 1024) {
+  if (R <= 1024) {
     if (PAIR) return launch_fwd<8, NB, 0, PAIR>(p, a, 128, st);
-    return launch_fwd<16, NB, 0, PAIR>(p, a, ((L + 16 * 32 - 1) / (16 * 32)) * 32, st);
+    return launch_fwd<16, NB, 0, PAIR>(p, a, ((R + 16 * 32 - 1) / (16 * 32)) * 32, st);
   }
-  // KT = 16 slots of nt rings: the polar caps (sin theta < kPoleSin, t < 0.05 L) fit in the
-  // first and last slot because nt >= L/16.
-  if (L <= kFwdChunk) return launch_fwd<16, NB, 0, PAIR>(p, a, ((L + 16 * 32 - 1) / (16 * 32)) * 32, st);
-  // L > kFwdChunk: the rings are split into the two polar caps (difference form throughout) and
+  // KT = 16 slots of nt rings: the polar caps (sin theta < kPoleSin, fewer than 0.05 R rings at
+  // either end of an equiangular grid) fit in the first and last slot because nt >= R/16.
+  if (R <= kFwdChunk) return launch_fwd<16, NB, 0, PAIR>(p, a, ((R + 16 * 32 - 1) / (16 * 32)) * 32, st);
+  // R > kFwdChunk: the rings are split into the two polar caps (difference form throughout) and
   // interior chunks of at most kFwdChunk rings (plain form); each launch writes a partial result
   // that a fixed-order sum turns into flm.
   if (!a0.part) return cudaErrorInvalidValue;
-  const long long part_elems = (long long)a.nsig * a.nN * L * a.flm_ld;
+  const long long part_elems = (long long)a.nsig * a.nN * p.L * a.flm_ld;
   int q = 0;
   cudaError_t e;
   // threads per CTA: KT * nt >= rows and nt <= rows (the last slot holds the last nt rings)
@@ -410,7 +410,7 @@ cudaError_t launch_fwd_nb(const Plan& p, const FwdArgs& a0, cudaStream_t st) {
   a.part = a0.part;
   a.row0 = 0; a.nrows = p.cap_n; a.part_off = part_elems * q++;
   if ((e = launch_fwd<4, NB, 1, PAIR>(p, a, nt_for(a.nrows, 4), st)) != cudaSuccess) return e;
-  a.row0 = p.cap_s; a.nrows = L - p.cap_s; a.part_off = part_elems * q++;
+  a.row0 = p.cap_s; a.nrows = R - p.cap_s; a.part_off = part_elems * q++;
   if ((e = launch_fwd<4, NB, 1, PAIR>(p, a, nt_for(a.nrows, 4), st)) != cudaSuccess) return e;
   const int interior = p.cap_s - p.cap_n;
   const int nchunk = (interior + kFwdChunk - 1) / kFwdChunk;
@@ -450,10 +450,10 @@ cudaError_t launch_theta_forward(const Plan& p, const FwdArgs& a, cudaStream_t s
   if (a.dtab) return launch_theta_forward_pre(p, a, st);
   if (p.precision == S2GB_FP32) return launch_theta_forward_f32(p, a, st);
   if (paired(p)) {
-    if (a.nsig >= 2 && p.L <= 1024) return launch_fwd_nb<2, true>(p, a, st);
+    if (a.nsig >= 2 && p.R <= 1024) return launch_fwd_nb<2, true>(p, a, st);
     return launch_fwd_nb<1, true>(p, a, st);
   }
-  if (a.nsig >= 4 && p.L <= 1024) return launch_fwd_nb<4, false>(p, a, st);
+  if (a.nsig >= 4 && p.R <= 1024) return launch_fwd_nb<4, false>(p, a, st);
   if (a.nsig >= 2) return launch_fwd_nb<2, false>(p, a, st);
   return launch_fwd_nb<1, false>(p, a, st);
 }

@@ -100,7 +100,7 @@ __device__ __forceinline__ void inverse_body_f32(const InvArgs& a, int m, int ni
   for (int i = 0; i < KT; ++i) {
     const int t = tile * KT * nt + i * nt + tid;
     tt[i] = t;
-    if (t < L) {
+    if (t < a.nring) {
       const RingData rd = a.ring[t];
       seed_value_f32(sd, rd, x[i], E[i]);
       v[i] = a.v32[t];
@@ -191,8 +191,8 @@ __device__ __forceinline__ void inverse_body_f32(const InvArgs& a, int m, int ni
 
 #pragma unroll
   for (int i = 0; i < KT; ++i) {
-    if (tt[i] < L) {
-      const long long col = a.m_mod ? (m >= 0 ? m : m + T) : mi;
+    if (tt[i] < a.nring) {
+      const long long col = a.m_mod ? (m >= 0 ? m : m + a.mmod) : mi;
 #pragma unroll
       for (int b = 0; b < NB; ++b) {
         const int sig = sig0 + b;
@@ -215,7 +215,7 @@ __global__ void __launch_bounds__(128) theta_inverse_kernel_f32(InvArgs a, int n
   const int m = a.mpos ? rank : m_of_rank(rank);
   const int ni = blockIdx.y;
   const int l0 = a.seed[(size_t)ni * (2 * L - 1) + m + L - 1].l0;
-  const int t_lo = tile * KT * blockDim.x, t_hi = min(L, t_lo + KT * (int)blockDim.x) - 1;
+  const int t_lo = tile * KT * blockDim.x, t_hi = min(a.nring, t_lo + KT * (int)blockDim.x) - 1;
   const bool diff = a.ring[t_lo].diff || a.ring[t_hi].diff;
   if (diff) inverse_body_f32<KT, NB, true>(a, m, ni, tile, l0, hs, cs);
   else inverse_body_f32<KT, NB, false>(a, m, ni, tile, l0, hs, cs);
@@ -273,11 +273,12 @@ __global__ void __launch_bounds__(128) theta_forward_kernel_f32(FwdArgs a) {
   }
   if (l0 >= L) return;
 
-  const long long col = a.m_mod ? (m >= 0 ? m : m + T) : mi;
+  const long long col = a.m_mod ? (m >= 0 ? m : m + a.mmod) : mi;
+  const int R = a.nrows;                 // rings t < R (one launch covers every ring)
   for (int q = tid; q < NB * rows; q += nt) {
     const int b = q / rows, pos = q % rows, sig = sig0 + b;
     bool act;
-    const int t = ring_of<KT>(pos / nt, pos % nt, nt, L, act);
+    const int t = ring_of<KT>(pos / nt, pos % nt, nt, R, act);
     float2 g = make_float2(0.f, 0.f);
     if (act && sig < a.nsig) {
       g = reinterpret_cast<const float2*>(a.g)[(size_t)(sig * a.nN + ni) * a.s_sig + t * a.s_t + col * a.s_m];
@@ -287,7 +288,7 @@ __global__ void __launch_bounds__(128) theta_forward_kernel_f32(FwdArgs a) {
   }
   for (int pos = tid; pos < rows; pos += nt) {
     bool act;
-    const int t = ring_of<KT>(pos / nt, pos % nt, nt, L, act);
+    const int t = ring_of<KT>(pos / nt, pos % nt, nt, R, act);
     vs[pos] = act ? a.v32[t] : 0.0f;
   }
   __syncthreads();
@@ -299,7 +300,7 @@ __global__ void __launch_bounds__(128) theta_forward_kernel_f32(FwdArgs a) {
 #pragma unroll
   for (int i = 0; i < KT; ++i) {
     bool act;
-    const int t = ring_of<KT>(i, tid, nt, L, act);
+    const int t = ring_of<KT>(i, tid, nt, R, act);
     if (act) {
       const RingData rd = a.ring[t];
       seed_value_f32(sd, rd, x[i], E[i]);
@@ -383,7 +384,7 @@ __global__ void __launch_bounds__(128) theta_forward_kernel_f32(FwdArgs a) {
 template <int KT, int NB>
 cudaError_t launch_inv32(const Plan& p, const InvArgs& a, cudaStream_t st) {
   const int nt = 128;
-  const int ntiles = (p.L + KT * nt - 1) / (KT * nt);
+  const int ntiles = (a.nring + KT * nt - 1) / (KT * nt);
   dim3 grid(a.nrank * ntiles, a.nN, (a.nsig + NB - 1) / NB);
   theta_inverse_kernel_f32<KT, NB><<<grid, nt, 0, st>>>(a, ntiles);
   return launched();
@@ -391,8 +392,8 @@ cudaError_t launch_inv32(const Plan& p, const InvArgs& a, cudaStream_t st) {
 
 template <int NB>
 cudaError_t launch_inv32_nb(const Plan& p, const InvArgs& a, cudaStream_t st) {
-  if (p.L <= 128) return launch_inv32<1, NB>(p, a, st);
-  if (p.L <= 512) return launch_inv32<2, NB>(p, a, st);
+  if (a.nring <= 128) return launch_inv32<1, NB>(p, a, st);
+  if (a.nring <= 512) return launch_inv32<2, NB>(p, a, st);
   return launch_inv32<4, NB>(p, a, st);
 }
 
@@ -409,13 +410,16 @@ cudaError_t launch_fwd32(const Plan& p, const FwdArgs& a, int nt, cudaStream_t s
 }
 
 template <int NB>
-cudaError_t launch_fwd32_nb(const Plan& p, const FwdArgs& a, cudaStream_t st) {
-  const int L = p.L;
-  if (L <= 128) return launch_fwd32<1, NB, 1>(p, a, ((L + 31) / 32) * 32, st);
-  if (L <= 256) return launch_fwd32<2, NB, 1>(p, a, 128, st);
-  if (L <= 512) return launch_fwd32<4, NB, 0>(p, a, 128, st);
-  if (L <= 1024) return launch_fwd32<8, NB, 0>(p, a, 128, st);
-  const int nt = ((L + 16 * 32 - 1) / (16 * 32)) * 32;
+cudaError_t launch_fwd32_nb(const Plan& p, const FwdArgs& a0, cudaStream_t st) {
+  const int R = p.R;       // rings of the sampling (float32 plans have R <= kFwdChunk)
+  FwdArgs a = a0;
+  a.row0 = 0;
+  a.nrows = R;
+  if (R <= 128) return launch_fwd32<1, NB, 1>(p, a, ((R + 31) / 32) * 32, st);
+  if (R <= 256) return launch_fwd32<2, NB, 1>(p, a, 128, st);
+  if (R <= 512) return launch_fwd32<4, NB, 0>(p, a, 128, st);
+  if (R <= 1024) return launch_fwd32<8, NB, 0>(p, a, 128, st);
+  const int nt = ((R + 16 * 32 - 1) / (16 * 32)) * 32;
   if (nt > 128) return cudaErrorInvalidConfiguration;
   return launch_fwd32<16, NB, 0>(p, a, nt, st);
 }
@@ -429,7 +433,7 @@ cudaError_t launch_theta_inverse_f32(const Plan& p, const InvArgs& a, cudaStream
 }
 
 cudaError_t launch_theta_forward_f32(const Plan& p, const FwdArgs& a, cudaStream_t st) {
-  if (a.nsig >= 8 && p.L <= 1024) return launch_fwd32_nb<8>(p, a, st);
+  if (a.nsig >= 8 && p.R <= 1024) return launch_fwd32_nb<8>(p, a, st);
   if (a.nsig >= 4) return launch_fwd32_nb<4>(p, a, st);
   if (a.nsig >= 2) return launch_fwd32_nb<2>(p, a, st);
   return launch_fwd32_nb<1>(p, a, st);

@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(128) theta_inverse_pre_kernel(InvArgs a, int n
   for (int b = 0; b < NBX; ++b) {
     const Slot sl = slot_of<NB, PAIR>(b, sig0, a.nsig, a.nN, ni, m, n, L);
     if (sl.sig_off < 0) continue;
-    const long long col = a.m_mod ? (sl.m >= 0 ? sl.m : sl.m + T) : sl.mi;
+    const long long col = a.m_mod ? (sl.m >= 0 ? sl.m : sl.m + a.mmod) : sl.mi;
 #pragma unroll
     for (int i = 0; i < KT; ++i) {
       const int t = tile * KT * nt + i * nt + tid;
@@ -277,7 +277,7 @@ __global__ void __launch_bounds__(128) theta_forward_pre_kernel(FwdArgs a) {
     const Slot sl = slot_of<NB, PAIR>(b, sig0, a.nsig, a.nN, ni, m, n, L);
     double2 g = make_double2(0.0, 0.0);
     if (t < L && sl.sig_off >= 0) {
-      const long long col = a.m_mod ? (sl.m >= 0 ? sl.m : sl.m + T) : sl.mi;
+      const long long col = a.m_mod ? (sl.m >= 0 ? sl.m : sl.m + a.mmod) : sl.mi;
       g = reinterpret_cast<const double2*>(a.g)[(size_t)sl.sig_off * a.s_sig + t * a.s_t + col * a.s_m];
       const double w = (a.use_nu ? a.nu[t] : 1.0) * sl.sign;
       g.x *= w; g.y *= w;

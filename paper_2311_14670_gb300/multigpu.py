@@ -75,19 +75,23 @@ def order_ranges(L: int, world: int, n_abs: int = 0, real: bool = False) -> list
     return [(cuts[r], cuts[r + 1]) for r in range(world)]
 
 
-def column_owner(L: int, ranges, layout: str) -> list:
-    """Rank owning each column: layout "mod" (T = 2L-1 columns, k = m mod T: ring spectra),
-    "centered" (T columns, m + L - 1: coefficients) or "real" (L columns, m >= 0: both arrays of
-    real-signal plans)."""
+def column_owner(L: int, ranges, layout: str, P: int | None = None) -> list:
+    """Rank owning each column: layout "mod" (P columns, k = m mod P: ring spectra, P = 2L-1 by
+    default; on MWSS P = 2L and the column k = L, which no order owns and every rank writes as 0,
+    goes to rank 0), "centered" (2L-1 columns, m + L - 1: coefficients) or "real" (L columns,
+    m >= 0: both arrays of real-signal plans)."""
     T = 2 * L - 1
-    owner = [-1] * (L if layout == "real" else T)
+    P = T if P is None else P
+    owner = [-1] * (L if layout == "real" else (P if layout == "mod" else T))
     for r, (lo, hi) in enumerate(ranges):
         for a in range(lo, hi):
             if layout == "real":
                 owner[a] = r
                 continue
             for m in ((0,) if a == 0 else (a, -a)):
-                owner[(m % T) if layout == "mod" else m + L - 1] = r
+                owner[(m % P) if layout == "mod" else m + L - 1] = r
+    if layout == "mod" and P > T and owner[L] < 0:
+        owner[L] = 0
     if min(owner) < 0:
         raise ValueError("the ranges do not cover every order")
     return owner
@@ -127,10 +131,10 @@ def sharded_inverse(plan, flm, ranges, rank: int, gather):
     import torch
 
     lo, hi = ranges[rank]
-    ft = torch.zeros(tuple(flm.shape), dtype=flm.dtype, device=flm.device)
+    ft = torch.zeros(plan.spectra_shape(flm.shape[0]), dtype=flm.dtype, device=flm.device)
     plan.inverse_theta_mrange(flm, lo, hi, out=ft)
     real = getattr(plan, "real", False)
-    ft = assemble_columns(gather(ft), column_owner(plan.L, ranges, "real" if real else "mod"))
+    ft = assemble_columns(gather(ft), column_owner(plan.L, ranges, "real" if real else "mod", ft.shape[-1]))
     return plan.inverse_phi(ft)
 
 

@@ -1,10 +1,11 @@
 """PyTorch-facing wrappers of libs2gb.so: plans, transforms on CUDA tensors, autograd.
 
-Tensors are CUDA tensors laid out as in ``include/s2gb.h``:
-  sphere:  f, flm of shape (batch, L, 2L-1), complex
-  Wigner:  f, flmn of shape (batch, 2N-1, L, 2L-1), complex
-  real signals (``real=True``, spin 0): f real of shape (batch, L, 2L-1), flm complex of shape
-           (batch, L, L) holding the orders m >= 0
+Tensors are CUDA tensors laid out as in ``include/s2gb.h``, with (R, P) the rings and phi samples
+of the sampling -- (L, 2L-1) for "mw", (L+1, 2L) for "mwss", (2L, 2L-1) for "dh":
+  sphere:  f of shape (batch, R, P), flm of shape (batch, L, 2L-1), complex
+  Wigner:  f of shape (batch, 2N-1, R, P), flmn of shape (batch, 2N-1, L, 2L-1), complex
+  real signals (``real=True``, spin 0; "mw" and "dh"): f real of shape (batch, R, P), flm complex
+           of shape (batch, L, L) holding the orders m >= 0
 complex128 / float64 for ``precision="fp64"`` plans, complex64 / float32 for ``"fp32"``.  Every call enqueues on
 PyTorch's current stream of the plan's device.  The autograd functions use the hand-written adjoint
 transforms for the backward pass (Sec. 5.2), which recompute the Wigner d-functions instead of
@@ -19,6 +20,12 @@ import torch
 from . import _native as nat
 
 _PRECISIONS = {"fp64": (nat.S2GB_FP64, torch.complex128), "fp32": (nat.S2GB_FP32, torch.complex64)}
+_SAMPLINGS = {"mw": nat.S2GB_MW, "mwss": nat.S2GB_MWSS, "dh": nat.S2GB_DH}
+
+
+def sampling_shape(L: int, sampling: str) -> tuple:
+    """(rings R, phi samples P) of a sampling scheme (Sec. 4.2)."""
+    return {"mw": (L, 2 * L - 1), "mwss": (L + 1, 2 * L), "dh": (2 * L, 2 * L - 1)}[sampling]
 _REAL_OF = {torch.complex128: torch.float64, torch.complex64: torch.float32}
 
 
@@ -28,8 +35,8 @@ class Plan:
     def __init__(self, L: int, spin: int = 0, N: int = 0, precision: str = "fp64", max_batch: int = 1,
                  device: int | torch.device | None = None, sampling: str = "mw", real: bool = False,
                  precompute: bool = False):
-        if sampling != "mw":
-            raise ValueError("only MW sampling is implemented")
+        if sampling not in _SAMPLINGS:
+            raise ValueError(f"sampling must be one of {list(_SAMPLINGS)}")
         if precision not in _PRECISIONS:
             raise ValueError(f"precision must be one of {list(_PRECISIONS)}")
         if device is None:
@@ -41,10 +48,12 @@ class Plan:
         self.dtype = _PRECISIONS[precision][1]          # coefficients (and complex signals)
         self.real = bool(real)
         self.precompute = bool(precompute)
+        self.sampling = sampling
+        self.R, self.P = sampling_shape(self.L, sampling)
         if self.real and (self.spin != 0 or self.N != 0):
             raise ValueError("real-signal plans are spin-0 sphere transforms (spin = 0, N = 0)")
         flags = (nat.S2GB_PLAN_REAL if self.real else 0) | (nat.S2GB_PLAN_PRECOMPUTE if self.precompute else 0)
-        self._h = nat.plan_create_flags(self.L, self.spin, self.N, nat.S2GB_MW, _PRECISIONS[precision][0],
+        self._h = nat.plan_create_flags(self.L, self.spin, self.N, _SAMPLINGS[sampling], _PRECISIONS[precision][0],
                                         self.max_batch, int(device), flags)
         self.signal_dtype = _REAL_OF[self.dtype] if self.real else self.dtype
         self._ws = {}
@@ -56,17 +65,25 @@ class Plan:
         return self.N >= 1
 
     def shape(self, batch: int) -> tuple:
-        """Shape of f (and of flm, for complex plans)."""
-        T = 2 * self.L - 1
-        return (batch, 2 * self.N - 1, self.L, T) if self.wigner else (batch, self.L, T)
+        """Shape of f."""
+        return (batch, 2 * self.N - 1, self.R, self.P) if self.wigner else (batch, self.R, self.P)
 
     def coef_shape(self, batch: int) -> tuple:
-        """Shape of flm (and of the theta stage's ring spectra)."""
-        return (batch, self.L, self.L) if self.real else self.shape(batch)
+        """Shape of flm."""
+        T = 2 * self.L - 1
+        if self.real:
+            return (batch, self.L, self.L)
+        return (batch, 2 * self.N - 1, self.L, T) if self.wigner else (batch, self.L, T)
+
+    def spectra_shape(self, batch: int) -> tuple:
+        """Shape of the theta stage's ring spectra ftilde[b][t][k] (k = m mod P; real: k = m)."""
+        return (batch, self.R, self.L if self.real else self.P)
 
     def _spec(self, kind: str):
         if kind == "signal":
             return self.shape, self.signal_dtype
+        if kind == "spectra":
+            return self.spectra_shape, self.dtype
         return self.coef_shape, self.dtype
 
     def workspace_bytes(self, batch: int) -> int:
@@ -135,20 +152,20 @@ class Plan:
 
     def inverse_theta(self, flm, out=None):
         """Theta stage of the inverse alone (s2gb_inverse_theta): ring spectra ftilde[b][t][k],
-        k = m mod T (real plans: k = m >= 0)."""
+        k = m mod P (real plans: k = m >= 0)."""
         return self.inverse_theta_mrange(flm, 0, self.L, out=out)
 
     def inverse_theta_mrange(self, flm, m_lo: int, m_hi: int, out=None):
         """Theta stage of the inverse for the orders with |m| in [m_lo, m_hi)
         (s2gb_inverse_theta_mrange); columns of other orders in ``out`` are left as they are."""
         batch = self._check(flm, "flm")
-        out = self._out(out, batch, "coef")
+        out = self._out(out, batch, "spectra")
         nat.inverse_theta_mrange(self._h, flm, out, batch, int(m_lo), int(m_hi), self._stream())
         return out
 
     def inverse_phi(self, ftilde, out=None, ws=None):
         """The phi stage of the sphere inverse: ring spectra -> f (s2gb_inverse_phi)."""
-        return self._run("inverse_phi", ftilde, out, ws, "coef", "signal")
+        return self._run("inverse_phi", ftilde, out, ws, "spectra", "signal")
 
     def forward_mrange(self, f, m_lo: int, m_hi: int, out=None, ws=None):
         """Forward transform whose theta stage covers the orders with |m| in [m_lo, m_hi) only
@@ -162,10 +179,10 @@ class Plan:
 
     def forward_theta(self, g, out=None):
         """Theta stage of the forward alone (s2gb_forward_theta): g[b][r][t] -> flm, r = m + L - 1
-        (real plans: r = m >= 0)."""
+        (real plans: r = m >= 0), t < R rings."""
         rows = self.L if self.real else 2 * self.L - 1
-        if g.dim() != 3 or tuple(g.shape[1:]) != (rows, self.L):
-            raise ValueError(f"g must have shape (batch, {rows}, L)")
+        if g.dim() != 3 or tuple(g.shape[1:]) != (rows, self.R):
+            raise ValueError(f"g must have shape (batch, {rows}, {self.R})")
         if g.dtype != self.dtype or g.device != self.device or not g.is_contiguous():
             raise ValueError("g must be a contiguous tensor of the plan's dtype and device")
         batch = g.shape[0]

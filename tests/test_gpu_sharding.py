@@ -72,4 +72,4 @@ def test_empty_and_out_of_bounds_order_ranges():
             p.forward_mrange(flm, lo, hi, out=out)
     w = Plan(8, N=2)
     with pytest.raises(_native.S2GBError):
-        w.inverse_phi(torch.zeros(w.shape(1), dtype=w.dtype, device=w.device))
+        w.inverse_phi(torch.zeros(w.spectra_shape(1), dtype=w.dtype, device=w.device))

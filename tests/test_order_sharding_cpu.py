@@ -49,6 +49,10 @@ def test_column_owner_layouts():
     assert [mod[m % T] for m in range(-3, 4)] == [1, 1, 0, 0, 0, 1, 1]
     with pytest.raises(ValueError):
         column_owner(L, [(0, 2)], "mod")
+    # MWSS ring spectra: P = 2L columns, k = m mod 2L; the column k = L has no order (rank 0)
+    ss = column_owner(L, ranges, "mod", 2 * L)
+    assert len(ss) == 2 * L and ss[L] == 0
+    assert [ss[m % (2 * L)] for m in range(-3, 4)] == [1, 1, 0, 0, 0, 1, 1]
 
 
 class _OraclePlan:
@@ -60,6 +64,9 @@ class _OraclePlan:
         self.dtype = torch.complex128
 
     def coef_shape(self, batch):
+        return (batch, self.L, 2 * self.L - 1)
+
+    def spectra_shape(self, batch):
         return (batch, self.L, 2 * self.L - 1)
 
     def _mask(self, lo, hi):

@@ -70,7 +70,9 @@ enum {
  *             rings), P = 2L.
  *   S2GB_DH   Driscoll-Healy (Sec. 4.2.1): R = 2L, theta_t = (2t+1) pi/(4L), P = 2L-1.
  * Every scheme has an exact forward quadrature for bandlimited signals: MW and MWSS through the
- * torus extension of Sec. 4.2.2, DH through its explicit weights.
+ * torus extension of Sec. 4.2.2, DH through its explicit weights.  On MWSS's two pole rings the
+ * d-functions are Kronecker deltas (Sec. 3.3); those rings are computed directly and the recursion
+ * runs over the L-1 interior rings.
  */
 enum { S2GB_MW = 0, S2GB_MWSS = 1, S2GB_DH = 2 };
 
@@ -89,8 +91,8 @@ enum {
  * recursion coefficient tables (Sec. 3.3 readings, O(L^2) per spin), the per-ring and per-order
  * log-space seed data (Eq. "initial_values") and the FFT weights; it creates cuFFT plans.
  * Returns S2GB_EINVAL for L < 1 or L > 8192, |spin| >= L (sphere), N < 0 or N > L, max_batch < 1,
- * an unknown sampling or precision; S2GB_EUNSUPPORTED for S2GB_FP32 with L > 2048 or more than
- * 2048 rings (MWSS at L = 2048, DH above L = 1024);
+ * an unknown sampling or precision; S2GB_EUNSUPPORTED for DH with L > 4096, and for S2GB_FP32
+ * with L > 2048 or DH with L > 1024;
  * S2GB_ENOMEM / S2GB_ECUDA / S2GB_ECUFFT on device failures.  On failure *out is set to NULL.  The
  * calling thread's current device is restored on return.
  */
@@ -174,8 +176,8 @@ int s2gb_adjoint_inverse(s2gb_plan plan, const void* f_bar, void* flm_bar, int b
  *     flm[b][l][m+L-1] = (-1)^s sqrt((2l+1)/(4 pi)) sum_t d^l_{m,-s}(theta_t) g[b][m+L-1][t],
  *   g of shape [batch][T][R] (order-major).
  * Same pointer, batch and stream rules as the transforms; no workspace is needed.  For N >= 1
- * plans these return S2GB_EUNSUPPORTED, and so does s2gb_forward_theta for more than 2048 rings
- * (its ring chunks need the transforms' workspace).
+ * plans these return S2GB_EUNSUPPORTED, and so does s2gb_forward_theta when the recursion runs over
+ * more than 2048 rings (its ring chunks need the transforms' workspace).
  */
 int s2gb_inverse_theta(s2gb_plan plan, const void* flm, void* ftilde, int batch, void* stream);
 int s2gb_forward_theta(s2gb_plan plan, const void* g, void* flm, int batch, void* stream);

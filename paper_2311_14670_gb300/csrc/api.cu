@@ -139,7 +139,8 @@ InvArgs inv_args(const Plan& p, const void* flm, void* out, int batch, const dou
   InvArgs a;
   a.flm = flm; a.out = out; a.s_sig = s_sig; a.s_t = s_t; a.s_m = s_m; a.m_mod = m_mod;
   a.mmod = p.P;
-  a.nsig = batch; a.nN = p.nN; a.L = p.L; a.nring = p.R; a.coef = p.coef; a.ring = p.ring; a.seed = p.seed;
+  a.nsig = batch; a.nN = p.nN; a.L = p.L; a.ring0 = p.ring0; a.nring = p.ring0 + p.nint;
+  a.coef = p.coef; a.ring = p.ring; a.seed = p.seed;
   a.scale = scale; a.coef32 = p.coef32; a.v32 = p.v32;
   a.dtab = p.dtab; a.tab_off = p.tab_off; a.live0 = p.live0;
   a.rank0 = 0; a.nrank = p.MR;
@@ -165,7 +166,7 @@ FwdArgs fwd_args(const Plan& p, const void* g, void* flm, int batch, const doubl
   a.mmod = p.P;
   a.nsig = batch; a.nN = p.nN; a.L = p.L; a.coef = p.coef; a.ring = p.ring; a.seed = p.seed;
   a.scale = scale; a.nu = p.nu; a.coef32 = p.coef32; a.v32 = p.v32;
-  a.row0 = 0; a.nrows = p.R; a.part = nullptr; a.part_off = 0;
+  a.row0 = p.ring0; a.nrows = p.nint; a.part = nullptr; a.part_off = 0;
   a.dtab = p.dtab; a.tab_off = p.tab_off; a.live0 = p.live0;
   a.rank0 = 0; a.nrank = p.MR;
   a.mpos = p.real ? 1 : 0; a.flm_ld = p.MR; a.flm_c0 = p.real ? 0 : p.L - 1;
@@ -429,11 +430,12 @@ int plan_create_impl(s2gb_plan* out, int L, int spin, int N, int sampling, int p
   if (sampling != S2GB_MW && sampling != S2GB_MWSS && sampling != S2GB_DH) return S2GB_EINVAL;
   if (precision != S2GB_FP64 && precision != S2GB_FP32) return S2GB_EINVAL;
   if (N == 0 && (spin <= -L || spin >= L)) return S2GB_EINVAL;
-  const int rings = sampling == S2GB_MWSS ? L + 1 : (sampling == S2GB_DH ? 2 * L : L);
+  // rings of the recursion kernels (MWSS: the interior; its two pole rings are handled exactly)
+  const int rings = sampling == S2GB_MWSS ? L - 1 : (sampling == S2GB_DH ? 2 * L : L);
   // float32 forward kernels hold every ring in one CTA; the ring-chunked float64 forward keeps its
-  // polar caps (under 0.05 of the rings each) within one 512-ring launch, i.e. at most 8193 rings
+  // polar caps (under 0.05 of the rings each) within one 512-ring launch, i.e. at most 8192 rings
   if (precision == S2GB_FP32 && (L > 2048 || rings > s2gb::kFwdChunk)) return S2GB_EUNSUPPORTED;
-  if (rings > 8193) return S2GB_EUNSUPPORTED;
+  if (rings > 8192) return S2GB_EUNSUPPORTED;
   if (real && sampling == S2GB_MWSS) return S2GB_EUNSUPPORTED;
   if (precompute && (precision != S2GB_FP64 || L > s2gb::kFwdChunk || sampling != S2GB_MW))
     return S2GB_EUNSUPPORTED;

@@ -284,11 +284,14 @@ int make_plan(Plan* p) {
     ring[t] = r;
   }
 
-  p->cap_n = 0;
-  while (p->cap_n < R && ring[p->cap_n].diff) ++p->cap_n;
-  p->cap_s = R;
+  p->ring0 = p->sampling == S2GB_MWSS ? 1 : 0;
+  p->nint = p->sampling == S2GB_MWSS ? L - 1 : R;
+  const int rend = p->ring0 + p->nint;
+  p->cap_n = p->ring0;
+  while (p->cap_n < rend && ring[p->cap_n].diff) ++p->cap_n;
+  p->cap_s = rend;
   while (p->cap_s > p->cap_n && ring[p->cap_s - 1].diff) --p->cap_s;
-  p->fwd_parts = (R <= kFwdChunk) ? 1 : 2 + (p->cap_s - p->cap_n + kFwdChunk - 1) / kFwdChunk;
+  p->fwd_parts = (p->nint <= kFwdChunk) ? 1 : 2 + (p->cap_s - p->cap_n + kFwdChunk - 1) / kFwdChunk;
 
   // ---- starting values d^{l0}_{m,n} (Eq. "initial_values" and Sec. 3.3 symmetries) ----
   std::vector<long double> lf2 = log2_factorials(2 * L + 2);

@@ -60,9 +60,12 @@ struct Plan {
                     // (MWSS), 0 (DH: explicit ring weights, no operator)
   int nN = 1;       // number of n values (1 for the sphere, 2N-1 for Wigner)
   int Nfft = 0;     // length of the fine theta grid of the forward quadrature (>= 4L-3)
-  int cap_n = 0;    // rings [0, cap_n) and [cap_s, R) use the difference form of the recursion
+  int ring0 = 0;    // the recursion kernels run over the rings [ring0, ring0 + nint): all of them
+  int nint = 0;     // on MW and DH; on MWSS the interior (the two pole rings, where d is a
+                    // Kronecker delta, are handled by the pole kernels)
+  int cap_n = 0;    // rings [ring0, cap_n) and [cap_s, ring0 + nint) use the difference form
   int cap_s = 0;
-  int fwd_parts = 1;  // forward theta stage in one launch (R <= kFwdChunk) or in ring chunks
+  int fwd_parts = 1;  // forward theta stage in one launch (nint <= kFwdChunk) or in ring chunks
   bool wigner = false;
   bool real = false;  // real signals (spin 0): orders m >= 0 only, f real, flm [L][L]
   int MR = 0;         // order rows of the theta-direction buffers: T (complex) or L (real)
@@ -114,7 +117,8 @@ struct InvArgs {
   int nsig;             // number of signals per n (batch)
   int nN;
   int L;
-  int nring;            // rings t < nring (R)
+  int ring0;            // the recursion kernel's rings: [ring0, nring)
+  int nring;
   const double* coef;
   const RingData* ring;
   const SeedData* seed;
@@ -174,6 +178,11 @@ inline void mrange_ranks(int lo, int hi, int& rank0, int& nrank) {
 cudaError_t launched();
 
 cudaError_t launch_theta_inverse(const Plan& p, const InvArgs& a, cudaStream_t st);
+// MWSS pole rings theta = 0 and pi (Sec. 3.3: d^l_{mn}(0) = delta_{mn}, d^l_{mn}(pi) =
+// (-1)^{l-n} delta_{m,-n}): the inverse-shaped stage writes both rings for the launch's orders,
+// the forward-shaped stage adds their terms to flm (after the interior rings' kernel)
+cudaError_t launch_pole_inverse(const Plan& p, const InvArgs& a, cudaStream_t st);
+cudaError_t launch_pole_forward(const Plan& p, const FwdArgs& a, cudaStream_t st);
 // precompute mode (theta_precompute.cu): table construction at plan creation, and the theta stages
 // reading it
 constexpr size_t kNoTable = ~(size_t)0;

@@ -60,7 +60,7 @@ __device__ __forceinline__ void inverse_body(const InvArgs& a, int m, int ni, in
   double2 acc[KT][NBX];
 #pragma unroll
   for (int i = 0; i < KT; ++i) {
-    const int t = tile * KT * nt + i * nt + tid;
+    const int t = a.ring0 + tile * KT * nt + i * nt + tid;
     tt[i] = t;
     if (t < a.nring) {
       const RingData rd = a.ring[t];
@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(128) theta_inverse_kernel(InvArgs a, int ntile
   if (PAIR && n == 0 && m < 0) return;        // produced by the CTA of -m
   const int l0 = a.seed[(size_t)ni * (2 * L - 1) + m + L - 1].l0;   // max(|m|, |n|)
   // Does this tile contain a ring that needs the difference form?
-  const int t_lo = tile * KT * blockDim.x, t_hi = min(a.nring, t_lo + KT * (int)blockDim.x) - 1;
+  const int t_lo = a.ring0 + tile * KT * blockDim.x, t_hi = min(a.nring, t_lo + KT * (int)blockDim.x) - 1;
   const bool diff = a.ring[t_lo].diff || a.ring[t_hi].diff;
   if (diff) inverse_body<KT, NB, true, PAIR>(a, m, ni, n, tile, l0, hs, cs);
   else inverse_body<KT, NB, false, PAIR>(a, m, ni, n, tile, l0, hs, cs);
@@ -352,7 +352,8 @@ __global__ void __launch_bounds__(128) theta_forward_kernel(FwdArgs a) {
 template <int KT, int NB, bool PAIR>
 cudaError_t launch_inv(const Plan& p, const InvArgs& a, cudaStream_t st) {
   const int nt = 128;
-  const int ntiles = (a.nring + KT * nt - 1) / (KT * nt);
+  const int ntiles = (a.nring - a.ring0 + KT * nt - 1) / (KT * nt);
+  if (ntiles == 0) return cudaSuccess;          // no rings for the recursion (MWSS, L = 1)
   dim3 grid(a.nrank * ntiles, PAIR ? (a.nN + 1) / 2 : a.nN, (a.nsig + NB - 1) / NB);
   theta_inverse_kernel<KT, NB, PAIR><<<grid, nt, 0, st>>>(a, ntiles);
   return launched();
@@ -360,8 +361,9 @@ cudaError_t launch_inv(const Plan& p, const InvArgs& a, cudaStream_t st) {
 
 template <int NB, bool PAIR>
 cudaError_t launch_inv_nb(const Plan& p, const InvArgs& a, cudaStream_t st) {
-  if (a.nring <= 128) return launch_inv<1, NB, PAIR>(p, a, st);
-  if (a.nring <= 512) return launch_inv<2, NB, PAIR>(p, a, st);
+  const int rings = a.nring - a.ring0;
+  if (rings <= 128) return launch_inv<1, NB, PAIR>(p, a, st);
+  if (rings <= 512) return launch_inv<2, NB, PAIR>(p, a, st);
   return launch_inv<4, NB, PAIR>(p, a, st);
 }
 
@@ -380,13 +382,13 @@ cudaError_t launch_fwd(const Plan& p, const FwdArgs& a, int nt, cudaStream_t st)
 
 template <int NB, bool PAIR>
 cudaError_t launch_fwd_nb(const Plan& p, const FwdArgs& a0, cudaStream_t st) {
-  const int R = p.R;       // rings of the sampling
+  const int R = p.nint;    // rings of the recursion kernels: [ring0, ring0 + nint)
   FwdArgs a = a0;
-  a.row0 = 0;
+  a.row0 = p.ring0;
   a.nrows = R;
   a.part = nullptr;
   a.part_off = 0;
-  if (R <= 128) return launch_fwd<1, NB, 1, PAIR>(p, a, ((R + 31) / 32) * 32, st);
+  if (R <= 128) return launch_fwd<1, NB, 1, PAIR>(p, a, R > 32 ? ((R + 31) / 32) * 32 : 32, st);
   if (R <= 256) return launch_fwd<2, NB, 1, PAIR>(p, a, 128, st);
   if (R <= 512) return launch_fwd<4, NB, 0, PAIR>(p, a, 128, st);
   // Unpaired: 16 rings per thread (64 threads) halve the cross-thread reduction; paired CTAs carry
@@ -408,9 +410,9 @@ cudaError_t launch_fwd_nb(const Plan& p, const FwdArgs& a0, cudaStream_t st) {
   // threads per CTA: KT * nt >= rows and nt <= rows (the last slot holds the last nt rings)
   auto nt_for = [](int rows, int kt) { return min(128, ((rows + kt - 1) / kt + 31) / 32 * 32); };
   a.part = a0.part;
-  a.row0 = 0; a.nrows = p.cap_n; a.part_off = part_elems * q++;
+  a.row0 = p.ring0; a.nrows = p.cap_n - p.ring0; a.part_off = part_elems * q++;
   if ((e = launch_fwd<4, NB, 1, PAIR>(p, a, nt_for(a.nrows, 4), st)) != cudaSuccess) return e;
-  a.row0 = p.cap_s; a.nrows = R - p.cap_s; a.part_off = part_elems * q++;
+  a.row0 = p.cap_s; a.nrows = p.ring0 + R - p.cap_s; a.part_off = part_elems * q++;
   if ((e = launch_fwd<4, NB, 1, PAIR>(p, a, nt_for(a.nrows, 4), st)) != cudaSuccess) return e;
   const int interior = p.cap_s - p.cap_n;
   const int nchunk = (interior + kFwdChunk - 1) / kFwdChunk;
@@ -432,8 +434,9 @@ bool paired(const Plan& p) { return paired_plan(p); }
 
 }  // namespace
 
-cudaError_t launch_theta_inverse(const Plan& p, const InvArgs& a, cudaStream_t st) {
-  if (a.nrank <= 0) return cudaSuccess;             // no orders in range: nothing to launch
+namespace {
+
+cudaError_t launch_theta_inverse_rings(const Plan& p, const InvArgs& a, cudaStream_t st) {
   if (a.dtab) return launch_theta_inverse_pre(p, a, st);
   if (p.precision == S2GB_FP32) return launch_theta_inverse_f32(p, a, st);
   if (paired(p)) {
@@ -445,17 +448,33 @@ cudaError_t launch_theta_inverse(const Plan& p, const InvArgs& a, cudaStream_t s
   return launch_inv_nb<1, false>(p, a, st);
 }
 
-cudaError_t launch_theta_forward(const Plan& p, const FwdArgs& a, cudaStream_t st) {
-  if (a.nrank <= 0) return cudaSuccess;
+cudaError_t launch_theta_forward_rings(const Plan& p, const FwdArgs& a, cudaStream_t st) {
   if (a.dtab) return launch_theta_forward_pre(p, a, st);
   if (p.precision == S2GB_FP32) return launch_theta_forward_f32(p, a, st);
   if (paired(p)) {
-    if (a.nsig >= 2 && p.R <= 1024) return launch_fwd_nb<2, true>(p, a, st);
+    if (a.nsig >= 2 && p.nint <= 1024) return launch_fwd_nb<2, true>(p, a, st);
     return launch_fwd_nb<1, true>(p, a, st);
   }
-  if (a.nsig >= 4 && p.R <= 1024) return launch_fwd_nb<4, false>(p, a, st);
+  if (a.nsig >= 4 && p.nint <= 1024) return launch_fwd_nb<4, false>(p, a, st);
   if (a.nsig >= 2) return launch_fwd_nb<2, false>(p, a, st);
   return launch_fwd_nb<1, false>(p, a, st);
+}
+
+}  // namespace
+
+// The recursion kernels over the rings [ring0, ring0 + nint), then (MWSS) the two pole rings.
+cudaError_t launch_theta_inverse(const Plan& p, const InvArgs& a, cudaStream_t st) {
+  if (a.nrank <= 0) return cudaSuccess;             // no orders in range: nothing to launch
+  const cudaError_t e = launch_theta_inverse_rings(p, a, st);
+  if (e != cudaSuccess || p.sampling != S2GB_MWSS) return e;
+  return launch_pole_inverse(p, a, st);
+}
+
+cudaError_t launch_theta_forward(const Plan& p, const FwdArgs& a, cudaStream_t st) {
+  if (a.nrank <= 0) return cudaSuccess;
+  const cudaError_t e = launch_theta_forward_rings(p, a, st);
+  if (e != cudaSuccess || p.sampling != S2GB_MWSS) return e;
+  return launch_pole_forward(p, a, st);
 }
 
 }  // namespace s2gb

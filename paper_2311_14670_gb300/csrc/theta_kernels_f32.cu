@@ -98,7 +98,7 @@ __device__ __forceinline__ void inverse_body_f32(const InvArgs& a, int m, int ni
   float2 blk[KT][NB], hi[KT][NB], lo[KT][NB];
 #pragma unroll
   for (int i = 0; i < KT; ++i) {
-    const int t = tile * KT * nt + i * nt + tid;
+    const int t = a.ring0 + tile * KT * nt + i * nt + tid;
     tt[i] = t;
     if (t < a.nring) {
       const RingData rd = a.ring[t];
@@ -215,7 +215,7 @@ __global__ void __launch_bounds__(128) theta_inverse_kernel_f32(InvArgs a, int n
   const int m = a.mpos ? rank : m_of_rank(rank);
   const int ni = blockIdx.y;
   const int l0 = a.seed[(size_t)ni * (2 * L - 1) + m + L - 1].l0;
-  const int t_lo = tile * KT * blockDim.x, t_hi = min(a.nring, t_lo + KT * (int)blockDim.x) - 1;
+  const int t_lo = a.ring0 + tile * KT * blockDim.x, t_hi = min(a.nring, t_lo + KT * (int)blockDim.x) - 1;
   const bool diff = a.ring[t_lo].diff || a.ring[t_hi].diff;
   if (diff) inverse_body_f32<KT, NB, true>(a, m, ni, tile, l0, hs, cs);
   else inverse_body_f32<KT, NB, false>(a, m, ni, tile, l0, hs, cs);
@@ -274,11 +274,11 @@ __global__ void __launch_bounds__(128) theta_forward_kernel_f32(FwdArgs a) {
   if (l0 >= L) return;
 
   const long long col = a.m_mod ? (m >= 0 ? m : m + a.mmod) : mi;
-  const int R = a.nrows;                 // rings t < R (one launch covers every ring)
+  const int R = a.nrows, r0 = a.row0;    // rings [r0, r0 + R) (one launch covers every ring)
   for (int q = tid; q < NB * rows; q += nt) {
     const int b = q / rows, pos = q % rows, sig = sig0 + b;
     bool act;
-    const int t = ring_of<KT>(pos / nt, pos % nt, nt, R, act);
+    const int t = r0 + ring_of<KT>(pos / nt, pos % nt, nt, R, act);
     float2 g = make_float2(0.f, 0.f);
     if (act && sig < a.nsig) {
       g = reinterpret_cast<const float2*>(a.g)[(size_t)(sig * a.nN + ni) * a.s_sig + t * a.s_t + col * a.s_m];
@@ -288,7 +288,7 @@ __global__ void __launch_bounds__(128) theta_forward_kernel_f32(FwdArgs a) {
   }
   for (int pos = tid; pos < rows; pos += nt) {
     bool act;
-    const int t = ring_of<KT>(pos / nt, pos % nt, nt, R, act);
+    const int t = r0 + ring_of<KT>(pos / nt, pos % nt, nt, R, act);
     vs[pos] = act ? a.v32[t] : 0.0f;
   }
   __syncthreads();
@@ -300,7 +300,7 @@ __global__ void __launch_bounds__(128) theta_forward_kernel_f32(FwdArgs a) {
 #pragma unroll
   for (int i = 0; i < KT; ++i) {
     bool act;
-    const int t = ring_of<KT>(i, tid, nt, R, act);
+    const int t = r0 + ring_of<KT>(i, tid, nt, R, act);
     if (act) {
       const RingData rd = a.ring[t];
       seed_value_f32(sd, rd, x[i], E[i]);
@@ -384,7 +384,8 @@ __global__ void __launch_bounds__(128) theta_forward_kernel_f32(FwdArgs a) {
 template <int KT, int NB>
 cudaError_t launch_inv32(const Plan& p, const InvArgs& a, cudaStream_t st) {
   const int nt = 128;
-  const int ntiles = (a.nring + KT * nt - 1) / (KT * nt);
+  const int ntiles = (a.nring - a.ring0 + KT * nt - 1) / (KT * nt);
+  if (ntiles == 0) return cudaSuccess;          // no rings for the recursion (MWSS, L = 1)
   dim3 grid(a.nrank * ntiles, a.nN, (a.nsig + NB - 1) / NB);
   theta_inverse_kernel_f32<KT, NB><<<grid, nt, 0, st>>>(a, ntiles);
   return launched();
@@ -392,8 +393,8 @@ cudaError_t launch_inv32(const Plan& p, const InvArgs& a, cudaStream_t st) {
 
 template <int NB>
 cudaError_t launch_inv32_nb(const Plan& p, const InvArgs& a, cudaStream_t st) {
-  if (a.nring <= 128) return launch_inv32<1, NB>(p, a, st);
-  if (a.nring <= 512) return launch_inv32<2, NB>(p, a, st);
+  if (a.nring - a.ring0 <= 128) return launch_inv32<1, NB>(p, a, st);
+  if (a.nring - a.ring0 <= 512) return launch_inv32<2, NB>(p, a, st);
   return launch_inv32<4, NB>(p, a, st);
 }
 
@@ -411,11 +412,11 @@ cudaError_t launch_fwd32(const Plan& p, const FwdArgs& a, int nt, cudaStream_t s
 
 template <int NB>
 cudaError_t launch_fwd32_nb(const Plan& p, const FwdArgs& a0, cudaStream_t st) {
-  const int R = p.R;       // rings of the sampling (float32 plans have R <= kFwdChunk)
+  const int R = p.nint;    // rings of the recursion (float32 plans have nint <= kFwdChunk)
   FwdArgs a = a0;
-  a.row0 = 0;
+  a.row0 = p.ring0;
   a.nrows = R;
-  if (R <= 128) return launch_fwd32<1, NB, 1>(p, a, ((R + 31) / 32) * 32, st);
+  if (R <= 128) return launch_fwd32<1, NB, 1>(p, a, R > 32 ? ((R + 31) / 32) * 32 : 32, st);
   if (R <= 256) return launch_fwd32<2, NB, 1>(p, a, 128, st);
   if (R <= 512) return launch_fwd32<4, NB, 0>(p, a, 128, st);
   if (R <= 1024) return launch_fwd32<8, NB, 0>(p, a, 128, st);
@@ -433,7 +434,7 @@ cudaError_t launch_theta_inverse_f32(const Plan& p, const InvArgs& a, cudaStream
 }
 
 cudaError_t launch_theta_forward_f32(const Plan& p, const FwdArgs& a, cudaStream_t st) {
-  if (a.nsig >= 8 && p.R <= 1024) return launch_fwd32_nb<8>(p, a, st);
+  if (a.nsig >= 8 && p.nint <= 1024) return launch_fwd32_nb<8>(p, a, st);
   if (a.nsig >= 4) return launch_fwd32_nb<4>(p, a, st);
   if (a.nsig >= 2) return launch_fwd32_nb<2>(p, a, st);
   return launch_fwd32_nb<1>(p, a, st);

@@ -4,7 +4,8 @@ Bar (float64): relative max error max|gpu - oracle| / max|oracle| <= 1e-12 on th
 inputs.  Small cases compare every output (inverse on bandlimited coefficients, forward on
 arbitrary samples, which exercises the whole linear map including the MWSS poles and the phi
 frequency no order owns), adjoints against the oracle's dense conjugate transpose; large cases
-compare sampled rings and round trips, including the ring-chunked forward (more than 2048 rings).
+compare sampled rings and round trips, including the ring-chunked forward (DH, more than 2048
+rings).  On MWSS the recursion runs over the interior rings and the pole rings are exact.
 """
 import numpy as np
 import pytest
@@ -141,8 +142,8 @@ def test_real_mwss_is_refused():
     ("mwss", 2048, 0, 1, [0, 1, 3, 1024, 2047, 2048]),
 ])
 def test_large_sampled_rings_and_round_trip(sampling, L, spin, batch, rings):
-    """Full-size cases: sampled rings of the inverse against the oracle, and the round trip
-    (MWSS at L = 2048 has 2049 rings: its forward runs the ring-chunked theta stage)."""
+    """Full-size cases: sampled rings of the inverse against the oracle (the MWSS poles among
+    them), and the round trip."""
     p = plan(L, sampling, spin, max_batch=batch)
     flm = synth.flm_gaussian(L, spin, batch, seed=1400 + L)
     x = to_gpu(flm)
@@ -202,3 +203,24 @@ def test_order_sharded_transforms_are_bitwise_unsharded(sampling):
     assert column_owner(L, ranges, "mod", P)[L % P] >= 0
     assert torch.equal(p.inverse_phi(ft), p.inverse(flm))
     assert torch.equal(fl, p.forward(f))
+
+
+@pytest.mark.parametrize("L,spin,batch", [(1, 0, 1), (2, 1, 2), (5, -2, 3), (40, 0, 2), (97, 3, 1)])
+def test_mwss_theta_stages_include_the_poles(L, spin, batch):
+    """The theta stages alone on MWSS: the recursion covers the interior rings and the pole rings
+    theta = 0, pi (Kronecker-delta d-functions) are added exactly; both compared with the oracle's
+    d-functions on all L+1 rings."""
+    from oracle.sampling import mwss_thetas
+    from oracle.wigner import wigner_d_table
+    p = plan(L, "mwss", spin, max_batch=batch)
+    flm = synth.flm_gaussian(L, spin, batch, seed=L + 40)
+    got = to_np(p.inverse_theta(to_gpu(flm)))                             # [b][t][m mod 2L]
+    ref = OT._theta_inverse(flm, L, -spin, OT.ell_factor(L, spin), mwss_thetas(L))
+    cols = [m % (2 * L) for m in range(-(L - 1), L)]
+    assert rel_max(got[..., cols], ref) <= TOL64
+    assert np.all(got[..., L] == 0)                                       # the phi frequency L
+    g = synth.signal_gaussian((batch, 2 * L - 1, L + 1), seed=L + 41)
+    D = wigner_d_table(np.arange(L), -spin, mwss_thetas(L))               # [l][m][t]
+    ref = np.einsum("bmt,lmt->blm", g, D) * OT.ell_factor(L, spin)[:, None]
+    ref = np.where(OT.coeff_mask(L, -spin), ref, 0)
+    assert rel_max(to_np(p.forward_theta(to_gpu(g))), ref) <= TOL64

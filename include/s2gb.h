@@ -129,9 +129,23 @@ int s2gb_plan_create_real(s2gb_plan* out, int L, int sampling, int precision, in
  * (L = 1024 spin 0: 4.3 GB; spin 2: 8.6 GB; L = 2048 spin 0: 34 GB; real plans as spin 0);
  * s2gb_plan_device_bytes includes it.  FP64 MW plans with L <= 2048 only (else S2GB_EUNSUPPORTED);
  * S2GB_ENOMEM when the table does not fit.
+ *
+ * S2GB_PLAN_MRECURSION: the theta stages generate the d-functions with the paper's own recursion
+ * over the order m (Sec. 3.3, Eq. wigner-d-recursion: downward from m = l, started from Eq.
+ * initial_values, run independently for every (l, theta)) instead of the default recursion over
+ * the degree l.  Same results to rounding; every transform and adjoint of sphere and Wigner plans
+ * (FP64 only; not with S2GB_PLAN_REAL or S2GB_PLAN_PRECOMPUTE: S2GB_EUNSUPPORTED).  Each (l, theta)
+ * runs two chains -- at theta for m >= rint(n cos theta) and at pi - theta for the rest, through
+ * d^l_{m,n}(theta) = (-1)^{l+n} d^l_{-m,n}(pi - theta) -- so that no chain crosses its lower
+ * turning point; the ring theta = pi (and theta = 0), where the recursion coefficient is
+ * undefined, takes the closed forms of Sec. 3.3.  Because m is both the recursion index and the
+ * output index of the contraction, the kernels sum across threads and write per-block partial
+ * sums into the workspace (s2gb_workspace_bytes includes them); the theta-only entry points and
+ * s2gb_inverse_noalloc return S2GB_EUNSUPPORTED for these plans.
  */
 #define S2GB_PLAN_REAL 1u
 #define S2GB_PLAN_PRECOMPUTE 2u
+#define S2GB_PLAN_MRECURSION 4u
 int s2gb_plan_create_flags(s2gb_plan* out, int L, int spin, int N, int sampling, int precision,
                            int max_batch, int device, unsigned flags);
 

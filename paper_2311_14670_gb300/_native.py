@@ -28,6 +28,7 @@ S2GB_FP64 = 0
 S2GB_FP32 = 1
 S2GB_PLAN_REAL = 1
 S2GB_PLAN_PRECOMPUTE = 2
+S2GB_PLAN_MRECURSION = 4
 
 _lib = None
 

@@ -145,6 +145,7 @@ InvArgs inv_args(const Plan& p, const void* flm, void* out, int batch, const dou
   a.dtab = p.dtab; a.tab_off = p.tab_off; a.live0 = p.live0;
   a.rank0 = 0; a.nrank = p.MR;
   a.mpos = p.real ? 1 : 0; a.flm_ld = p.MR; a.flm_c0 = p.real ? 0 : p.L - 1;
+  a.mpart = nullptr;
   return a;
 }
 
@@ -170,6 +171,7 @@ FwdArgs fwd_args(const Plan& p, const void* g, void* flm, int batch, const doubl
   a.dtab = p.dtab; a.tab_off = p.tab_off; a.live0 = p.live0;
   a.rank0 = 0; a.nrank = p.MR;
   a.mpos = p.real ? 1 : 0; a.flm_ld = p.MR; a.flm_c0 = p.real ? 0 : p.L - 1;
+  a.mpart = nullptr;
   return a;
 }
 
@@ -234,6 +236,7 @@ int do_forward(Plan& p, const void* f, void* flm, int batch, const Workspace& w,
     a = fwd_args(p, w.B, flm, batch, p.scale_fwd, (long long)p.MR * p.TS, 1, p.TS, 0, 1);
   }
   a.part = w.D;
+  a.mpart = w.D;
   order_ranks(p, mlo, mhi, a.rank0, a.nrank);
   return cuda_rc(launch_theta_forward(p, a, st));
 }
@@ -248,6 +251,7 @@ int do_inverse(Plan& p, const void* flm, void* f, int batch, const Workspace& w,
   FftRunner fr{p, st, w.fft, batch};
   const size_t plane = (size_t)p.R * p.P;
   InvArgs a = inv_args(p, flm, w.A, batch, p.scale_inv, (long long)plane, p.P, 1, 1);
+  a.mpart = w.D;
   S2GB_TRY(cuda_rc(launch_theta_inverse(p, a, st)));
   S2GB_TRY(cuda_rc(zero_nyquist(p, w.A, batch * p.nN, st)));
   if (!p.wigner) return fr.run(p.fft_phi, w.A, f, plane, CUFFT_INVERSE);
@@ -269,6 +273,7 @@ int do_adjoint_inverse(Plan& p, const void* fbar, void* flmbar, int batch, const
   S2GB_TRY(fr.run(p.fft_phi, sig_in, w.A, (size_t)p.nN * plane, CUFFT_FORWARD));
   FwdArgs a = fwd_args(p, w.A, flmbar, batch, p.scale_inv, (long long)plane, p.P, 1, 1, 0);
   a.part = w.D;
+  a.mpart = w.D;
   return cuda_rc(launch_theta_forward(p, a, st));
 }
 
@@ -279,10 +284,12 @@ int do_adjoint_forward(Plan& p, const void* flmbar, void* fbar, int batch, const
   const size_t plane = (size_t)p.R * p.P;
   if (p.sampling == S2GB_DH) {
     InvArgs a = inv_args(p, flmbar, w.A, batch, p.scale_fwd, (long long)plane, p.P, 1, 1);
+    a.mpart = w.D;
     S2GB_TRY(cuda_rc(launch_theta_inverse(p, a, st)));
     S2GB_TRY(cuda_rc(launch_ring_weight(p, w.A, S, p.P, st)));
   } else {
     InvArgs a = inv_args(p, flmbar, w.B, batch, p.scale_fwd, (long long)p.MR * p.TS, 1, p.TS, 0);
+    a.mpart = w.D;
     S2GB_TRY(cuda_rc(launch_theta_inverse(p, a, st)));
     S2GB_TRY(cuda_rc(launch_nu_extend(p, w.B, S * p.MR, st)));
     S2GB_TRY(theta_weight_operator(p, fr, w.A, w.B, S));
@@ -423,7 +430,7 @@ extern "C" {
 
 namespace {
 int plan_create_impl(s2gb_plan* out, int L, int spin, int N, int sampling, int precision, int max_batch,
-                     int device, bool real, bool precompute = false) {
+                     int device, bool real, bool precompute = false, bool mrec = false) {
   if (!out) return S2GB_EINVAL;
   *out = nullptr;
   if (L < 1 || L > 8192 || N < 0 || N > L || max_batch < 1) return S2GB_EINVAL;
@@ -439,6 +446,7 @@ int plan_create_impl(s2gb_plan* out, int L, int spin, int N, int sampling, int p
   if (real && sampling == S2GB_MWSS) return S2GB_EUNSUPPORTED;
   if (precompute && (precision != S2GB_FP64 || L > s2gb::kFwdChunk || sampling != S2GB_MW))
     return S2GB_EUNSUPPORTED;
+  if (mrec && (precision != S2GB_FP64 || real || precompute)) return S2GB_EUNSUPPORTED;
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return S2GB_EINVAL;
   s2gb_plan h = new (std::nothrow) s2gb_plan_s;
@@ -449,6 +457,7 @@ int plan_create_impl(s2gb_plan* out, int L, int spin, int N, int sampling, int p
   p.sampling = sampling;
   p.real = real;
   p.precompute = precompute;
+  p.mrec = mrec;
   int rc;
   {
     s2gb::DeviceGuard g(device);
@@ -477,11 +486,11 @@ int s2gb_plan_create_real(s2gb_plan* out, int L, int sampling, int precision, in
 int s2gb_plan_create_flags(s2gb_plan* out, int L, int spin, int N, int sampling, int precision,
                            int max_batch, int device, unsigned flags) {
   if (out) *out = nullptr;
-  if (flags & ~(unsigned)(S2GB_PLAN_REAL | S2GB_PLAN_PRECOMPUTE)) return S2GB_EINVAL;
+  if (flags & ~(unsigned)(S2GB_PLAN_REAL | S2GB_PLAN_PRECOMPUTE | S2GB_PLAN_MRECURSION)) return S2GB_EINVAL;
   const bool real = (flags & S2GB_PLAN_REAL) != 0;
   if (real && (spin != 0 || N != 0)) return S2GB_EINVAL;
   return plan_create_impl(out, L, spin, N, sampling, precision, max_batch, device, real,
-                          (flags & S2GB_PLAN_PRECOMPUTE) != 0);
+                          (flags & S2GB_PLAN_PRECOMPUTE) != 0, (flags & S2GB_PLAN_MRECURSION) != 0);
 }
 
 void s2gb_plan_destroy(s2gb_plan plan) {
@@ -519,7 +528,7 @@ int s2gb_inverse_theta_mrange(s2gb_plan plan, const void* flm, void* ftilde, int
                               int m_hi, void* stream) {
   if (!plan || !flm || !ftilde) return S2GB_EINVAL;
   s2gb::Plan& p = plan->p;
-  if (p.wigner) return S2GB_EUNSUPPORTED;
+  if (p.wigner || p.mrec) return S2GB_EUNSUPPORTED;   // order recursion: its partials need a workspace
   if (batch < 1 || batch > p.max_batch) return S2GB_EINVAL;
   if (m_lo < 0 || m_lo > m_hi || m_hi > p.L) return S2GB_EINVAL;
   const size_t es = p.precision == S2GB_FP64 ? 16 : 8;
@@ -552,7 +561,7 @@ int s2gb_inverse_phi(s2gb_plan plan, const void* ftilde, void* f, int batch, voi
 int s2gb_forward_theta(s2gb_plan plan, const void* gin, void* flm, int batch, void* stream) {
   if (!plan || !gin || !flm) return S2GB_EINVAL;
   s2gb::Plan& p = plan->p;
-  if (p.wigner || p.fwd_parts > 1) return S2GB_EUNSUPPORTED;   // L > 2048 needs a workspace
+  if (p.wigner || p.fwd_parts > 1 || p.mrec) return S2GB_EUNSUPPORTED;   // these need a workspace
   if (batch < 1 || batch > p.max_batch) return S2GB_EINVAL;
   const size_t es = p.precision == S2GB_FP64 ? 16 : 8;
   if (s2gb::overlaps(gin, (size_t)batch * p.MR * p.R * es, flm, (size_t)batch * p.L * p.MR * es))
@@ -618,7 +627,7 @@ int noalloc_scratch(int device, void** out) {
 extern "C" int s2gb_inverse_noalloc(s2gb_plan plan, const void* flm, void* f, int batch, void* stream) {
   if (!plan || !flm || !f) return S2GB_EINVAL;
   s2gb::Plan& p = plan->p;
-  if (p.real) return S2GB_EUNSUPPORTED;
+  if (p.real || p.mrec) return S2GB_EUNSUPPORTED;
   if (batch < 1 || batch > p.max_batch) return S2GB_EINVAL;
   const size_t es = p.precision == S2GB_FP64 ? 16 : 8;
   const size_t sig_bytes = (size_t)batch * p.nN * p.R * p.P * es;

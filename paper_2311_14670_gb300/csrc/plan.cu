@@ -164,6 +164,29 @@ __global__ void coefn_kernel(double* coef, const int* n_of, int nN, int L) {
   }
 }
 
+// Coefficients of the order recursion (Sec. 3.3, Eq. "wigner-d-recursion") for the step m -> m-1
+// at degree l: (A, B) = (a_{m-1}, a_{m-1}/a_m), a_m = 2/sqrt((l-m)(l+m+1)), for -l < m <= l
+// (B = 0 at m = l, where d_{l+1} = 0), in double-double and rounded once.  Layout [l][m + L - 1].
+__global__ void mrec_ab_kernel(double* ab, int L) {
+  const int T = 2 * L - 1;
+  const long long total = (long long)L * T;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const long long l = idx / T;
+    const long long m = idx % T - (L - 1);
+    double* out = ab + 2 * idx;
+    if (m > l || m <= -l) {
+      out[0] = 0.0; out[1] = 0.0;
+      continue;
+    }
+    const dd R1 = dd_sqrt(dd_from_ll((l - m + 1) * (l + m)));
+    const dd A = dd_div(dd_from_ll(2), R1);
+    const dd B = (m == l) ? dd{0.0, 0.0} : dd_div(dd_sqrt(dd_from_ll((l - m) * (l + m + 1))), R1);
+    out[0] = A.hi + A.lo;
+    out[1] = B.hi + B.lo;
+  }
+}
+
 __global__ void to_float_kernel(const double* __restrict__ in, float* __restrict__ out, size_t n) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
     out[i] = (float)in[i];
@@ -284,14 +307,19 @@ int make_plan(Plan* p) {
     ring[t] = r;
   }
 
-  p->ring0 = p->sampling == S2GB_MWSS ? 1 : 0;
-  p->nint = p->sampling == S2GB_MWSS ? L - 1 : R;
+  p->ring0 = 0;
+  p->nint = R;
+  if (p->sampling == S2GB_MWSS) {             // theta = 0 and pi are rings: exact pole kernels
+    p->ring0 = 1; p->nint = L - 1; p->pole_n = 0; p->pole_s = L;
+  } else if (p->sampling == S2GB_MW && p->mrec) {   // theta = pi (last ring) likewise
+    p->nint = L - 1; p->pole_s = L - 1;
+  }
   const int rend = p->ring0 + p->nint;
   p->cap_n = p->ring0;
   while (p->cap_n < rend && ring[p->cap_n].diff) ++p->cap_n;
   p->cap_s = rend;
   while (p->cap_s > p->cap_n && ring[p->cap_s - 1].diff) --p->cap_s;
-  p->fwd_parts = (p->nint <= kFwdChunk) ? 1 : 2 + (p->cap_s - p->cap_n + kFwdChunk - 1) / kFwdChunk;
+  p->fwd_parts = (p->nint <= kFwdChunk || p->mrec) ? 1 : 2 + (p->cap_s - p->cap_n + kFwdChunk - 1) / kFwdChunk;
 
   // ---- starting values d^{l0}_{m,n} (Eq. "initial_values" and Sec. 3.3 symmetries) ----
   std::vector<long double> lf2 = log2_factorials(2 * L + 2);
@@ -379,6 +407,22 @@ int make_plan(Plan* p) {
   if ((rc = upload(&p->nu, nu, &bytes))) return rc;
   if ((rc = upload(&p->wfine, wf, &bytes))) return rc;
   if ((rc = upload(&p->n_of, n_of, &bytes))) return rc;
+  if (p->mrec) {
+    std::vector<double> csc(R, 0.0);
+    for (int t = p->ring0; t < p->ring0 + p->nint; ++t) {
+      long double th;
+      if (p->sampling == S2GB_MWSS) th = (long double)t * kPiL / (long double)L;
+      else if (p->sampling == S2GB_DH) th = (long double)(2 * t + 1) * kPiL / (4.0L * L);
+      else th = (long double)(2 * t + 1) * kPiL / (long double)T;
+      csc[t] = (double)(1.0L / std::sin(th));
+    }
+    if ((rc = upload(&p->csc, csc, &bytes))) return rc;
+    const size_t ab_bytes = (size_t)L * T * 2 * sizeof(double);
+    if (cudaMalloc((void**)&p->mrec_ab, ab_bytes) != cudaSuccess) return S2GB_ENOMEM;
+    bytes += ab_bytes;
+    mrec_ab_kernel<<<1024, 256>>>(p->mrec_ab, L);
+    if (launched() != cudaSuccess) return S2GB_ECUDA;
+  }
   const int per_step = p->precision == S2GB_FP64 ? kCoefPerStepN : kCoefPerStep;
   const size_t coef_bytes = (size_t)nN * T * L * per_step * sizeof(double);
   if (cudaMalloc((void**)&p->coef, coef_bytes) != cudaSuccess) return S2GB_ENOMEM;
@@ -460,6 +504,8 @@ void free_plan(Plan* p) {
   cudaFree(p->nu);
   cudaFree(p->wfine);
   cudaFree(p->n_of);
+  cudaFree(p->mrec_ab);
+  cudaFree(p->csc);
   for (int q = 0; q < 2; ++q) {
     if (p->fft_made[q]) {
       cufftDestroy(p->fft_phi[q]);
@@ -479,7 +525,8 @@ static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 //   A: phi spectra [S][R][SW] and the fine theta grid [S][MR][Nfft] (forward), ring spectra (inverse)
 //   B: theta-torus rows [S][MR][max(T, TS)], or a signal-sized buffer [S][R][SW] (Wigner, DH)
 //   C: a second signal-sized buffer (Wigner: the gamma DFT)
-//   D: partial coefficients of the ring-chunked forward theta stage (R > kFwdChunk)
+//   D: partial coefficients of the ring-chunked forward theta stage (R > kFwdChunk), or the
+//      per-CTA partial sums of the order-recursion kernels
 // with S = batch * nN and SW = P (complex signals) or L (real signals: orders m >= 0).
 void workspace_regions(const Plan& p, int batch, size_t out[4]) {
   const size_t es = p.precision == S2GB_FP64 ? 16 : 8;
@@ -494,6 +541,7 @@ void workspace_regions(const Plan& p, int batch, size_t out[4]) {
   out[1] = S * wB * es;
   out[2] = p.wigner ? S * spectra * es : 0;
   out[3] = p.fwd_parts > 1 ? (size_t)p.fwd_parts * S * p.L * (size_t)p.MR * es : 0;
+  if (p.mrec) out[3] = mrec_part_bytes(p, batch);
 }
 
 size_t workspace_bytes(const Plan& p, int batch) {

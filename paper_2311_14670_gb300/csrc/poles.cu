@@ -1,13 +1,15 @@
-// The two pole rings of MWSS sampling (theta = 0 and theta = pi are rings of the grid).  There the
+// Pole rings: theta = 0 and pi on MWSS sampling, and theta = pi on MW sampling when the theta stage
+// runs the order recursion (whose lambda_m = (n - m cos b)/sin b is undefined there).  There the
 // Wigner d-functions are Kronecker deltas (Sec. 3.3):
 //     d^l_{mn}(0) = delta_{m,n},        d^l_{mn}(pi) = (-1)^{l-n} delta_{m,-n},
 // so each pole ring couples one order to the coefficients and the three-term recursion is not
-// needed there.  The recursion kernels run over the interior rings [1, L) only, and these kernels
-// supply the poles exactly:
+// needed there.  The recursion kernels run over the other rings only, and these kernels supply the
+// poles exactly:
 //   inverse-shaped:  ftilde_m(pole) = [m = m*] sum_{l >= |n|} scale_l flm_{l,m*} sgn_l,
 //   forward-shaped:  flm_{l,m*} += scale_l w_pole sgn_l g_{m*}(pole)      (after the interior sum),
 // with m* = n, sgn_l = 1 at theta = 0 and m* = -n, sgn_l = (-1)^{l-n} at theta = pi, and w_pole the
-// ring weight (1 for MWSS's self-reflected rings, or 1 in the unweighted adjoint).  Sums run in a
+// ring weight (1 for the self-reflected rings theta = 0, pi of MW and MWSS, or 1 in the unweighted
+// adjoint).  Sums run in a
 // fixed order (deterministic).  Data are complex128 or complex64 (accumulated in float64).
 #include <cuda_runtime.h>
 
@@ -26,16 +28,19 @@ struct Real<float2> { using type = float; };
 
 constexpr int kPoleThreads = 256;
 
-// Grid: x = signal index s = sig * nN + ni, y = pole (0: theta = 0 at ring 0; 1: theta = pi at
-// ring L).  Writes the pole ring of every order with |m| in [mlo, mhi).
+// Grid: x = signal index s = sig * nN + ni, y = pole (0: theta = 0 at ring pn; 1: theta = pi at
+// ring ps; a negative ring index means the plan has no such ring).  Writes the pole ring of every
+// order with |m| in [mlo, mhi).
 template <typename C>
 __global__ void __launch_bounds__(kPoleThreads) pole_inverse_kernel(InvArgs a, const int* __restrict__ n_of,
-                                                                    int mlo, int mhi) {
+                                                                    int mlo, int mhi, int pn, int ps) {
   using Rl = typename Real<C>::type;
   __shared__ double red[2][kPoleThreads / 32];
   __shared__ double2 val;
   const int L = a.L;
   const int s = blockIdx.x, pole = blockIdx.y;
+  const int t = pole ? ps : pn;
+  if (t < 0) return;
   const int ni = s % a.nN;
   const int n = n_of[ni];
   const int ms = pole ? -n : n;
@@ -66,7 +71,6 @@ __global__ void __launch_bounds__(kPoleThreads) pole_inverse_kernel(InvArgs a, c
     }
   }
   __syncthreads();
-  const int t = pole ? L : 0;
   C* out = reinterpret_cast<C*>(a.out) + (size_t)s * a.s_sig + (size_t)t * a.s_t;
   for (int q = threadIdx.x; q < 2 * L - 1; q += blockDim.x) {
     const int m = q - (L - 1);
@@ -82,7 +86,7 @@ __global__ void __launch_bounds__(kPoleThreads) pole_inverse_kernel(InvArgs a, c
 
 // One thread per (signal index s, degree l): adds the two pole terms, theta = 0 first.
 template <typename C>
-__global__ void pole_forward_kernel(FwdArgs a, const int* __restrict__ n_of, int mlo, int mhi) {
+__global__ void pole_forward_kernel(FwdArgs a, const int* __restrict__ n_of, int mlo, int mhi, int pn, int ps) {
   using Rl = typename Real<C>::type;
   const int L = a.L;
   const size_t total = (size_t)a.nsig * a.nN * L;
@@ -98,7 +102,8 @@ __global__ void pole_forward_kernel(FwdArgs a, const int* __restrict__ n_of, int
     if (l < an || an < mlo || an >= mhi) continue;
     const double sc = a.scale[(size_t)ni * L + l];
     for (int pole = 0; pole < 2; ++pole) {
-      const int t = pole ? L : 0;
+      const int t = pole ? ps : pn;
+      if (t < 0) continue;
       const int m = pole ? -n : n;
       const long long col = a.m_mod ? (m >= 0 ? m : m + a.mmod) : (long long)(m + L - 1);
       const C gv = g[s * a.s_sig + (size_t)t * a.s_t + col * a.s_m];
@@ -127,9 +132,9 @@ cudaError_t launch_pole_inverse(const Plan& p, const InvArgs& a, cudaStream_t st
   rank_orders(a.rank0, a.nrank, mlo, mhi);
   dim3 grid((unsigned)(a.nsig * a.nN), 2);
   if (p.precision == S2GB_FP64)
-    pole_inverse_kernel<double2><<<grid, kPoleThreads, 0, st>>>(a, p.n_of, mlo, mhi);
+    pole_inverse_kernel<double2><<<grid, kPoleThreads, 0, st>>>(a, p.n_of, mlo, mhi, p.pole_n, p.pole_s);
   else
-    pole_inverse_kernel<float2><<<grid, kPoleThreads, 0, st>>>(a, p.n_of, mlo, mhi);
+    pole_inverse_kernel<float2><<<grid, kPoleThreads, 0, st>>>(a, p.n_of, mlo, mhi, p.pole_n, p.pole_s);
   return launched();
 }
 
@@ -140,9 +145,9 @@ cudaError_t launch_pole_forward(const Plan& p, const FwdArgs& a, cudaStream_t st
   const size_t n = (size_t)a.nsig * a.nN * a.L;
   const unsigned blocks = (unsigned)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
   if (p.precision == S2GB_FP64)
-    pole_forward_kernel<double2><<<blocks, 256, 0, st>>>(a, p.n_of, mlo, mhi);
+    pole_forward_kernel<double2><<<blocks, 256, 0, st>>>(a, p.n_of, mlo, mhi, p.pole_n, p.pole_s);
   else
-    pole_forward_kernel<float2><<<blocks, 256, 0, st>>>(a, p.n_of, mlo, mhi);
+    pole_forward_kernel<float2><<<blocks, 256, 0, st>>>(a, p.n_of, mlo, mhi, p.pole_n, p.pole_s);
   return launched();
 }
 

@@ -62,7 +62,11 @@ struct Plan {
   int Nfft = 0;     // length of the fine theta grid of the forward quadrature (>= 4L-3)
   int ring0 = 0;    // the recursion kernels run over the rings [ring0, ring0 + nint): all of them
   int nint = 0;     // on MW and DH; on MWSS the interior (the two pole rings, where d is a
-                    // Kronecker delta, are handled by the pole kernels)
+                    // Kronecker delta, are handled by the pole kernels), likewise MW's ring theta = pi
+                    // with the order recursion (its lambda_m has 1/sin(theta))
+  int pole_n = -1;  // ring index of theta = 0 handled by the pole kernels, or -1
+  int pole_s = -1;  // ring index of theta = pi handled by the pole kernels, or -1
+  bool mrec = false;  // theta stages by the recursion over the order m (theta_mrec.cu)
   int cap_n = 0;    // rings [ring0, cap_n) and [cap_s, ring0 + nint) use the difference form
   int cap_s = 0;
   int fwd_parts = 1;  // forward theta stage in one launch (nint <= kFwdChunk) or in ring chunks
@@ -82,6 +86,8 @@ struct Plan {
   double* nu = nullptr;        // [R] ring weights of the forward quadrature: fold factors
                                // (MW 2, ..., 2, 1; MWSS 1, 2, ..., 2, 1) or DH weights * 2 pi/P
   int* n_of = nullptr;         // [nN] n for each n index
+  double* mrec_ab = nullptr;   // [L][T] (a_{m-1}, a_{m-1}/a_m) of the order recursion (mrec plans)
+  double* csc = nullptr;       // [R] 1/sin(theta) of the interior rings (mrec plans)
   size_t device_bytes = 0;
 
   // precompute mode (FP64, L <= kFwdChunk): d^l_{m,n}(theta_t) of every (n, m) theta kernels run,
@@ -133,6 +139,7 @@ struct InvArgs {
   int mpos;             // 1: rank r is order m = r (real-signal plans: m >= 0 only)
   int flm_ld;           // row length of flm (T; L for real-signal plans)
   int flm_c0;           // column of m = 0 in flm (L - 1; 0 for real-signal plans)
+  void* mpart;          // order-recursion plans: workspace for the per-CTA partial sums
 };
 
 struct FwdArgs {
@@ -164,7 +171,22 @@ struct FwdArgs {
   int mpos;             // flm layout and order mapping as in InvArgs
   int flm_ld;
   int flm_c0;
+  void* mpart;          // order-recursion plans: workspace for the per-CTA partial sums
 };
+
+// Arguments of the order-recursion kernels (theta_mrec.cu)
+struct MrecArgs {
+  const double2* ab;    // [L][T] (a_{m-1}, a_{m-1}/a_m)
+  const double* csc;    // [R] 1/sin(theta)
+  const int* n_of;
+  void* part;           // partial sums
+  int nint;             // rings of the recursion
+  int mlo, mhi;         // orders |m| in [mlo, mhi) are written
+  int mlow1;            // forward: lowest order of the CTA's first sweep
+};
+cudaError_t launch_theta_inverse_mrec(const Plan& p, const InvArgs& a, cudaStream_t st);
+cudaError_t launch_theta_forward_mrec(const Plan& p, const FwdArgs& a, cudaStream_t st);
+size_t mrec_part_bytes(const Plan& p, int batch);   // workspace region D of order-recursion plans
 
 // m-ranks of the orders with |m| in [lo, hi), 0 <= lo <= hi <= L (empty: count 0)
 inline void mrange_ranks(int lo, int hi, int& rank0, int& nrank) {

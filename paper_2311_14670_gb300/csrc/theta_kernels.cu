@@ -437,6 +437,7 @@ bool paired(const Plan& p) { return paired_plan(p); }
 namespace {
 
 cudaError_t launch_theta_inverse_rings(const Plan& p, const InvArgs& a, cudaStream_t st) {
+  if (p.mrec) return launch_theta_inverse_mrec(p, a, st);
   if (a.dtab) return launch_theta_inverse_pre(p, a, st);
   if (p.precision == S2GB_FP32) return launch_theta_inverse_f32(p, a, st);
   if (paired(p)) {
@@ -449,6 +450,7 @@ cudaError_t launch_theta_inverse_rings(const Plan& p, const InvArgs& a, cudaStre
 }
 
 cudaError_t launch_theta_forward_rings(const Plan& p, const FwdArgs& a, cudaStream_t st) {
+  if (p.mrec) return launch_theta_forward_mrec(p, a, st);
   if (a.dtab) return launch_theta_forward_pre(p, a, st);
   if (p.precision == S2GB_FP32) return launch_theta_forward_f32(p, a, st);
   if (paired(p)) {
@@ -462,18 +464,19 @@ cudaError_t launch_theta_forward_rings(const Plan& p, const FwdArgs& a, cudaStre
 
 }  // namespace
 
-// The recursion kernels over the rings [ring0, ring0 + nint), then (MWSS) the two pole rings.
+// The recursion kernels over the rings [ring0, ring0 + nint), then the pole rings the plan hands
+// to the exact pole kernels (MWSS; MW with the order recursion).
 cudaError_t launch_theta_inverse(const Plan& p, const InvArgs& a, cudaStream_t st) {
   if (a.nrank <= 0) return cudaSuccess;             // no orders in range: nothing to launch
   const cudaError_t e = launch_theta_inverse_rings(p, a, st);
-  if (e != cudaSuccess || p.sampling != S2GB_MWSS) return e;
+  if (e != cudaSuccess || (p.pole_n < 0 && p.pole_s < 0)) return e;
   return launch_pole_inverse(p, a, st);
 }
 
 cudaError_t launch_theta_forward(const Plan& p, const FwdArgs& a, cudaStream_t st) {
   if (a.nrank <= 0) return cudaSuccess;
   const cudaError_t e = launch_theta_forward_rings(p, a, st);
-  if (e != cudaSuccess || p.sampling != S2GB_MWSS) return e;
+  if (e != cudaSuccess || (p.pole_n < 0 && p.pole_s < 0)) return e;
   return launch_pole_forward(p, a, st);
 }
 

@@ -34,7 +34,7 @@ class Plan:
 
     def __init__(self, L: int, spin: int = 0, N: int = 0, precision: str = "fp64", max_batch: int = 1,
                  device: int | torch.device | None = None, sampling: str = "mw", real: bool = False,
-                 precompute: bool = False):
+                 precompute: bool = False, mrecursion: bool = False):
         if sampling not in _SAMPLINGS:
             raise ValueError(f"sampling must be one of {list(_SAMPLINGS)}")
         if precision not in _PRECISIONS:
@@ -48,11 +48,13 @@ class Plan:
         self.dtype = _PRECISIONS[precision][1]          # coefficients (and complex signals)
         self.real = bool(real)
         self.precompute = bool(precompute)
+        self.mrecursion = bool(mrecursion)      # theta stages by the paper's recursion over m
         self.sampling = sampling
         self.R, self.P = sampling_shape(self.L, sampling)
         if self.real and (self.spin != 0 or self.N != 0):
             raise ValueError("real-signal plans are spin-0 sphere transforms (spin = 0, N = 0)")
-        flags = (nat.S2GB_PLAN_REAL if self.real else 0) | (nat.S2GB_PLAN_PRECOMPUTE if self.precompute else 0)
+        flags = ((nat.S2GB_PLAN_REAL if self.real else 0) | (nat.S2GB_PLAN_PRECOMPUTE if self.precompute else 0)
+                 | (nat.S2GB_PLAN_MRECURSION if self.mrecursion else 0))
         self._h = nat.plan_create_flags(self.L, self.spin, self.N, _SAMPLINGS[sampling], _PRECISIONS[precision][0],
                                         self.max_batch, int(device), flags)
         self.signal_dtype = _REAL_OF[self.dtype] if self.real else self.dtype

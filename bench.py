@@ -61,11 +61,19 @@ WORKLOADS = {
     "l1024s0b1mwss": (1024, 0, 0, 1, 0.0, "spin-0 SHT round trip, L=1024, MWSS 1025x2048, batch 1, FP64"),
     "l2048s0b1mwss": (2048, 0, 0, 1, 0.0, "spin-0 SHT round trip, L=2048, MWSS 2049x4096, batch 1, FP64"),
     "l1024s2b4dh": (1024, 2, 0, 4, 1.0, "spin-2 SHT round trip, L=1024, DH 2048x2047, batch 4, FP64"),
+    "l1024s2b4mrec": (1024, 2, 0, 4, 1.0, "spin-2 SHT round trip, L=1024, MW, batch 4, FP64, theta stages by "
+                      "the paper's recursion over the order m"),
+    "l2048s0b1mrec": (2048, 0, 0, 1, 0.0, "spin-0 SHT round trip, L=2048, MW, batch 1, FP64, theta stages by "
+                      "the paper's recursion over the order m"),
+    "l2048s2b1mrec": (2048, 2, 0, 1, 0.0, "spin-2 SHT round trip, L=2048, MW, batch 1, FP64, theta stages by "
+                      "the paper's recursion over the order m"),
+    "l2048s2b1": (2048, 2, 0, 1, 0.0, "spin-2 SHT round trip, L=2048, MW 2048x4095, batch 1, FP64"),
 }
 PRECISION = {"l2048s0b16f32grad": "fp32"}
 REAL = {"l2048realb1", "l1024realb4", "l2048realb1pre"}
 PRECOMPUTE = {"l1024s2b4pre", "l1024s0b1pre", "l2048s0b1pre", "l2048realb1pre"}
 GRAD = {"l2048s0b16f32grad"}
+MREC = {"l1024s2b4mrec", "l2048s0b1mrec", "l2048s2b1mrec"}
 SAMPLING = {"l1024s0b1dh": "dh", "l2048s0b1dh": "dh", "l1024s0b1mwss": "mwss", "l2048s0b1mwss": "mwss",
             "l1024s2b4dh": "dh"}
 METRIC = "transforms/sec"
@@ -189,7 +197,7 @@ def run_ours(args, world, rank, local):
     tp0 = time.perf_counter()
     sampling = SAMPLING.get(args.workload, "mw")
     plan = Plan(L, spin=spin, N=N, max_batch=B, device=local, precision=precision, real=real,
-                precompute=args.workload in PRECOMPUTE, sampling=sampling)
+                precompute=args.workload in PRECOMPUTE, sampling=sampling, mrecursion=args.workload in MREC)
     torch.cuda.synchronize(dev)
     plan_ms = (time.perf_counter() - tp0) * 1e3
     cdt = plan.dtype
@@ -284,6 +292,12 @@ def run_ours(args, world, rank, local):
         stages = [("theta_inverse", lambda: plan.inverse_theta(xd_, out=ft))]
         if R <= 2048:    # above, the forward theta stage runs in ring chunks inside forward() only
             stages.append(("theta_forward", lambda: plan.forward_theta(g, out=fl)))
+        if plan.mrecursion:
+            # the order-recursion theta stages write partial sums into the workspace, so they run
+            # only inside the transforms: time the whole inverse and forward (the theta stage plus
+            # the phi DFTs and, in the forward, the theta-direction quadrature operator)
+            stages = [("inverse_transform", lambda: plan.inverse(xd_, out=f, ws=ws)),
+                      ("forward_transform", lambda: plan.forward(f, out=y, ws=ws))]
         for name, fn in stages:
             fn()
             torch.cuda.synchronize(dev)

@@ -30,9 +30,9 @@
 //            each CTA writes its 64-degree partial, and a fixed-order sum over the partials gives
 //            ftilde (deterministic).
 //   forward  flm_{l,m} = sum_t g_m(t) d^l_m(t): a lane owns one degree and 16 chains of 16 rings
-//            (the sum over those rings is in-thread), 8 warps of a CTA own 128 rings of the same 32
-//            degrees, summed through shared memory; per-CTA partials over 128-ring blocks are
-//            summed in a fixed order.
+//            (the sum over those rings is in-thread), 4 warps of a CTA own 64 rings of the same 32
+//            degrees, summed through shared memory; per-CTA partials over 64-ring blocks are summed
+//            in a fixed order.
 // Chains of one lane share lambda_m (inverse) or are fed from lane-uniform shared-memory values
 // (forward: lambda_m and g_m per ring); their starting values are computed before the sweep and
 // held in the chain registers until the recursion reaches m = l.
@@ -48,10 +48,11 @@ using namespace theta;
 constexpr int kIW = 4;         // inverse: warps per CTA
 constexpr int kIK = 16;        // inverse: degrees (chains) per lane
 constexpr int kIL = kIW * kIK; // inverse: degrees per CTA
-constexpr int kFW = 8;         // forward: warps per CTA
+constexpr int kFW = 4;         // forward: warps per CTA
 constexpr int kFT = 16;        // forward: rings (chains) per lane
 constexpr int kFR = kFW * kFT; // forward: rings per CTA
-constexpr int kCh = 8;         // orders per staged chunk
+constexpr int kCh = 8;         // inverse: orders per staged chunk
+constexpr int kChF = 4;        // forward: orders per staged chunk
 
 // Ring seen from pi - b (chain B): same v, the other hemisphere, sin/cos of the half angle swapped.
 __device__ __forceinline__ RingData reflect_ring(const RingData& r) {
@@ -243,15 +244,15 @@ __global__ void __launch_bounds__(kIW * 32) mrec_inverse_kernel(InvArgs a, MrecA
 }
 
 // ------------------------------------------------------------------------------------------
-// Forward.  Grid: x = degree group (32 degrees, highest first), y = block of 128 rings, z = n
+// Forward.  Grid: x = degree group (32 degrees, highest first), y = block of 64 rings, z = n
 // index x batch groups.  part layout: [ring block][S][L][2L-1] (the flm layout).
 // ------------------------------------------------------------------------------------------
 template <int NB, bool PAIR>
 struct FwdSmem {
   static constexpr int NBX = PAIR ? 2 * NB : NB;
-  double2 gv[kCh][kFR][NBX];     // g_m(t) (times the ring weight; the -m partner with (-1)^m)
-  double lam[kCh][kFR];          // lambda_m(t)
-  double2 ab[kCh][32];           // (a_{m-1}, a_{m-1}/a_m) of the 32 degrees
+  double2 gv[kChF][kFR][NBX];     // g_m(t) (times the ring weight; the -m partner with (-1)^m)
+  double lam[kChF][kFR];          // lambda_m(t)
+  double2 ab[kChF][32];           // (a_{m-1}, a_{m-1}/a_m) of the 32 degrees
   double2 red[2][kFW][32][NBX];
   int mstar[kFR];
 };
@@ -286,9 +287,9 @@ __device__ __forceinline__ void forward_sweep(const FwdArgs& a, const MrecArgs& 
   double2* part = reinterpret_cast<double2*>(q.part) + (size_t)gr * nsigs * L * T;
   int buf = 0;
   unsigned live = 0;
-  for (int mc = ltop; mc >= mlow; mc -= kCh) {
+  for (int mc = ltop; mc >= mlow; mc -= kChF) {
     __syncthreads();
-    for (int idx = threadIdx.x; idx < kCh * kFR * NBX; idx += blockDim.x) {
+    for (int idx = threadIdx.x; idx < kChF * kFR * NBX; idx += blockDim.x) {
       const int b = idx % NBX, rr = (idx / NBX) % kFR, j = idx / (NBX * kFR);
       const int t = r0 + rr, mm = mc - j;
       const int bb = PAIR ? (b % NB) : b;
@@ -305,7 +306,7 @@ __device__ __forceinline__ void forward_sweep(const FwdArgs& a, const MrecArgs& 
       }
       sm.gv[j][rr][b] = gval;
     }
-    for (int idx = threadIdx.x; idx < kCh * kFR; idx += blockDim.x) {
+    for (int idx = threadIdx.x; idx < kChF * kFR; idx += blockDim.x) {
       const int rr = idx % kFR, j = idx / kFR;
       const int t = r0 + rr, mm = mc - j;
       double lam = 0.0;
@@ -315,13 +316,13 @@ __device__ __forceinline__ void forward_sweep(const FwdArgs& a, const MrecArgs& 
       }
       sm.lam[j][rr] = lam;
     }
-    for (int idx = threadIdx.x; idx < kCh * 32; idx += blockDim.x) {
+    for (int idx = threadIdx.x; idx < kChF * 32; idx += blockDim.x) {
       const int d = idx % 32, j = idx / 32;
       const int ll = lg0 + d, mm = mc - j;
       sm.ab[j][d] = (ll < L && mm <= ll && mm > -ll) ? q.ab[(size_t)ll * T + mm + L - 1] : make_double2(0.0, 0.0);
     }
     __syncthreads();
-    const int jend = min(kCh, mc - mlow + 1);
+    const int jend = min(kChF, mc - mlow + 1);
     for (int j = 0; j < jend; ++j) {
       const int m = mc - j;
       if (((ltop - m) & 7) == 0) {

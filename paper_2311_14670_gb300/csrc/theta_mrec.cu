@@ -25,14 +25,16 @@
 // Thread mapping.  The recursion variable m is also the output index of both contractions, so the
 // sums run across chains:
 //   inverse  ftilde_m(t) = sum_l h_{l,m} d^l_m(t): a lane owns one ring and 16 chains of 16
-//            consecutive degrees (the sum over those degrees is in-thread), 4 warps of a CTA own 64
-//            degrees of the same 32 rings and are summed through shared memory in a fixed order;
-//            each CTA writes its 64-degree partial, and a fixed-order sum over the partials gives
-//            ftilde (deterministic).
+//            consecutive degrees (the sum over those degrees is in-thread), the 2 warps of a CTA
+//            own 32 degrees of the same 32 rings and are summed through shared memory in a fixed
+//            order; each CTA writes its 32-degree partial, and a fixed-order sum over the partials
+//            gives ftilde (deterministic).
 //   forward  flm_{l,m} = sum_t g_m(t) d^l_m(t): a lane owns one degree and 16 chains of 16 rings
-//            (the sum over those rings is in-thread), 4 warps of a CTA own 64 rings of the same 32
-//            degrees, summed through shared memory; per-CTA partials over 64-ring blocks are summed
-//            in a fixed order.
+//            (the sum over those rings is in-thread), the 2 warps of a CTA own 32 rings of the same
+//            32 degrees, summed through shared memory; per-CTA partials over 32-ring blocks are
+//            summed in a fixed order.
+// Small CTAs (64 threads) keep the work per CTA small: the chains' lengths grow with the degree,
+// and fewer, larger CTAs left the GPU idle behind the high-degree ones (measured).
 // Chains of one lane share lambda_m (inverse) or are fed from lane-uniform shared-memory values
 // (forward: lambda_m and g_m per ring); their starting values are computed before the sweep and
 // held in the chain registers until the recursion reaches m = l.
@@ -45,10 +47,10 @@ namespace s2gb {
 namespace {
 using namespace theta;
 
-constexpr int kIW = 4;         // inverse: warps per CTA
+constexpr int kIW = 2;         // inverse: warps per CTA
 constexpr int kIK = 16;        // inverse: degrees (chains) per lane
 constexpr int kIL = kIW * kIK; // inverse: degrees per CTA
-constexpr int kFW = 4;         // forward: warps per CTA
+constexpr int kFW = 2;         // forward: warps per CTA
 constexpr int kFT = 16;        // forward: rings (chains) per lane
 constexpr int kFR = kFW * kFT; // forward: rings per CTA
 constexpr int kCh = 8;         // inverse: orders per staged chunk
@@ -78,7 +80,7 @@ __device__ __forceinline__ void mstep(double& x, double& y, double lam, double2 
 }
 
 // ------------------------------------------------------------------------------------------
-// Inverse.  Grid: x = tile of 32 rings, y = degree group (64 degrees, highest first), z = n index
+// Inverse.  Grid: x = tile of 32 rings, y = degree group (32 degrees, highest first), z = n index
 // x batch groups of NB signals.  part layout: [group][S][2L-1 (m + L - 1)][nint (ring - ring0)].
 // ------------------------------------------------------------------------------------------
 template <int NB, bool PAIR>
@@ -244,7 +246,7 @@ __global__ void __launch_bounds__(kIW * 32) mrec_inverse_kernel(InvArgs a, MrecA
 }
 
 // ------------------------------------------------------------------------------------------
-// Forward.  Grid: x = degree group (32 degrees, highest first), y = block of 64 rings, z = n
+// Forward.  Grid: x = degree group (32 degrees, highest first), y = block of 32 rings, z = n
 // index x batch groups.  part layout: [ring block][S][L][2L-1] (the flm layout).
 // ------------------------------------------------------------------------------------------
 template <int NB, bool PAIR>

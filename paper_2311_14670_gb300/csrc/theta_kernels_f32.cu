@@ -4,9 +4,10 @@
 //     converted to a float mantissa plus an integer exponent;
 //   * the recursion and the products in float32 (coefficients rounded once from the double-double
 //     tables), dead-chain bookkeeping every 2 steps because of float32's narrow exponent range;
-//   * compensated accumulation: the inverse folds blocks of 8 degrees into a (hi, lo) pair with
+//   * compensated accumulation: the inverse folds blocks of 32 degrees into a (hi, lo) pair with
 //     Knuth's two-sum; the forward reduces its per-thread partial sums across the warp with a
-//     two-sum reduce-scatter and across warps in float64.
+//     reduce-scatter whose top two levels use two-sum, and across warps in float64;
+//   * once all chains of a warp are live, the exponent bookkeeping stops (a live chain stays live).
 #include "theta_common.cuh"
 
 namespace s2gb {
@@ -81,9 +82,14 @@ __device__ __forceinline__ void step_f32(float& x, float& y, float v, unsigned n
 }
 
 // ------------------------------------------------------------------------------------------ inverse
+// Accumulation: each thread sums 32 degrees (one staged chunk) per (ring, signal) in float32
+// registers, then folds that block sum into a compensated (hi, lo) pair kept in shared memory
+// (acc: [KT * NB slots][hi, lo][threads]) with Knuth's two-sum.  Keeping the pairs in shared memory
+// leaves registers for up to 8 signals per CTA, over which the recursion is shared.
 template <int KT, int NB, bool DIFF>
 __device__ __forceinline__ void inverse_body_f32(const InvArgs& a, int m, int ni, int tile, int l0,
-                                                 float2* __restrict__ hs, float* __restrict__ cs) {
+                                                 float2* __restrict__ hs, float* __restrict__ cs,
+                                                 float2* __restrict__ acc) {
   const int L = a.L, T = 2 * L - 1;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int mi = m + L - 1;
@@ -95,7 +101,7 @@ __device__ __forceinline__ void inverse_body_f32(const InvArgs& a, int m, int ni
   int E[KT], tt[KT];
   bool north[KT];
   unsigned nmask[KT];
-  float2 blk[KT][NB], hi[KT][NB], lo[KT][NB];
+  float2 blk[KT][NB];
 #pragma unroll
   for (int i = 0; i < KT; ++i) {
     const int t = a.ring0 + tile * KT * nt + i * nt + tid;
@@ -113,11 +119,15 @@ __device__ __forceinline__ void inverse_body_f32(const InvArgs& a, int m, int ni
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
       blk[i][b] = make_float2(0.f, 0.f);
-      hi[i][b] = make_float2(0.f, 0.f);
-      lo[i][b] = make_float2(0.f, 0.f);
+      acc[(2 * (i * NB + b)) * nt + tid] = make_float2(0.f, 0.f);
+      acc[(2 * (i * NB + b) + 1) * nt + tid] = make_float2(0.f, 0.f);
     }
   }
 
+  // once every chain of the warp is live (|d| >= 2^-90 in float32 range) it stays live: the
+  // exponent bookkeeping and the live-mask votes stop
+  bool all_live = false;
+  unsigned live = 0;
   const double* scale = a.scale + (size_t)ni * L;
   for (int jc = l0; jc < L; jc += kChunk32) {
     __syncthreads();
@@ -139,9 +149,11 @@ __device__ __forceinline__ void inverse_body_f32(const InvArgs& a, int m, int ni
     __syncthreads();
     const int jend = min(kChunk32, L - jc);
     for (int j8 = 0; j8 < jend; j8 += 8) {
-      unsigned live = 0;
+      if (!all_live) {
+        live = 0;
 #pragma unroll
-      for (int i = 0; i < KT; ++i) live |= (__any_sync(0xffffffffu, E[i] == 0) ? 1u : 0u) << i;
+        for (int i = 0; i < KT; ++i) live |= (__any_sync(0xffffffffu, E[i] == 0) ? 1u : 0u) << i;
+      }
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
         const int jj = j8 + u;
@@ -167,24 +179,33 @@ __device__ __forceinline__ void inverse_body_f32(const InvArgs& a, int m, int ni
             for (int i = 0; i < KT; ++i) step_f32<DIFF>(x[i], y[i], v[i], nmask[i], north[i], c);
           }
         }
-        if (u & 1) {
+        if ((u & 1) && !all_live) {
 #pragma unroll
           for (int i = 0; i < KT; ++i) renorm_f32(x[i], y[i], E[i]);
           live = 0;   // chains may have come alive: refresh the warp-uniform mask
+          bool mine = true;
 #pragma unroll
-          for (int i = 0; i < KT; ++i) live |= (__any_sync(0xffffffffu, E[i] == 0) ? 1u : 0u) << i;
+          for (int i = 0; i < KT; ++i) {
+            live |= (__any_sync(0xffffffffu, E[i] == 0) ? 1u : 0u) << i;
+            mine = mine && E[i] == 0;
+          }
+          all_live = __all_sync(0xffffffffu, mine);
         }
       }
-      // fold the block of 8 degrees into the compensated (hi, lo) sums
+    }
+    // fold the chunk's block sums into the compensated (hi, lo) pairs
 #pragma unroll
-      for (int i = 0; i < KT; ++i) {
+    for (int i = 0; i < KT; ++i) {
 #pragma unroll
-        for (int b = 0; b < NB; ++b) {
-          float s, e;
-          two_sum_f(hi[i][b].x, blk[i][b].x, s, e); hi[i][b].x = s; lo[i][b].x += e;
-          two_sum_f(hi[i][b].y, blk[i][b].y, s, e); hi[i][b].y = s; lo[i][b].y += e;
-          blk[i][b] = make_float2(0.f, 0.f);
-        }
+      for (int b = 0; b < NB; ++b) {
+        float2& hi = acc[(2 * (i * NB + b)) * nt + tid];
+        float2& lo = acc[(2 * (i * NB + b) + 1) * nt + tid];
+        float2 h2 = hi, l2 = lo;
+        float s, e;
+        two_sum_f(h2.x, blk[i][b].x, s, e); h2.x = s; l2.x += e;
+        two_sum_f(h2.y, blk[i][b].y, s, e); h2.y = s; l2.y += e;
+        hi = h2; lo = l2;
+        blk[i][b] = make_float2(0.f, 0.f);
       }
     }
   }
@@ -197,9 +218,10 @@ __device__ __forceinline__ void inverse_body_f32(const InvArgs& a, int m, int ni
       for (int b = 0; b < NB; ++b) {
         const int sig = sig0 + b;
         if (sig < a.nsig) {
+          const float2 hi = acc[(2 * (i * NB + b)) * nt + tid], lo = acc[(2 * (i * NB + b) + 1) * nt + tid];
           float2* o = reinterpret_cast<float2*>(a.out) + (size_t)(sig * a.nN + ni) * a.s_sig +
                       tt[i] * a.s_t + col * a.s_m;
-          *o = make_float2(hi[i][b].x + lo[i][b].x, hi[i][b].y + lo[i][b].y);
+          *o = make_float2(hi.x + lo.x, hi.y + lo.y);
         }
       }
     }
@@ -210,6 +232,7 @@ template <int KT, int NB>
 __global__ void __launch_bounds__(128) theta_inverse_kernel_f32(InvArgs a, int ntiles) {
   __shared__ float2 hs[kChunk32 * NB];
   __shared__ float cs[kChunk32 * kCoefPerStep];
+  extern __shared__ float2 acc_smem[];            // [KT * NB][2][blockDim.x]
   const int L = a.L;
   const int rank = a.rank0 + (int)(blockIdx.x / ntiles), tile = blockIdx.x % ntiles;
   const int m = a.mpos ? rank : m_of_rank(rank);
@@ -217,16 +240,30 @@ __global__ void __launch_bounds__(128) theta_inverse_kernel_f32(InvArgs a, int n
   const int l0 = a.seed[(size_t)ni * (2 * L - 1) + m + L - 1].l0;
   const int t_lo = a.ring0 + tile * KT * blockDim.x, t_hi = min(a.nring, t_lo + KT * (int)blockDim.x) - 1;
   const bool diff = a.ring[t_lo].diff || a.ring[t_hi].diff;
-  if (diff) inverse_body_f32<KT, NB, true>(a, m, ni, tile, l0, hs, cs);
-  else inverse_body_f32<KT, NB, false>(a, m, ni, tile, l0, hs, cs);
+  if (diff) inverse_body_f32<KT, NB, true>(a, m, ni, tile, l0, hs, cs, acc_smem);
+  else inverse_body_f32<KT, NB, false>(a, m, ni, tile, l0, hs, cs, acc_smem);
 }
 
 // ------------------------------------------------------------------------------------------ forward
-// Warp reduce-scatter of 32 (hi, lo) pairs with two-sum additions: lane l ends with slot l.
-__device__ __forceinline__ void warp_reduce_scatter32_f(float (&h)[32], float (&l)[32], float& oh, float& ol) {
+// Warp reduce-scatter of 32 partial sums: lane l ends with slot l as an unevaluated (hi, lo) pair.
+// The first three levels (sums of up to 8 lanes) add in plain float32; the top two levels, where
+// the partial sums and hence the rounding errors are largest, use Knuth's two-sum and carry the
+// error terms.
+__device__ __forceinline__ void warp_reduce_scatter32_f(float (&h)[32], float& oh, float& ol) {
   const int lane = threadIdx.x & 31;
 #pragma unroll
-  for (int w = 16; w >= 1; w >>= 1) {
+  for (int w = 16; w >= 4; w >>= 1) {
+    const bool up = (lane & w) != 0;
+#pragma unroll
+    for (int s = 0; s < w; ++s) {
+      const float send = up ? h[s] : h[s + w];
+      const float keep = up ? h[s + w] : h[s];
+      h[s] = keep + __shfl_xor_sync(0xffffffffu, send, w);
+    }
+  }
+  float l[2] = {0.f, 0.f};
+#pragma unroll
+  for (int w = 2; w >= 1; w >>= 1) {
     const bool up = (lane & w) != 0;
 #pragma unroll
     for (int s = 0; s < w; ++s) {
@@ -247,7 +284,7 @@ __device__ __forceinline__ void warp_reduce_scatter32_f(float (&h)[32], float (&
 }
 
 template <int KT, int NB, int PAT>
-__global__ void __launch_bounds__(128) theta_forward_kernel_f32(FwdArgs a) {
+__global__ void __launch_bounds__(256) theta_forward_kernel_f32(FwdArgs a) {
   constexpr int JR = 16 / NB;
   extern __shared__ double smem64[];
   const int L = a.L, T = 2 * L - 1;
@@ -315,13 +352,18 @@ __global__ void __launch_bounds__(128) theta_forward_kernel_f32(FwdArgs a) {
 
   const float* coef_m = a.coef32 + ((size_t)ni * T + mi) * (size_t)L * kCoefPerStep;
   int buf = 0;
+  // once every chain of the warp is live it stays live: the bookkeeping and votes stop
+  bool all_live = false;
+  unsigned live = 0;
   for (int j0 = l0; j0 < L; j0 += JR) {
-    float ph[32], pl[32];
+    float ph[32];
 #pragma unroll
-    for (int s = 0; s < 32; ++s) { ph[s] = 0.f; pl[s] = 0.f; }
-    unsigned live = 0;
+    for (int s = 0; s < 32; ++s) ph[s] = 0.f;
+    if (!all_live) {
+      live = 0;
 #pragma unroll
-    for (int i = 0; i < KT; ++i) live |= (__any_sync(0xffffffffu, E[i] == 0) ? 1u : 0u) << i;
+      for (int i = 0; i < KT; ++i) live |= (__any_sync(0xffffffffu, E[i] == 0) ? 1u : 0u) << i;
+    }
 #pragma unroll
     for (int jr = 0; jr < JR; ++jr) {
       const int j = j0 + jr;
@@ -354,16 +396,21 @@ __global__ void __launch_bounds__(128) theta_forward_kernel_f32(FwdArgs a) {
           }
         }
       }
-      if ((jr & 1) || jr == JR - 1) {
+      if (((jr & 1) || jr == JR - 1) && !all_live) {
 #pragma unroll
         for (int i = 0; i < KT; ++i) renorm_f32(x[i], y[i], E[i]);
         live = 0;   // chains may have come alive: refresh the warp-uniform mask
+        bool mine = true;
 #pragma unroll
-        for (int i = 0; i < KT; ++i) live |= (__any_sync(0xffffffffu, E[i] == 0) ? 1u : 0u) << i;
+        for (int i = 0; i < KT; ++i) {
+          live |= (__any_sync(0xffffffffu, E[i] == 0) ? 1u : 0u) << i;
+          mine = mine && E[i] == 0;
+        }
+        all_live = __all_sync(0xffffffffu, mine);
       }
     }
     float oh, ol;
-    warp_reduce_scatter32_f(ph, pl, oh, ol);
+    warp_reduce_scatter32_f(ph, oh, ol);
     red[(buf * nwarps + warp) * 32 + lane] = (double)oh + (double)ol;
     __syncthreads();
     if (warp == 0) {
@@ -386,8 +433,12 @@ cudaError_t launch_inv32(const Plan& p, const InvArgs& a, cudaStream_t st) {
   const int nt = 128;
   const int ntiles = (a.nring - a.ring0 + KT * nt - 1) / (KT * nt);
   if (ntiles == 0) return cudaSuccess;          // no rings for the recursion (MWSS, L = 1)
+  const size_t smem = sizeof(float2) * 2 * KT * NB * nt;
+  auto kern = theta_inverse_kernel_f32<KT, NB>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
   dim3 grid(a.nrank * ntiles, a.nN, (a.nsig + NB - 1) / NB);
-  theta_inverse_kernel_f32<KT, NB><<<grid, nt, 0, st>>>(a, ntiles);
+  kern<<<grid, nt, smem, st>>>(a, ntiles);
   return launched();
 }
 
@@ -420,14 +471,17 @@ cudaError_t launch_fwd32_nb(const Plan& p, const FwdArgs& a0, cudaStream_t st) {
   if (R <= 256) return launch_fwd32<2, NB, 1>(p, a, 128, st);
   if (R <= 512) return launch_fwd32<4, NB, 0>(p, a, 128, st);
   if (R <= 1024) return launch_fwd32<8, NB, 0>(p, a, 128, st);
-  const int nt = ((R + 16 * 32 - 1) / (16 * 32)) * 32;
-  if (nt > 128) return cudaErrorInvalidConfiguration;
-  return launch_fwd32<16, NB, 0>(p, a, nt, st);
+  // up to 2048 rings: 8 rings per thread and up to 256 threads (the polar caps fit in the first and
+  // last slot of nt >= R/8 rings); more threads per SM than 16 rings per thread would allow
+  const int nt = ((R + 8 * 32 - 1) / (8 * 32)) * 32;
+  if (nt > 256) return cudaErrorInvalidConfiguration;
+  return launch_fwd32<8, NB, 0>(p, a, nt, st);
 }
 
 }  // namespace
 
 cudaError_t launch_theta_inverse_f32(const Plan& p, const InvArgs& a, cudaStream_t st) {
+  if (a.nsig >= 8) return launch_inv32_nb<8>(p, a, st);
   if (a.nsig >= 4) return launch_inv32_nb<4>(p, a, st);
   if (a.nsig >= 2) return launch_inv32_nb<2>(p, a, st);
   return launch_inv32_nb<1>(p, a, st);

@@ -70,8 +70,10 @@ WORKLOADS = {
     "l2048s2b1": (2048, 2, 0, 1, 0.0, "spin-2 SHT round trip, L=2048, MW 2048x4095, batch 1, FP64"),
     "l1024s0b4f32": (1024, 0, 0, 4, 1.0, "spin-0 SHT round trip, L=1024, MW 1024x2047, batch 4, FP32 mixed "
                      "precision (float64 starting values)"),
+    "l1024s0b16f32": (1024, 0, 0, 16, 1.0, "spin-0 SHT round trip, L=1024, MW 1024x2047, batch 16, FP32 mixed "
+                      "precision (float64 starting values)"),
 }
-PRECISION = {"l2048s0b16f32grad": "fp32", "l1024s0b4f32": "fp32"}
+PRECISION = {"l2048s0b16f32grad": "fp32", "l1024s0b4f32": "fp32", "l1024s0b16f32": "fp32"}
 REAL = {"l2048realb1", "l1024realb4", "l2048realb1pre"}
 PRECOMPUTE = {"l1024s2b4pre", "l1024s0b1pre", "l2048s0b1pre", "l2048realb1pre"}
 GRAD = {"l2048s0b16f32grad"}

@@ -126,39 +126,6 @@ __device__ __forceinline__ Slot slot_of(int b, int sig0, int nsig, int nN, int n
   return sl;
 }
 
-struct StepCoef {
-  double A, C, Kn, Ks, Kdn, Kds;
-};
-
-__device__ __forceinline__ StepCoef load_coef(const double* c) {
-  const double2* c2 = reinterpret_cast<const double2*>(c);
-  double2 a = __ldg(c2), b = __ldg(c2 + 1), d = __ldg(c2 + 2);
-  return {a.x, a.y, b.x, b.y, d.x, d.y};
-}
-
-// One recursion step of a chain. north/diff are per-chain constants.
-template <bool DIFF>
-__device__ __forceinline__ void step(double& x, double& y, double v, unsigned north_mask, bool north,
-                                     const StepCoef& c) {
-  // sA = -A on north rings, +A on south rings
-  const double sA = flip_sign(c.A, north_mask);
-  if (!DIFF) {
-    const double K = north ? c.Kn : c.Ks;
-    const double P = fma(sA, v, K);
-    const double xn = fma(P, x, -(c.C * y));
-    y = x;
-    x = xn;
-  } else {
-    const double K = north ? c.Kdn : c.Kds;
-    const double Q = fma(sA, v, K);
-    const double sC = flip_sign(c.C, north_mask ^ 0x80000000u);   // +C north, -C south
-    const double en = fma(Q, x, sC * y);
-    const double sg = north ? 1.0 : -1.0;                          // sigma
-    x = fma(sg, x, en);
-    y = en;
-  }
-}
-
 __device__ __forceinline__ int m_of_rank(int r) {   // 0, -1, 1, -2, 2, ...: longest chains first
   return (r == 0) ? 0 : ((r & 1) ? -((r + 1) >> 1) : (r >> 1));
 }

@@ -316,6 +316,13 @@ def run_ours(args, world, rank, local):
             flops = algorithmic_flops(L, n_list, R, B, real)
             kern[name] = {"ms": kms, "flops": flops, "tflops": flops / (kms * 1e-3) / 1e12}
 
+    # the step split into the two theta kernels and everything else (phi / theta-direction FFTs on
+    # cuFFT, glue kernels): per step, from the separately timed theta kernels
+    stage_split = None
+    if "theta_inverse" in kern and "theta_forward" in kern:
+        th = kern["theta_inverse"]["ms"] + kern["theta_forward"]["ms"]
+        stage_split = {"theta_kernels_ms": round(th, 3),
+                       "fft_and_glue_ms": round(max(0.0, ms / args.steps - th), 3)}
     ms, ms_e2e = max_over_ranks([ms, ms_e2e], device=dev)
     # a gradient step is one inverse transform plus its adjoint: 2 transforms per signal, as a round trip
     transforms_per_step = 2 * B * world * (2 * N - 1 if N else 1)
@@ -358,6 +365,7 @@ def run_ours(args, world, rank, local):
                 "h2d_bytes_per_step": in_bytes, "d2h_bytes_per_step": in_bytes},
         "gpu_launches": k1 - k0,
         "kernels": kern,
+        "stages": stage_split,
         "roofline": roof,
         "clocks": {k: ck[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
     }

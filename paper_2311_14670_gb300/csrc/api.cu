@@ -40,6 +40,28 @@ cudaError_t launched() {
   return cudaGetLastError();
 }
 
+// cudaFuncSetAttribute(MaxDynamicSharedMemorySize) once per (kernel, device) and size: later calls
+// that need no larger size do not touch the runtime, so transforms can be captured into CUDA graphs
+// once they have run (the attribute is not a stream operation).
+cudaError_t set_dynamic_smem(const void* func, size_t bytes) {
+  static std::mutex mu;
+  static std::vector<std::pair<std::pair<const void*, int>, size_t>> done;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  for (auto& d : done)
+    if (d.first.first == func && d.first.second == dev) {
+      if (bytes <= d.second) return cudaSuccess;
+      e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+      if (e == cudaSuccess) d.second = bytes;
+      return e;
+    }
+  e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) done.push_back({{func, dev}, bytes});
+  return e;
+}
+
 namespace {
 
 struct DeviceGuard {

@@ -198,6 +198,8 @@ inline void mrange_ranks(int lo, int hi, int& rank0, int& nrank) {
 // Every launcher returns launched(): it counts one launch of this library's kernels (a host-side,
 // process-wide counter read by s2gb_kernels_launched) and returns cudaGetLastError().
 cudaError_t launched();
+// sets a kernel's dynamic shared-memory limit, once per (kernel, device) and size (api.cu)
+cudaError_t set_dynamic_smem(const void* func, size_t bytes);
 
 cudaError_t launch_theta_inverse(const Plan& p, const InvArgs& a, cudaStream_t st);
 // MWSS pole rings theta = 0 and pi (Sec. 3.3: d^l_{mn}(0) = delta_{mn}, d^l_{mn}(pi) =

@@ -373,7 +373,7 @@ cudaError_t launch_fwd(const Plan& p, const FwdArgs& a, int nt, cudaStream_t st)
   const int rows = KT * nt;
   const size_t smem = sizeof(double2) * NBX * rows + sizeof(double) * (2 * (nt / 32) * 32 + rows);
   auto kern = theta_forward_kernel<KT, NB, PAT, PAIR>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = set_dynamic_smem((const void*)kern, smem);
   if (e != cudaSuccess) return e;
   dim3 grid(a.nrank, PAIR ? (a.nN + 1) / 2 : a.nN, (a.nsig + NB - 1) / NB);
   kern<<<grid, nt, smem, st>>>(a);

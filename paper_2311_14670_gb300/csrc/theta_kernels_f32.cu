@@ -435,7 +435,7 @@ cudaError_t launch_inv32(const Plan& p, const InvArgs& a, cudaStream_t st) {
   if (ntiles == 0) return cudaSuccess;          // no rings for the recursion (MWSS, L = 1)
   const size_t smem = sizeof(float2) * 2 * KT * NB * nt;
   auto kern = theta_inverse_kernel_f32<KT, NB>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = set_dynamic_smem((const void*)kern, smem);
   if (e != cudaSuccess) return e;
   dim3 grid(a.nrank * ntiles, a.nN, (a.nsig + NB - 1) / NB);
   kern<<<grid, nt, smem, st>>>(a, ntiles);
@@ -454,7 +454,7 @@ cudaError_t launch_fwd32(const Plan& p, const FwdArgs& a, int nt, cudaStream_t s
   const int rows = KT * nt;
   const size_t smem = sizeof(double) * 2 * (nt / 32) * 32 + sizeof(float2) * NB * rows + sizeof(float) * rows;
   auto kern = theta_forward_kernel_f32<KT, NB, PAT>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = set_dynamic_smem((const void*)kern, smem);
   if (e != cudaSuccess) return e;
   dim3 grid(a.nrank, a.nN, (a.nsig + NB - 1) / NB);
   kern<<<grid, nt, smem, st>>>(a);

@@ -507,7 +507,7 @@ cudaError_t launch_inv_m(const Plan& p, const InvArgs& a, const MrecArgs& q, cud
   if (nt > 0) {
     const size_t smem = sizeof(InvSmem<NB, PAIR>);
     auto kern = mrec_inverse_kernel<NB, PAIR>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = set_dynamic_smem((const void*)kern, smem);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)((nt + 31) / 32), (unsigned)((a.L + kIL - 1) / kIL),
               (unsigned)(a.nN * ((a.nsig + NB - 1) / NB)));
@@ -526,7 +526,7 @@ cudaError_t launch_fwd_m(const Plan& p, const FwdArgs& a, const MrecArgs& q, cud
   if (nr > 0) {
     const size_t smem = sizeof(FwdSmem<NB, PAIR>);
     auto kern = mrec_forward_kernel<NB, PAIR>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = set_dynamic_smem((const void*)kern, smem);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)((a.L + 31) / 32), (unsigned)nblocks, (unsigned)(a.nN * ((a.nsig + NB - 1) / NB)));
     kern<<<grid, kFW * 32, smem, st>>>(a, q);

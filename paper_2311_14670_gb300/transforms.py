@@ -192,6 +192,12 @@ class Plan:
         nat.forward_theta(self._h, g, out, batch, self._stream())
         return out
 
+    def graphed(self, steps, batch: int) -> "GraphedTransform":
+        """The transforms ``steps`` (names of Plan methods, e.g. ["inverse", "forward"], each
+        feeding the next) on ``batch`` signals, captured once into a CUDA graph; see
+        GraphedTransform."""
+        return GraphedTransform(self, list(steps), int(batch))
+
     def close(self):
         if getattr(self, "_h", None):
             nat.plan_destroy(self._h)
@@ -202,6 +208,72 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+_KINDS = {"forward": ("signal", "coef"), "inverse": ("coef", "signal"),
+          "adjoint_forward": ("coef", "signal"), "adjoint_inverse": ("signal", "coef")}
+
+
+class GraphedTransform:
+    """A chain of transforms on a fixed batch, captured into one CUDA graph and replayed.
+
+    For small bandlimits a transform is a handful of short kernel and cuFFT launches whose launch
+    overhead exceeds their run time; replaying the captured graph issues them as one graph launch.
+    The input, the intermediate results, the output and the workspace are static buffers owned by
+    this object: ``__call__`` copies its argument into the input buffer, replays, and returns the
+    output buffer (overwritten by the next call).  The transforms run once before capture (so the
+    library's one-time kernel settings are made outside the capture).  Replays do not advance the
+    library's launch counter (``launches_per_replay`` holds the count taken at capture).
+    """
+
+    def __init__(self, plan: Plan, steps, batch: int):
+        if not steps or any(st not in _KINDS for st in steps):
+            raise ValueError(f"steps must be names among {list(_KINDS)}")
+        for a, b in zip(steps, steps[1:]):
+            if _KINDS[a][1] != _KINDS[b][0]:
+                raise ValueError(f"{a} produces a {_KINDS[a][1]} array, {b} takes a {_KINDS[b][0]} array")
+        if not 1 <= batch <= plan.max_batch:
+            raise ValueError(f"batch {batch} outside [1, {plan.max_batch}]")
+        self.plan, self.steps, self.batch = plan, steps, batch
+
+        def buf(kind):
+            shape_of, dtype = plan._spec(kind)
+            return torch.zeros(shape_of(batch), dtype=dtype, device=plan.device)
+
+        self.bufs = [buf(_KINDS[steps[0]][0])] + [buf(_KINDS[st][1]) for st in steps]
+        self.ws = torch.empty(plan.workspace_bytes(batch), dtype=torch.uint8, device=plan.device)
+        side = torch.cuda.Stream(plan.device)
+        side.wait_stream(torch.cuda.current_stream(plan.device))
+        with torch.cuda.stream(side):
+            self._run()                               # outside the capture: one-time settings
+        torch.cuda.synchronize(plan.device)
+        k0 = nat.kernels_launched()
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph, stream=side):
+            self._run()
+        self.launches_per_replay = nat.kernels_launched() - k0
+        torch.cuda.synchronize(plan.device)
+
+    def _run(self):
+        for i, st in enumerate(self.steps):
+            getattr(self.plan, st)(self.bufs[i], out=self.bufs[i + 1], ws=self.ws)
+
+    @property
+    def input(self) -> torch.Tensor:
+        return self.bufs[0]
+
+    @property
+    def output(self) -> torch.Tensor:
+        return self.bufs[-1]
+
+    def replay(self) -> torch.Tensor:
+        """Replay on the current stream with the input buffer as it is."""
+        self.graph.replay()
+        return self.bufs[-1]
+
+    def __call__(self, x: torch.Tensor) -> torch.Tensor:
+        self.bufs[0].copy_(x)
+        return self.replay()
 
 
 class _Forward(torch.autograd.Function):

@@ -14,7 +14,13 @@
 // <= L-1 in theta, int_0^pi G d sin = int_torus H d |sin|/2... = (2pi/T) sum over the torus of H d,
 // folded onto the L rings with nu_t = 2 (t < L-1) and nu_{L-1} = 1.  This integrates exactly what
 // the upsample-to-2L route of Sec. 4.2.2 integrates, on L rings instead of 2L.
-// Inverse (Eqs. disc_ish_expanded, disc_ish_fft): theta kernel into [t][m mod T], then IDFT_T.
+// MWSS (Sec. 4.2.2, L+1 rings with both poles, P = 2L phi samples): the same construction on a
+// torus of TS = 2L points starting at theta = 0 (fine grid unshifted, the Nyquist frequency L of
+// the 2L-point DFTs dropped), fold factors 1 on the two poles and 2 elsewhere.  DH (Sec. 4.2.1,
+// 2L rings): no torus operator -- the theta kernel applies the DH weights times 2 pi/P to the phi
+// spectra directly.
+// Inverse (Eqs. disc_ish_expanded, disc_ish_fft): theta kernel into [t][m mod P], then IDFT_P
+// (P = T on MW and DH).
 // Wigner (Sec. 2.3, 4.5): a gamma DFT (forward, scaled by 2 pi/(2N-1)) or IDFT (inverse) around
 // 2N-1 spin-(-n) stages, with per-degree factors 1 (forward) and (2l+1)/(8 pi^2) (inverse).
 // Adjoints (Sec. 5.2): every stage transposed in reverse order; the operator between the two

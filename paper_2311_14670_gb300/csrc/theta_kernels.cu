@@ -174,7 +174,8 @@ __global__ void __launch_bounds__(128) theta_inverse_kernel(InvArgs a, int ntile
 
 // ------------------------------------------------------------------------------------------
 // Forward theta stage: flm[sig][l][m] = scale_l sum_t d^l_{m,n}(theta_t) g[sig][m][t] (* nu_t).
-// One CTA per (m, n, batch group) owns all L rings: thread tid holds rings t = i*blockDim + tid.
+// One CTA per (m, n, batch group) owns all rings of the launch: thread tid holds rings
+// t = row0 + i*blockDim + tid (the last slot the last blockDim rings).
 // Per degree every thread forms partial sums over its KT rings (FMA chains); partial sums of
 // JR = 16/NB consecutive degrees (32 doubles) are reduced across the warp by a reduce-scatter
 // (31 additions per lane for 32 values, lane l ends with value l), then across warps through

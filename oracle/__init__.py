@@ -11,9 +11,11 @@ It is plain, slow and meant to be read against the paper:
 * ``sampling``   -- McEwen-Wiaux (MW) sample positions (Sec. 4.2.2) and the MW quadrature
                     weights at an upsampled bandlimit (Sec. 4.2.2, weight formula and upsampling).
 * ``wigner``     -- Wigner small-d functions: the Jacobi-polynomial representation (Sec. 3.1)
-                    in arbitrary precision, and the paper's recursion over the order m
+                    in arbitrary precision, the paper's recursion over the order m
                     (Sec. 3.3, Eq. "wigner-d-recursion", started from Eq. "initial_values",
-                    with the running renormalisation of Sec. 3.4; poles from Sec. 3.3).
+                    with the running renormalisation of Sec. 3.4; poles from Sec. 3.3), and, as
+                    a third independent method, the half-integer recursion over the degree
+                    (after Risbo 1996) from the product of representations.
 * ``transforms`` -- forward / inverse spin-s SHT by separation of variables (Sec. 4.1,
                     Eqs. disc_sh_expanded, disc_sh_fft, disc_ish_fft, disc_ish_expanded) with
                     direct DFT sums, the Wigner transform as gamma-DFT plus spin-(-n) SHTs

@@ -1,6 +1,7 @@
 """Wigner small-d functions d^l_{mn}(beta) for the oracle (test infrastructure only).
 
-Two evaluations that share nothing but the definition:
+Three evaluations that share nothing but the definition (the third, ``wigner_d_halfstep``, is
+documented at its definition below):
 
 ``wigner_d_jacobi``
     The Jacobi-polynomial representation of Sec. 3.1 (Eq. "wignerd_jacobi", after Varshalovich
@@ -186,3 +187,45 @@ def wigner_d_table(ells, n: int, betas) -> np.ndarray:
     blockD = np.where(np.abs(mgrid) <= L_ok[:, None, None], blockD, 0.0)
     D[np.ix_(idx_l, np.arange(2 * M + 1), idx_b)] = blockD
     return D
+
+
+def wigner_d_halfstep(L: int, betas) -> np.ndarray:
+    """d^l_{mn}(beta) for every integer l < L and all |m|, |n| <= l, by the half-integer recursion
+    over the degree (after Risbo 1996): the representation of degree j is the stretched part of
+    the product of those of degrees j - 1/2 and 1/2, so with the Clebsch-Gordan coefficients
+    <j-1/2, m-mu; 1/2, mu | j, m> = sqrt((j + 2 mu m) / (2j)),
+
+        d^j_{mn} = sum_{mu, nu = +-1/2} sqrt((j + 2 mu m)(j + 2 nu n)) / (2j)
+                                        d^{j-1/2}_{m-mu, n-nu} d^{1/2}_{mu nu},
+
+    d^{1/2}_{++} = d^{1/2}_{--} = cos(b/2), d^{1/2}_{+-} = -sin(b/2), d^{1/2}_{-+} = sin(b/2).
+    Every step is a product of unitary maps, so the recursion is stable in float64 at any beta;
+    it shares nothing with the recursion over m or the Jacobi form.  O(L^3) per angle: for test
+    sizes.  Returns D of shape (L, 2L-1, 2L-1, len(betas)) with D[l, m+L-1, n+L-1, k] =
+    d^l_{mn}(betas[k]) (0 where |m| or |n| > l).
+    """
+    b = np.atleast_1d(np.asarray(betas)).astype(np.longdouble)
+    p = np.cos(b / 2).astype(np.float64)
+    q = np.sin(b / 2).astype(np.float64)
+    nb = len(b)
+    out = np.zeros((L, 2 * L - 1, 2 * L - 1, nb))
+    d = np.ones((1, 1, nb))                        # degree 0
+    out[0, L - 1, L - 1] = 1.0
+    for tj in range(1, 2 * L - 1):                 # 2j, j = 1/2, 1, ..., L-1
+        a = np.arange(tj + 1)                      # m = -j + a
+        sa = np.sqrt(a / tj)[:, None, None]        # sqrt((j + m) / (2j))
+        ra = np.sqrt((tj - a) / tj)[:, None, None]  # sqrt((j - m) / (2j))
+        sb = np.sqrt(a / tj)[None, :, None]
+        rb = np.sqrt((tj - a) / tj)[None, :, None]
+        prev = np.zeros((tj + 2, tj + 2, nb))      # padded: prev index a' + 1
+        prev[1:tj + 1, 1:tj + 1] = d
+        pm = prev[0:tj + 1, 0:tj + 1]              # d^{j-1/2}_{m-1/2, n-1/2}
+        p_ = prev[0:tj + 1, 1:tj + 2]              # d^{j-1/2}_{m-1/2, n+1/2}
+        m_ = prev[1:tj + 2, 0:tj + 1]              # d^{j-1/2}_{m+1/2, n-1/2}
+        mm = prev[1:tj + 2, 1:tj + 2]              # d^{j-1/2}_{m+1/2, n+1/2}
+        d = (sa * sb * p * pm - sa * rb * q * p_ + ra * sb * q * m_ + ra * rb * p * mm)
+        if tj % 2 == 0:
+            l = tj // 2
+            out[l, L - 1 - l:L + l, L - 1 - l:L + l] = d
+    return out
+

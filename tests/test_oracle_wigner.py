@@ -154,3 +154,40 @@ def test_seed_is_initial_value_formula():
                    * (-mpmath.sin(bb / 2)) ** (ell - n) * mpmath.cos(bb / 2) ** (ell + n))
         got = table_value(ell, ell, n, b)
         assert abs(got - float(ref)) <= 1e-14 * abs(float(ref)) + 1e-300
+
+
+# ---- a third, independent method: the half-integer recursion over the degree (after Risbo 1996)
+def test_halfstep_recursion_matches_jacobi_small_l():
+    from oracle.wigner import wigner_d_halfstep, wigner_d_jacobi
+    L = 6
+    betas = np.array([0.0, 0.3, 1.2, np.pi / 2, 2.9, np.pi])
+    H = wigner_d_halfstep(L, betas)
+    err = 0.0
+    for l in range(L):
+        for m in range(-l, l + 1):
+            for n in range(-l, l + 1):
+                for k, b in enumerate(betas):
+                    err = max(err, abs(H[l, m + L - 1, n + L - 1, k] - float(wigner_d_jacobi(l, m, n, float(b)))))
+    assert err <= 2e-15
+
+
+@pytest.mark.parametrize("n", [0, 2, -3, 7])
+def test_paper_recursion_over_m_matches_halfstep_recursion_l119(n):
+    """The paper's recursion over m (two-sided) and the half-integer recursion over the degree agree
+    to L = 120, near both poles and at the equator."""
+    from oracle.wigner import wigner_d_halfstep
+    L = 120
+    betas = np.array([1e-3, 0.05, 0.7, 1.5707, 2.2, 3.1])
+    H = wigner_d_halfstep(L, betas)[:, :, n + L - 1, :]                  # [l, m, beta]
+    T = wigner_d_table(np.arange(L), n, betas.astype(np.longdouble))       # [l, m, beta]
+    assert np.abs(H - T).max() <= 5e-14
+
+
+def test_halfstep_matrices_are_orthogonal():
+    from oracle.wigner import wigner_d_halfstep
+    L = 40
+    H = wigner_d_halfstep(L, np.array([0.9, 2.5]))
+    for l in (1, 17, 39):
+        for k in range(2):
+            M = H[l, L - 1 - l:L + l, L - 1 - l:L + l, k]
+            assert np.abs(M @ M.T - np.eye(2 * l + 1)).max() <= 1e-13

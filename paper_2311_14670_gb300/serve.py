@@ -66,6 +66,29 @@ class _HostPool:
         self.free[(tuple(t.shape), t.dtype)].append(t)
 
 
+def next_admission(pending: dict, free_slots: int, running: int, in_flight: int, plan_bytes: int,
+                   budget: int, max_batch: int, footprint):
+    """The admission policy of the server loop (host logic only).
+
+    ``pending`` maps a kind (L, spin, direction) to its queue of waiting requests (oldest first;
+    each has an ``arrival`` time); ``footprint(kind, batch)`` gives the device bytes of a batch
+    (input + output + workspace).  Returns (kind, batch) to launch next, or None to wait: the kind
+    of the oldest waiting request, batched up to ``max_batch`` of its requests, when a stream slot
+    is free and the batch fits the budget next to everything in flight and the resident plans -- or
+    when nothing is running at all (a batch larger than the budget still runs, alone).
+    ``plan_bytes`` may be a callable, read after ``footprint`` (which may create the kind's plan).
+    """
+    if not pending or free_slots <= 0:
+        return None
+    kind = min(pending, key=lambda k: pending[k][0].arrival)
+    batch = min(len(pending[kind]), max_batch)
+    fp = footprint(kind, batch)
+    pb = plan_bytes() if callable(plan_bytes) else plan_bytes
+    if running and in_flight + fp + pb > budget:
+        return None
+    return kind, batch
+
+
 class Server:
     def __init__(self, device: int = 0, budget_bytes: int = 16 << 30, streams: int = 4,
                  max_batch: int = 4, precision: str = "fp64"):
@@ -136,16 +159,16 @@ class Server:
             running = still
             while pending:
                 free = [i for i, b in enumerate(self.busy) if not b]
-                if not free:
-                    break
-                kind = min(pending, key=lambda k: pending[k][0].arrival)   # oldest request first
-                q = pending[kind]
+                nxt = next_admission(pending, len(free), len(running), self.in_flight, lambda: self.plan_bytes,
+                                     self.budget, self.max_batch,
+                                     lambda k, b: self.footprint(self.plan(k[0], k[1]), b))
+                if nxt is None:
+                    break                                  # no free stream, or wait for memory
+                kind, batch = nxt
                 L, spin, direction = kind
                 p = self.plan(L, spin)
-                batch = min(len(q), self.max_batch)
                 fp = self.footprint(p, batch)
-                if running and self.in_flight + fp + self.plan_bytes > self.budget:
-                    break                                                # wait for memory
+                q = pending[kind]
                 reqs = [q.popleft() for _ in range(batch)]
                 if not q:
                     del pending[kind]

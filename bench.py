@@ -268,6 +268,9 @@ def run_ours(args, world, rank, local):
         barrier()
     ms = e0.elapsed_time(e1)
     err = None if grad_mode else float((y - x).abs().max() / x.abs().max())
+    # the three figures of the round-trip error: relative max (above), relative RMS, mean |diff|
+    err_rms = None if grad_mode else float(torch.linalg.vector_norm(y - x) / torch.linalg.vector_norm(x))
+    err_mean = None if grad_mode else float((y - x).abs().mean())
 
     # end to end through the public API: pinned host input -> device -> step -> host result, every
     # step.  The transforms run on the launch stream; the copies run on a second stream with two
@@ -409,6 +412,8 @@ def run_ours(args, world, rank, local):
                    "parallelism": f"dp{world} (independent batches, no data-path collective)",
                    "plan_ms": round(plan_ms, 1), "plan_device_bytes": plan.device_bytes()},
         "roundtrip_rel_max_err": err,
+        "roundtrip_rel_rms_err": err_rms,
+        "roundtrip_mean_abs_err": err_mean,
         "e2e": {"value": round(weak_scaling_throughput(transforms_per_step // world, world, ms_e2e, args.steps), 3),
                 "unit": "transforms/s",
                 "copies": "pinned host <-> device every step on a second stream, double-buffered, "

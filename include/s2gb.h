@@ -56,7 +56,7 @@ typedef struct s2gb_plan_s* s2gb_plan;
 enum {
   S2GB_OK = 0,
   S2GB_EINVAL = -1,        /* bad argument: null pointer, size out of range, in == out, ... */
-  S2GB_EUNSUPPORTED = -2,  /* valid request that this build does not implement */
+  S2GB_EUNSUPPORTED = -2,  /* valid request that this library does not implement */
   S2GB_ENOMEM = -3,        /* device allocation failed (plan creation only) */
   S2GB_ECUDA = -4,         /* a CUDA runtime call or kernel launch failed */
   S2GB_ECUFFT = -5,        /* a cuFFT call failed */

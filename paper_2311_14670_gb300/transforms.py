@@ -26,11 +26,17 @@ _SAMPLINGS = {"mw": nat.S2GB_MW, "mwss": nat.S2GB_MWSS, "dh": nat.S2GB_DH}
 def sampling_shape(L: int, sampling: str) -> tuple:
     """(rings R, phi samples P) of a sampling scheme (Sec. 4.2)."""
     return {"mw": (L, 2 * L - 1), "mwss": (L + 1, 2 * L), "dh": (2 * L, 2 * L - 1)}[sampling]
+
+
 _REAL_OF = {torch.complex128: torch.float64, torch.complex64: torch.float32}
 
 
 class Plan:
-    """A transform plan (``s2gb_plan_create``) plus a per-batch-size workspace cache."""
+    """A transform plan (``s2gb_plan_create``) plus a per-batch-size workspace cache.
+
+    Calls that take no ``ws`` share the cached workspace of their batch size, so they must not
+    overlap on the device: calls on one stream are fine, and concurrent streams pass a workspace
+    each (``ws=torch.empty(plan.workspace_bytes(batch), dtype=torch.uint8, device=...)``)."""
 
     def __init__(self, L: int, spin: int = 0, N: int = 0, precision: str = "fp64", max_batch: int = 1,
                  device: int | torch.device | None = None, sampling: str = "mw", real: bool = False,

@@ -7,6 +7,7 @@ torch extension machinery: the library has a plain C ABI (``include/s2gb.h``).
 from __future__ import annotations
 
 import os
+import platform
 import shutil
 import subprocess
 import sys
@@ -22,6 +23,22 @@ SOURCES = ["api.cu", "plan.cu", "theta_kernels.cu", "theta_kernels_f32.cu", "the
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I" + os.path.join(ROOT, "include")]
+
+
+STAMP = os.path.join(BUILD, "host")
+
+
+def _host_tag() -> str:
+    """The machine the objects are built for: objects of another host architecture are rebuilt."""
+    return platform.machine()
+
+
+def _stamp_matches(stamp: str = STAMP) -> bool:
+    try:
+        with open(stamp) as fh:
+            return fh.read().strip() == _host_tag()
+    except OSError:
+        return False
 
 
 def _nvcc() -> str:
@@ -44,6 +61,7 @@ def build(verbose: bool = False, force: bool = False, ptxas_verbose: bool = Fals
     """Compile (if needed) and return the path of libs2gb.so."""
     nvcc = _nvcc()
     os.makedirs(BUILD, exist_ok=True)
+    force = force or not _stamp_matches()
     jobs = []
     for s in SOURCES:
         src = os.path.join(CSRC, s)
@@ -72,6 +90,8 @@ def build(verbose: bool = False, force: bool = False, ptxas_verbose: bool = Fals
         if r.returncode:
             sys.stderr.write(r.stdout + r.stderr)
             raise RuntimeError("link failed: " + " ".join(cmd))
+        with open(STAMP, "w") as fh:
+            fh.write(_host_tag() + "\n")
     return LIB
 
 

@@ -80,3 +80,12 @@ def test_plan_flags_are_checked_before_any_device_work(libpath):
     assert lib.s2gb_plan_create_flags(ctypes.byref(h), 4096, 0, 0, 0, 0, 1, 0,
                                       nat.S2GB_PLAN_PRECOMPUTE) == nat.S2GB_EUNSUPPORTED
     assert h.value is None
+
+
+def test_build_rebuilds_objects_of_another_host_architecture(tmp_path, libpath):
+    from paper_2311_14670_gb300 import build
+    assert build._stamp_matches()                      # written by the build of this host
+    other = tmp_path / "host"
+    other.write_text("some-other-machine\n")
+    assert not build._stamp_matches(str(other))
+    assert not build._stamp_matches(str(tmp_path / "missing"))

@@ -1,6 +1,8 @@
 """Pins of the oracle's MWSS and DH samplings (Sec. 4.2) against closed forms: exactness of the
 quadrature weights, the grids through known spherical harmonics, round trips, agreement of the
 forward transforms across samplings, and the dense adjoint against the MW adjoints."""
+import os
+
 import numpy as np
 import pytest
 from numpy.polynomial import legendre
@@ -101,3 +103,55 @@ def test_wigner_n1_is_the_scaled_spin0_transform(sampling):
     f_w = OT.wigner_inverse_s(a[None], L, 1, sampling)[0]
     f_s = OT.inverse_s(a * ratio[:, None], L, 0, sampling)
     assert np.abs(f_w - f_s).max() <= 1e-14 * np.abs(f_s).max()
+
+
+GOLDEN_DIR = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _golden(name):
+    """The printed values of a golden file: key -> value, the key being every column but the last."""
+    out = {}
+    with open(os.path.join(GOLDEN_DIR, name)) as fh:
+        for line in fh:
+            line = line.split("#")[0].strip()
+            if line:
+                *key, v = line.split()
+                out[tuple(key)] = float(v)
+    return out
+
+
+def _valid(L, N):
+    return np.stack([OT.coeff_mask(L, n) for n in range(-(N - 1), N)])
+
+
+@pytest.mark.parametrize("sampling", ["mwss", "dh"])
+@pytest.mark.parametrize("L", [8, 16, 32])
+def test_round_trip_error_magnitude_matches_paper(sampling, L):
+    """The oracle's mean per-coefficient round-trip error on MWSS and DH is at the float64 level the
+    paper prints for its on-the-fly transforms (Table sh_error_results; the norm is ambiguous, so
+    within a factor 10)."""
+    paper = _golden("paper_roundtrip_errors_samplings.txt")[("sht_" + sampling, str(L))]
+    rng = np.random.default_rng(L)
+    errs = []
+    for _ in range(3):
+        a = rng.standard_normal((L, 2 * L - 1)) + 1j * rng.standard_normal((L, 2 * L - 1))
+        a = np.where(OT.coeff_mask(L, 0), a, 0)
+        d = OT.forward_s(OT.inverse_s(a, L, 0, sampling), L, 0, sampling) - a
+        errs.append(np.abs(d[OT.coeff_mask(L, 0)]).mean())
+    assert np.mean(errs) < 10 * paper
+
+
+@pytest.mark.parametrize("sampling", ["mw", "mwss"])
+@pytest.mark.parametrize("L", [8, 16])
+def test_wigner_round_trip_error_magnitude_matches_paper(sampling, L):
+    """The same for the Wigner transform with N = 5 on MW and MWSS (Table wig_error_results)."""
+    if sampling == "mw":
+        paper = _golden("paper_roundtrip_errors_mw.txt")[("W%d" % L,)]
+    else:
+        paper = _golden("paper_roundtrip_errors_samplings.txt")[("wigner_mwss", str(L))]
+    N = 5
+    rng = np.random.default_rng(L)
+    a = rng.standard_normal((2 * N - 1, L, 2 * L - 1)) + 1j * rng.standard_normal((2 * N - 1, L, 2 * L - 1))
+    a = np.where(_valid(L, N), a, 0)
+    d = OT.wigner_forward_s(OT.wigner_inverse_s(a, L, N, sampling), L, N, sampling) - a
+    assert np.abs(d[_valid(L, N)]).mean() < 10 * paper

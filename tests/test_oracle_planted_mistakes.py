@@ -1,0 +1,96 @@
+"""The oracle's pins catch plausible mistakes: each test plants one mistake in the oracle (on the
+CPU, by replacing one of its functions for the duration of the test) and checks that a pin of
+``test_oracle_transforms`` then fails.  A pin that still passed with the mistake in place would
+not be pinning that part of the oracle.
+
+Mistakes planted, with the pin that must catch them:
+  * the spin sign (-1)^s dropped from c_l                  -> brute force from the Jacobi form
+  * d^l_{n,m} used where d^l_{m,n} belongs (transposed)     -> brute force from the Jacobi form
+  * the phi-DFT exponent sign flipped (both directions)     -> closed-form Y_lm (a round trip would
+                                                               not notice)
+  * the torus-extension parity (-1)^{m+s} dropped           -> round trip
+  * uniform theta weights instead of the MW weights         -> round trip
+  * the DH-like grid (2t+1) pi/(2L) in place of MW's        -> closed-form Y_lm
+  * the gamma-DFT exponent sign flipped (Wigner)            -> inverse of a unit coefficient = D*
+  * the Wigner factor (2l+1)/(8 pi^2) replaced by c_l       -> inverse of a unit coefficient = D*
+"""
+import numpy as np
+import pytest
+
+import oracle.transforms as T
+import test_oracle_transforms as pins
+
+
+def _fails(check, *args):
+    with pytest.raises(AssertionError):
+        check(*args)
+
+
+def test_the_pins_pass_without_a_planted_mistake():
+    pins.test_inverse_brute_force_from_jacobi(4, 1)
+    pins.test_inverse_gives_closed_form_Ylm(2, 1)
+    pins.test_round_trip(17, 1)
+    pins.test_wigner_inverse_of_unit_is_conjugate_D()
+
+
+def test_dropped_spin_sign_in_c_l(monkeypatch):
+    monkeypatch.setattr(T, "ell_factor", lambda L, spin: np.sqrt((2 * np.arange(L) + 1) / (4 * np.pi)))
+    _fails(pins.test_inverse_brute_force_from_jacobi, 4, 1)
+
+
+def test_transposed_d_function(monkeypatch):
+    orig = T.wigner_d_table
+
+    def transposed(ells, n, thetas):
+        D = orig(ells, n, thetas)                       # [l, m, t], m centred on the middle column
+        w = D.shape[1]
+        m = np.arange(w) - (w - 1) // 2
+        return D * ((-1.0) ** ((m - n) % 2))[None, :, None]    # d^l_{n,m} = (-1)^{m-n} d^l_{m,n}
+
+    monkeypatch.setattr(T, "wigner_d_table", transposed)
+    _fails(pins.test_inverse_brute_force_from_jacobi, 4, 1)
+
+
+def test_flipped_phi_dft_sign(monkeypatch):
+    orig = T.phi_dft_matrix
+    monkeypatch.setattr(T, "phi_dft_matrix", lambda L, sign: orig(L, -sign))
+    pins.test_round_trip(8, 0)                          # the round trip alone cannot see it
+    _fails(pins.test_inverse_gives_closed_form_Ylm, 2, 1)
+
+
+def test_dropped_torus_extension_parity(monkeypatch):
+    def no_parity(F, L, n, orders=None):
+        G = np.zeros(F.shape[:-2] + (2 * L - 1, F.shape[-1]), dtype=np.complex128)
+        G[..., :L, :] = F
+        G[..., L:, :] = F[..., :L - 1, :][..., ::-1, :]
+        return G
+
+    monkeypatch.setattr(T, "_extend", no_parity)
+    _fails(pins.test_round_trip, 17, 1)
+
+
+def test_uniform_theta_weights(monkeypatch):
+    monkeypatch.setattr(T, "mw_theta_weights", lambda Lp: np.full(Lp, 2.0 / Lp))
+    _fails(pins.test_round_trip, 17, 1)
+
+
+def test_wrong_ring_positions(monkeypatch):
+    monkeypatch.setattr(T, "mw_thetas", lambda L, dtype=np.longdouble:
+                        ((2 * np.arange(L) + 1) * np.pi / (2 * L)).astype(dtype))
+    _fails(pins.test_inverse_gives_closed_form_Ylm, 2, 1)
+
+
+def test_flipped_gamma_dft_sign(monkeypatch):
+    orig = T._gamma_matrix
+    monkeypatch.setattr(T, "_gamma_matrix", lambda N, sign: orig(N, -sign))
+    _fails(pins.test_wigner_inverse_of_unit_is_conjugate_D)
+
+
+def test_sphere_factor_in_the_wigner_inverse(monkeypatch):
+    orig = T._theta_inverse
+
+    def sphere_scaled(flm, L, n, scale, thetas):
+        return orig(flm, L, n, (-1.0) ** n * np.sqrt((2 * np.arange(L) + 1) / (4 * np.pi)), thetas)
+
+    monkeypatch.setattr(T, "_theta_inverse", sphere_scaled)
+    _fails(pins.test_wigner_inverse_of_unit_is_conjugate_D)

@@ -1,6 +1,6 @@
 """The oracle's pins catch plausible mistakes: each test plants one mistake in the oracle (on the
-CPU, by replacing one of its functions for the duration of the test) and checks that a pin of
-``test_oracle_transforms`` then fails.  A pin that still passed with the mistake in place would
+CPU, by replacing one of its functions for the duration of the test) and checks that one of the
+oracle's pins then fails.  A pin that still passed with the mistake in place would
 not be pinning that part of the oracle.
 
 Mistakes planted, with the pin that must catch them:
@@ -13,12 +13,21 @@ Mistakes planted, with the pin that must catch them:
   * the DH-like grid (2t+1) pi/(2L) in place of MW's        -> closed-form Y_lm
   * the gamma-DFT exponent sign flipped (Wigner)            -> inverse of a unit coefficient = D*
   * the Wigner factor (2l+1)/(8 pi^2) replaced by c_l       -> inverse of a unit coefficient = D*
+  * ln((k+1)!) for ln(k!) in the seeds                      -> closed-form d^1, d^2
+  * the DH weight's sine series one term too long           -> exact integration of P_n, n < 2L
+  * the MWSS pole rings counted twice                       -> exact integration of cos^n
+The pins of the d-functions, the samplings and the transforms live in ``test_oracle_wigner``,
+``test_oracle_samplings`` and ``test_oracle_transforms``.
 """
 import numpy as np
 import pytest
 
+import oracle.sampling as S
 import oracle.transforms as T
+import oracle.wigner as W
+import test_oracle_samplings as spins
 import test_oracle_transforms as pins
+import test_oracle_wigner as dpins
 
 
 def _fails(check, *args):
@@ -94,3 +103,45 @@ def test_sphere_factor_in_the_wigner_inverse(monkeypatch):
 
     monkeypatch.setattr(T, "_theta_inverse", sphere_scaled)
     _fails(pins.test_wigner_inverse_of_unit_is_conjugate_D)
+
+
+# ---------------------------------------------------------------- d-functions and samplings
+
+
+def test_sampling_and_d_pins_pass_without_a_planted_mistake():
+    dpins.test_closed_forms_l1_l2(1.0)
+    spins.test_dh_weights_integrate_legendre_polynomials_exactly(8)
+    spins.test_mwss_weights_integrate_even_torus_functions(12)
+
+
+def test_log_factorials_off_by_one(monkeypatch):
+    """ln((k+1)!) in place of ln(k!) in the seeds of Eq. initial_values."""
+    orig = W._log_factorials
+    monkeypatch.setattr(W, "_log_factorials", lambda kmax: orig(kmax + 1)[1:])
+    _fails(dpins.test_closed_forms_l1_l2, 1.0)
+
+
+def test_dh_weight_sum_one_term_too_long(monkeypatch):
+    """The DH weight's sine series summed over k <= L instead of k < L."""
+    def long_sum(L):
+        th = S.dh_thetas(L)
+        k = np.arange(L + 1).astype(np.longdouble)
+        s = (np.sin(np.outer(th, 2 * k + 1)) / (2 * k + 1)).sum(axis=1)
+        return (np.longdouble(2) / L * np.sin(th) * s).astype(np.float64)
+
+    monkeypatch.setattr(spins, "dh_theta_weights", long_sum)
+    _fails(spins.test_dh_weights_integrate_legendre_polynomials_exactly, 8)
+
+
+def test_mwss_poles_counted_twice(monkeypatch):
+    """The MWSS pole rings folded with their own reflection (counted twice)."""
+    orig = S.mwss_theta_weights
+
+    def doubled(Lp):
+        q = orig(Lp).copy()
+        q[0] *= 2
+        q[-1] *= 2
+        return q
+
+    monkeypatch.setattr(spins, "mwss_theta_weights", doubled)
+    _fails(spins.test_mwss_weights_integrate_even_torus_functions, 12)

@@ -374,7 +374,9 @@ def run_ours(args, world, rank, local):
     if "theta_inverse" in kern and "theta_forward" in kern:
         th = kern["theta_inverse"]["ms"] + kern["theta_forward"]["ms"]
         stage_split = {"theta_kernels_ms": round(th, 3),
-                       "fft_and_glue_ms": round(max(0.0, ms / args.steps - th), 3)}
+                       "fft_and_glue_ms": round(max(0.0, ms / args.steps - th), 3),
+                       # this GPU's transforms per second if the step were the theta kernels alone
+                       "theta_stage_transforms_per_s": round(2 * B * (2 * N - 1 if N else 1) / (th * 1e-3), 3)}
     ms, ms_e2e = max_over_ranks([ms, ms_e2e], device=dev)
     # a gradient step is one inverse transform plus its adjoint: 2 transforms per signal, as a round trip
     transforms_per_step = 2 * B * world * (2 * N - 1 if N else 1)

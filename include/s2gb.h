@@ -91,8 +91,9 @@ enum {
  * recursion coefficient tables (Sec. 3.3 readings, O(L^2) per spin), the per-ring and per-order
  * log-space seed data (Eq. "initial_values") and the FFT weights; it creates cuFFT plans.
  * Returns S2GB_EINVAL for L < 1 or L > 8192, |spin| >= L (sphere), N < 0 or N > L, max_batch < 1,
- * an unknown sampling or precision; S2GB_EUNSUPPORTED for DH with L > 4096, and for S2GB_FP32
- * with L > 2048 or DH with L > 1024;
+ * an unknown sampling or precision; S2GB_EUNSUPPORTED for DH with L > 4096, for S2GB_FP32
+ * with L > 2048 or DH with L > 1024, and when max_batch * (2N-1 for Wigner plans, else 1) *
+ * max(R, 2L-1) exceeds 2^31 - 1 (the FFT stages' 32-bit batch counts);
  * S2GB_ENOMEM / S2GB_ECUDA / S2GB_ECUFFT on device failures.  On failure *out is set to NULL.  The
  * calling thread's current device is restored on return.
  */

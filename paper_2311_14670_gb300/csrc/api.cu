@@ -475,6 +475,14 @@ int plan_create_impl(s2gb_plan* out, int L, int spin, int N, int sampling, int p
   if (precompute && (precision != S2GB_FP64 || L > s2gb::kFwdChunk || sampling != S2GB_MW))
     return S2GB_EUNSUPPORTED;
   if (mrec && (precision != S2GB_FP64 || real || precompute)) return S2GB_EUNSUPPORTED;
+  {
+    // the cuFFT plans take 32-bit batch counts: max_batch * (2N-1) signals times the rows of the
+    // largest batched FFT (the rings of the phi DFT, or the order rows of the theta operator)
+    const long long nsig = (long long)max_batch * (N >= 1 ? 2LL * N - 1 : 1LL);
+    const long long rings_all = sampling == S2GB_DH ? 2LL * L : (sampling == S2GB_MWSS ? L + 1LL : (long long)L);
+    const long long order_rows = real ? (long long)L : 2LL * L - 1;
+    if (nsig * (rings_all > order_rows ? rings_all : order_rows) > 2147483647LL) return S2GB_EUNSUPPORTED;
+  }
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return S2GB_EINVAL;
   s2gb_plan h = new (std::nothrow) s2gb_plan_s;

@@ -51,6 +51,10 @@ def test_strerror_and_argument_rejection_without_gpu(libpath):
     assert lib.s2gb_plan_create(ctypes.byref(h), 8, 0, 0, 0, 9, 1, 0) == nat.S2GB_EINVAL   # precision
     assert lib.s2gb_plan_create(ctypes.byref(h), 8, 0, 0, 0, 0, 0, 0) == nat.S2GB_EINVAL   # max_batch
     assert lib.s2gb_plan_create(None, 8, 0, 0, 0, 0, 1, 0) == nat.S2GB_EINVAL
+    # max_batch x (2N-1) x rows beyond the 32-bit FFT batch counts: refused before any device work
+    assert lib.s2gb_plan_create(ctypes.byref(h), 1024, 0, 0, 0, 0, 1 << 21, 0) == nat.S2GB_EUNSUPPORTED
+    assert h.value is None
+    assert lib.s2gb_plan_create(ctypes.byref(h), 64, 0, 32, 2, 0, 1 << 19, 0) == nat.S2GB_EUNSUPPORTED
     # null plans
     assert lib.s2gb_workspace_bytes(None, 1) == 0
     assert lib.s2gb_forward(None, None, None, 1, None, 0, None) == nat.S2GB_EINVAL
@@ -71,7 +75,7 @@ def test_plan_flags_are_checked_before_any_device_work(libpath):
     lib = nat.lib()
     h = ctypes.c_void_p(1)
     # unknown flag bits, a real plan with spin or N, precompute in FP32 or above L = 2048
-    assert lib.s2gb_plan_create_flags(ctypes.byref(h), 8, 0, 0, 0, 0, 1, 0, 4) == nat.S2GB_EINVAL
+    assert lib.s2gb_plan_create_flags(ctypes.byref(h), 8, 0, 0, 0, 0, 1, 0, 8) == nat.S2GB_EINVAL
     assert h.value is None
     assert lib.s2gb_plan_create_flags(ctypes.byref(h), 8, 1, 0, 0, 0, 1, 0, nat.S2GB_PLAN_REAL) == nat.S2GB_EINVAL
     assert lib.s2gb_plan_create_flags(ctypes.byref(h), 8, 0, 2, 0, 0, 1, 0, nat.S2GB_PLAN_REAL) == nat.S2GB_EINVAL

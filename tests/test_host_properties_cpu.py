@@ -1,6 +1,7 @@
-"""Property tests (hypothesis) of the host logic that decides how work is split and admitted:
-the order ranges of a sharded transform, the column ownership used to assemble the shards, and
-the server's admission policy.  CPU only; skipped where hypothesis is not installed."""
+"""Property tests (hypothesis) at random parameters, CPU only (skipped where hypothesis is not
+installed): the host logic that decides how work is split and admitted -- the order ranges of a
+sharded transform, the column ownership used to assemble the shards, the server's admission
+policy -- and the oracle's d-functions against the Jacobi representation."""
 import collections
 from types import SimpleNamespace
 
@@ -79,3 +80,21 @@ def test_admission_policy(reqs, free, running, in_flight, plan_bytes, budget, ma
         assert got is None
     else:
         assert got == (oldest, batch)
+
+
+@settings(max_examples=150, deadline=None)
+@given(ell=st.integers(0, 60), data=st.data(),
+       beta=st.floats(1e-7, 3.14159265358979 - 1e-7, allow_nan=False))
+def test_oracle_d_function_matches_the_jacobi_form_anywhere(ell, data, beta):
+    """The oracle's d^l_{mn}(beta) (the paper's recursion over m, two-sided) against the Jacobi
+    representation in 40-digit arithmetic at random (l, m, n, beta)."""
+    import numpy as np
+
+    mpmath = pytest.importorskip("mpmath")
+    from oracle.wigner import wigner_d_jacobi, wigner_d_table
+
+    n = data.draw(st.integers(-ell, ell))
+    m = data.draw(st.integers(-ell, ell))
+    got = wigner_d_table([ell], n, np.array([beta], dtype=np.longdouble))[0, m + ell, 0]
+    ref = float(wigner_d_jacobi(ell, m, n, mpmath.mpf(beta), dps=40))
+    assert abs(got - ref) <= 1e-14

@@ -404,8 +404,6 @@ bool overlaps(const void* a, size_t abytes, const void* b, size_t bbytes) {
   return x < y + bbytes && y < x + abytes;
 }
 
-bool overlaps(const void* a, const void* b, size_t bytes) { return overlaps(a, bytes, b, bytes); }
-
 enum class Op { Forward, Inverse, AdjForward, AdjInverse, InversePhi };
 
 int run(s2gb_plan plan, Op op, const void* in, void* out, int batch, void* ws, size_t ws_bytes,

@@ -130,7 +130,12 @@ class Server:
             req.out = None
 
     def run(self, requests: list, keep_results: bool = True) -> dict:
-        """Serve ``requests`` in real time (arrival times relative to the call); returns statistics."""
+        """Serve ``requests`` in real time (arrival times relative to the call); returns statistics
+        (the latency figures are None for an empty stream)."""
+        if not requests:
+            return {"requests": 0, "wall_s": 0.0, "throughput_rps": 0.0, "p50_ms": None, "p99_ms": None,
+                    "mean_ms": None, "launches": self.launches, "peak_in_flight_bytes": self.peak_in_flight,
+                    "plan_bytes": self.plan_bytes, "budget_bytes": self.budget}
         arrivals = [(r.arrival, r.rid, r) for r in requests]
         heapq.heapify(arrivals)
         pending: dict = {}

@@ -84,9 +84,9 @@ GRAPH = {"l64s0b1graph"}
 SAMPLING = {"l1024s0b1dh": "dh", "l2048s0b1dh": "dh", "l1024s0b1mwss": "mwss", "l2048s0b1mwss": "mwss",
             "l1024s2b4dh": "dh"}
 METRIC = "transforms/sec"
-FP64_LANES_PER_SM_CLK = 2      # DFMA lanes per SM per clock on GB300 (measured 1.88-1.89 at load)
-FP32_LANES_PER_SM_CLK = 128    # FFMA lanes per SM per clock (measured 118.5 at load)
-NUM_SMS = 152
+# nominal FMA lanes per SM per clock (GB300), for the nominal peak printed beside the measured one
+FP64_LANES_PER_SM_CLK = 2
+FP32_LANES_PER_SM_CLK = 128
 
 
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "theta_traffic.json")
@@ -116,11 +116,63 @@ def profiled_traffic(workload: str, kernel: str):
     return rec.get("dram_bytes_per_launch", {}).get(kernel)
 
 
-def algorithmic_flops(L: int, n_list, R: int, batch: int, real: bool = False) -> float:
-    """Per launch of one theta kernel: elements (l, m, theta) x (5 + 4B) flops (FMA = 2); real
-    signals have the orders m >= 0 only, L (L + 1) / 2 pairs (l, m)."""
+def algorithmic_flops(L: int, n_list, R: int, batch: int, real: bool = False, paired: bool = False) -> float:
+    """Per launch of one theta kernel: every element (l, m, theta) costs 4B flops of contraction
+    (a real d times B complex values, FMA = 2) and every recursion chain 5 flops per step.  Real
+    signals have the orders m >= 0 only, L (L + 1) / 2 pairs (l, m).  Paired plans (spin-0 sphere
+    and Wigner: d^l_{-m,-n} = (-1)^{m-n} d^l_{m,n}) run one recursion for the columns (m, n) and
+    (-m, -n), so the recursion is counted once per pair: (P + L00) / 2 chains per ring, L00 = L
+    self-paired (l, 0, 0) elements when n = 0 is in the plan."""
     pairs = L * (L + 1) // 2 if real else sum(L * L - n * n for n in n_list)
-    return float(pairs * R) * (5 + 4 * batch)
+    chains = (pairs + (L if 0 in n_list else 0)) // 2 if paired else pairs
+    return float(R) * (5.0 * chains + 4.0 * batch * pairs)
+
+
+def measured_fma_peak(precision: str, dev) -> dict:
+    """The FMA pipe's throughput on this GPU, measured with the library's FMA-chain kernel
+    (s2gb_fma_chain: independent chains, 4 CTAs of 256 threads per SM): best of three launches of
+    about 20 ms, CUDA events on the launching stream."""
+    import torch
+
+    from paper_2311_14670_gb300 import _native as nat
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    blocks, threads = 4 * sms, 256
+    f64 = precision == "fp64"
+    iters = 10_000 if f64 else 400_000
+    out = torch.empty(blocks * threads, dtype=torch.float64 if f64 else torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    prec = nat.S2GB_FP64 if f64 else nat.S2GB_FP32
+    flops = 2.0 * blocks * threads * nat.fma_chain_lanes() * iters
+    nat.fma_chain(prec, blocks, threads, iters, out, stream.cuda_stream)
+    best = None
+    for _ in range(3):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        nat.fma_chain(prec, blocks, threads, iters, out, stream.cuda_stream)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = a.elapsed_time(b)
+        best = ms if best is None else min(best, ms)
+    return {"tflops": flops / (best * 1e-3) / 1e12, "ms": best, "sms": sms,
+            "how": f"s2gb_fma_chain: {blocks} CTAs x {threads} threads x {nat.fma_chain_lanes()} independent "
+                   f"{precision.upper()} FMA chains x {iters} steps, best of 3 launches (CUDA events)"}
+
+
+def workload_config(workload: str, world: int) -> dict:
+    """The `config` of a bench line: the same dict for the GPU arm and the oracle (reference) arm."""
+    L, spin, N, B, ellp, desc = WORKLOADS[workload]
+    nN = 2 * N - 1 if N else 1
+    cols = L if workload in REAL else 2 * L - 1
+    es = 8 if PRECISION.get(workload, "fp64") == "fp32" else 16
+    coef_mb = B * nN * L * cols * es / 1e6
+    l2 = (f"inputs larger than L2: {coef_mb:.0f} MB of coefficients and as many of samples per step "
+          "(no flush between steps)" if coef_mb > 129 else
+          f"working set fits in L2 ({coef_mb:.2f} MB of coefficients per step; latency-bound size, not flushed)")
+    return {"workload": workload, "description": desc, "L": L, "spin": spin, "N": N,
+            "sampling": SAMPLING.get(workload, "mw"), "batch_per_gpu": B, "transforms_per_step": 2 * B * world * nN,
+            "step": ("loss forward (inverse) + backward (adjoint inverse) of the batch" if workload in GRAD
+                     else "inverse + forward of every signal in the batch"),
+            "l2": l2, "parallelism": f"dp{world} (independent batches, no data-path collective)"}
 
 
 class ClockSampler:
@@ -365,7 +417,7 @@ def run_ours(args, world, rank, local):
             b.record(stream)
             torch.cuda.synchronize(dev)
             kms = a.elapsed_time(b) / reps
-            flops = algorithmic_flops(L, n_list, R, B, real)
+            flops = algorithmic_flops(L, n_list, R, B, real, paired=plan.paired)
             kern[name] = {"ms": kms, "flops": flops, "tflops": flops / (kms * 1e-3) / 1e12}
 
     # the step split into the two theta kernels and everything else (phi / theta-direction FFTs on
@@ -388,7 +440,9 @@ def run_ours(args, world, rank, local):
     ck = clocks.summary()
     sm_max = ck["sm_max_mhz"] or 2070.0
     lanes = FP64_LANES_PER_SM_CLK if precision == "fp64" else FP32_LANES_PER_SM_CLK
-    peak = NUM_SMS * lanes * 2 * sm_max * 1e6 / 1e12    # TFLOP/s
+    meas = measured_fma_peak(precision, dev)
+    nominal = meas["sms"] * lanes * 2 * sm_max * 1e6 / 1e12    # TFLOP/s
+    peak = meas["tflops"]
     roof = None
     if kern:
         dom = max(kern, key=lambda k: kern[k]["ms"])
@@ -396,7 +450,10 @@ def run_ours(args, world, rank, local):
         roof = {"bound": "alu", "kernel": dom, "achieved": round(ach, 4), "peak": round(peak, 4),
                 "unit": "TFLOP/s", "frac": round(ach / peak, 4),
                 "traffic": profiled_traffic(args.workload, dom) if precision == "fp64" else None,
-                "peak_basis": f"{precision.upper()} FMA pipe: {NUM_SMS} SMs x {lanes} lanes x 2 flop x {sm_max:.0f} MHz"}
+                "peak_basis": f"{precision.upper()} FMA pipe, measured on this GPU: {meas['how']}",
+                "peak_nominal": round(nominal, 4),
+                "peak_nominal_basis": f"{meas['sms']} SMs x {lanes} lanes x 2 flop x {sm_max:.0f} MHz",
+                "frac_of_nominal": round(ach / nominal, 4)}
     value = weak_scaling_throughput(transforms_per_step // world, world, ms, args.steps)
     in_bytes = x.numel() * x.element_size()
     out = {
@@ -405,14 +462,9 @@ def run_ours(args, world, rank, local):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if precision == "fp64" else "f32 (f64 starting values)",
         "data": "synthetic (seeded complex Gaussian coefficients)",
-        "config": {"workload": args.workload, "description": desc, "L": L, "spin": spin, "N": N,
-                   "sampling": sampling, "batch_per_gpu": B, "transforms_per_step": transforms_per_step,
-                   "step": ("loss forward (inverse) + backward (adjoint inverse) of the batch" if grad_mode
-                            else "inverse + forward of every signal in the batch"),
-                   "l2": "working set > L2 (coefficients %.0f MB, workspace %.0f MB per step)"
-                         % (in_bytes / 1e6, ws.numel() / 1e6),
-                   "parallelism": f"dp{world} (independent batches, no data-path collective)",
-                   "plan_ms": round(plan_ms, 1), "plan_device_bytes": plan.device_bytes()},
+        "config": workload_config(args.workload, world),
+        "plan": {"create_ms": round(plan_ms, 1), "device_bytes": plan.device_bytes(),
+                 "workspace_bytes": ws.numel()},
         "roundtrip_rel_max_err": err,
         "roundtrip_rel_rms_err": err_rms,
         "roundtrip_mean_abs_err": err_mean,
@@ -429,11 +481,67 @@ def run_ours(args, world, rank, local):
         "roofline": roof,
         "clocks": {k: ck[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
     }
+    if args.workload == "l1024s2b4" and not args.no_l2048 and world == 1 and precision == "fp64":
+        out["l2048"] = l2048_records(dev, peak)
+        out["l2048"]["peak_tflops_measured"] = round(peak, 4)
     if not args.no_cpu_baseline and world == 1 and not grad_mode:
         out["cpu_baseline"] = cpu_baseline_parallel(args.workload, sampling, args.cpu_rings, args.cpu_procs)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+    return out
+
+
+def l2048_records(dev, peak_tflops: float, steps: int = 5, warmup: int = 3) -> dict:
+    """The L = 2048 round trips (MW, FP64, batch 1) beside the default line: spin 2 (unpaired
+    theta kernels) and spin 0 (paired).  Per configuration: the theta kernels' CUDA-event times and
+    their fraction of the measured FP64 peak, and the round trip's ms / transforms per second."""
+    import torch
+
+    from paper_2311_14670_gb300 import Plan, synth
+    out = {}
+    stream = torch.cuda.current_stream(dev)
+    for spin in (2, 0):
+        L = 2048
+        plan = Plan(L, spin=spin, max_batch=1, device=dev.index)
+        x = torch.from_numpy(synth.flm_gaussian(L, spin, 1, seed=2048 + spin)).to(dev)
+        f = torch.empty(plan.shape(1), dtype=plan.signal_dtype, device=dev)
+        y = torch.empty_like(x)
+        ws = plan.workspace(1)
+        g = torch.from_numpy(synth.signal_gaussian((1, 2 * L - 1, L), seed=77)).to(dev)
+        ft = torch.empty(plan.spectra_shape(1), dtype=plan.dtype, device=dev)
+        fl = torch.empty(plan.coef_shape(1), dtype=plan.dtype, device=dev)
+
+        def timed(fn, reps):
+            for _ in range(warmup):
+                fn()
+            torch.cuda.synchronize(dev)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(reps):
+                fn()
+            b.record(stream)
+            torch.cuda.synchronize(dev)
+            return a.elapsed_time(b) / reps
+
+        def rt():
+            plan.inverse(x, out=f, ws=ws)
+            plan.forward(f, out=y, ws=ws)
+
+        ms = timed(rt, steps)
+        err = float((y - x).abs().max() / x.abs().max())
+        flops = algorithmic_flops(L, [-spin], L, 1, paired=plan.paired)
+        ti = timed(lambda: plan.inverse_theta(x, out=ft), steps)
+        tf = timed(lambda: plan.forward_theta(g, out=fl), steps)
+        out[f"s{spin}b1"] = {
+            "roundtrip_ms": round(ms, 3), "transforms_per_s": round(2 / (ms * 1e-3), 3),
+            "theta_inverse_ms": round(ti, 3), "theta_forward_ms": round(tf, 3),
+            "theta_flops_per_launch": flops, "paired": plan.paired,
+            "frac_theta_inverse": round(flops / (ti * 1e-3) / 1e12 / peak_tflops, 4),
+            "frac_theta_forward": round(flops / (tf * 1e-3) / 1e12 / peak_tflops, 4),
+            "roundtrip_rel_max_err": err}
+        del plan, ws
+        torch.cuda.empty_cache()
     return out
 
 
@@ -473,7 +581,18 @@ def run_serve(args, world, rank, local):
     return res
 
 
-def cpu_baseline(workload: str, rings: int = 8) -> dict:
+_SETUP_CACHE = {}
+
+
+def _cached(key, fn):
+    """Inputs and oracle matrices of a bounded sample, built once per process (a pool worker times
+    several samples of the same workload; only the timed stages count)."""
+    if key not in _SETUP_CACHE:
+        _SETUP_CACHE[key] = fn()
+    return _SETUP_CACHE[key]
+
+
+def cpu_baseline(workload: str, rings: int = 4) -> dict:
     """The oracle (plain numpy, single thread) on a bounded sample of the workload, scaled to
     transforms/s.  The oracle's stages are timed on `rings`-sized slices and scaled by the size
     they are linear in: the inverse (d-table + synthesis) per ring; the forward's phi-DFT, torus
@@ -486,9 +605,9 @@ def cpu_baseline(workload: str, rings: int = 8) -> dict:
     T = 2 * L - 1
     n = 0 if N else -spin
     nn = 2 * N - 1 if N else 1
-    coef = synth.flm_gaussian(L, -n, B, seed=1, ell_power=ellp)
-    f = synth.signal_gaussian((B, L, T), seed=2)
-    k = max(4, min(L, rings))
+    coef = _cached(("coef", workload), lambda: synth.flm_gaussian(L, -n, B, seed=1, ell_power=ellp))
+    f = _cached(("f", workload), lambda: synth.signal_gaussian((B, L, T), seed=2))
+    k = max(2, min(L, rings))
     k2 = k // 2
 
     def fit(fn, full):
@@ -511,13 +630,13 @@ def cpu_baseline(workload: str, rings: int = 8) -> dict:
         sel = np.linspace(0, L - 1, j).astype(int)
         OT._theta_inverse(coef, L, n, scale, thetas[sel]) @ OT.phi_dft_matrix(L, +1).T
 
-    cmat, up = OT._upsample_matrices(L)
+    cmat, up = _cached(("up", L), lambda: OT._upsample_matrices(L))
 
     def fft(j):                                                # forward DFT/upsampling: per order
         sel = np.linspace(-(L - 1), L - 1, j).astype(int)
         up @ (cmat @ OT._extend(OT._phi_forward(f, L, sel), L, n, sel))
 
-    Gu = synth.signal_gaussian((B, 2 * L, T), seed=3)           # stand-in of the same shape
+    Gu = _cached(("Gu", workload), lambda: synth.signal_gaussian((B, 2 * L, T), seed=3))   # same shape
 
     def quad(j):                                               # forward quadrature: per degree
         OT._theta_forward_upsampled(Gu, L, n, scale, np.linspace(abs(n), L - 1, j).astype(int))
@@ -541,7 +660,7 @@ def cpu_baseline(workload: str, rings: int = 8) -> dict:
             "seconds_full_round_trip_est": round(total, 1)}
 
 
-def cpu_baseline_sampled(workload: str, sampling: str, rings: int = 8) -> dict:
+def cpu_baseline_sampled(workload: str, sampling: str, rings: int = 4) -> dict:
     """cpu_baseline for the MWSS and DH workloads (spin-s sphere transforms): the oracle's inverse
     timed per ring, its forward phi DFT (and, on MWSS, theta upsampling) per order and its
     quadrature per degree, each on two slice sizes and extrapolated as overhead + linear cost."""
@@ -551,9 +670,9 @@ def cpu_baseline_sampled(workload: str, sampling: str, rings: int = 8) -> dict:
     L, spin, N, B, ellp, _ = WORKLOADS[workload]
     R, P = OT.sampling_shape(L, sampling)
     T = 2 * L - 1
-    coef = synth.flm_gaussian(L, spin, B, seed=1, ell_power=ellp)
-    f = synth.signal_gaussian((B, R, P), seed=2)
-    k = max(4, min(L, rings))
+    coef = _cached(("coef", workload), lambda: synth.flm_gaussian(L, spin, B, seed=1, ell_power=ellp))
+    f = _cached(("f", workload), lambda: synth.signal_gaussian((B, R, P), seed=2))
+    k = max(2, min(L, rings))
     k2 = k // 2
 
     def fit(fn, full):
@@ -599,14 +718,14 @@ def cpu_baseline_sampled(workload: str, sampling: str, rings: int = 8) -> dict:
             "seconds_full_round_trip_est": round(total, 1)}
 
 
-def _baseline_worker(workload: str, sampling: str, rings: int, queue) -> None:
-    """One single-threaded oracle process of cpu_baseline_parallel (spawned: no CUDA state)."""
+def _baseline_task(args) -> dict:
+    """One single-threaded oracle sample in a pool worker (spawned: no CUDA state)."""
+    workload, sampling, rings = args
     try:
-        r = (cpu_baseline_sampled(workload, sampling, rings=rings) if sampling != "mw"
-             else cpu_baseline(workload, rings=rings))
-        queue.put(r)
+        return (cpu_baseline_sampled(workload, sampling, rings=rings) if sampling != "mw"
+                else cpu_baseline(workload, rings=rings))
     except Exception as exc:   # reported to the parent, which raises
-        queue.put({"error": repr(exc)})
+        return {"error": repr(exc)}
 
 
 def host_cores() -> int:
@@ -616,71 +735,80 @@ def host_cores() -> int:
         return os.cpu_count() or 1
 
 
+class OraclePool:
+    """`procs` spawned single-threaded oracle processes, kept for several samples.  One sample: every
+    process times the same bounded slice of the workload concurrently and extrapolates its own full
+    round trip under the others' load; the throughputs add up (independent transforms, one per
+    core).  The GPU arm's cpu_baseline is one such sample; each step of the reference arm is one."""
+
+    def __init__(self, procs: int):
+        import multiprocessing as mp
+        self.procs = max(1, procs)
+        self.pool = mp.get_context("spawn").Pool(self.procs) if self.procs > 1 else None
+
+    def sample(self, workload: str, sampling: str, rings: int) -> dict:
+        task = (workload, sampling, rings)
+        res = self.pool.map(_baseline_task, [task] * self.procs, chunksize=1) if self.pool else [_baseline_task(task)]
+        bad = [r["error"] for r in res if "error" in r]
+        if bad:
+            raise RuntimeError(f"oracle baseline process failed: {bad[0]}")
+        total = sum(r["value"] for r in res)
+        return {"value": round(total, 6), "unit": res[0]["unit"], "cores": self.procs, "kind": "oracle",
+                "sample": f"{self.procs} concurrent single-threaded oracle processes, one per host core; each: "
+                          + res[0]["sample"],
+                "per_process_value": round(total / self.procs, 6),
+                "seconds_measured": max(r["seconds_measured"] for r in res),
+                "seconds_full_round_trip_est": round(statistics.median(r["seconds_full_round_trip_est"] for r in res), 1)}
+
+    def close(self):
+        if self.pool:
+            self.pool.close()
+            self.pool.join()
+
+
 def cpu_baseline_parallel(workload: str, sampling: str, rings: int, procs: int) -> dict:
-    """The oracle on all host cores: `procs` single-threaded oracle processes (spawned) time the
-    same bounded sample concurrently; each extrapolates its own full round trip under the others'
-    load, and the throughputs add up (independent transforms, one per core).  `cores` is the number
-    of processes."""
-    procs = max(1, procs)
-    if procs == 1:
-        r = (cpu_baseline_sampled(workload, sampling, rings=rings) if sampling != "mw"
-             else cpu_baseline(workload, rings=rings))
-        return r
-    import multiprocessing as mp
-    ctx = mp.get_context("spawn")
-    queue = ctx.Queue()
-    workers = [ctx.Process(target=_baseline_worker, args=(workload, sampling, rings, queue)) for _ in range(procs)]
-    for w in workers:
-        w.start()
-    res = [queue.get(timeout=900) for _ in workers]
-    for w in workers:
-        w.join(timeout=60)
-    bad = [r["error"] for r in res if "error" in r]
-    if bad:
-        raise RuntimeError(f"oracle baseline process failed: {bad[0]}")
-    total = sum(r["value"] for r in res)
-    return {"value": round(total, 6), "unit": res[0]["unit"], "cores": procs, "kind": "oracle",
-            "sample": f"{procs} concurrent single-threaded oracle processes, one per host core; each: "
-                      + res[0]["sample"],
-            "per_process_value": round(total / procs, 6),
-            "seconds_measured": max(r["seconds_measured"] for r in res),
-            "seconds_full_round_trip_est": round(statistics.median(r["seconds_full_round_trip_est"] for r in res), 1)}
+    """cpu_baseline on all host cores: one OraclePool sample."""
+    pool = OraclePool(procs)
+    try:
+        return pool.sample(workload, sampling, rings)
+    finally:
+        pool.close()
 
 
 def run_reference(args, world, rank):
+    """The oracle arm: each step is one OraclePool sample of the workload (the same procedure as the
+    GPU arm's cpu_baseline).  `value` is the median over the timed steps of the extrapolated
+    transforms/s; `ms_per_step` is the measured wall time of a step (a bounded sample, not a whole
+    round trip), and the extrapolated time of a whole step is reported beside it."""
     if rank != 0:
         return None
     L, spin, N, B, ellp, desc = WORKLOADS[args.workload]
-    k = 4
-    samples = []
     sampling = SAMPLING.get(args.workload, "mw")
-
-    def sample():
-        return cpu_baseline_parallel(args.workload, sampling, k, args.cpu_procs)
-
-    for _ in range(args.warmup):
-        sample()
-    t0 = time.perf_counter()
-    last = None
-    for _ in range(args.steps):
-        last = sample()
-        samples.append(last["value"])
-    wall = time.perf_counter() - t0
+    pool = OraclePool(args.cpu_procs)
+    try:
+        for _ in range(args.warmup):
+            pool.sample(args.workload, sampling, args.cpu_rings)
+        samples, walls = [], []
+        last = None
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            last = pool.sample(args.workload, sampling, args.cpu_rings)
+            walls.append(time.perf_counter() - t0)
+            samples.append(last["value"])
+    finally:
+        pool.close()
     value = statistics.median(samples)
-    per = 2 * B * (2 * N - 1 if N else 1)
-    cb = {"value": value, "unit": "transforms/s", "cores": last["cores"] if last else args.cpu_procs,
-          "kind": "oracle",
-          "sample": (f"each step: {args.cpu_procs} concurrent single-threaded oracle processes (one per host "
-                     f"core), each timing the inverse on {k} of {L} rings and the forward on {k} of {L} "
-                     f"degrees, scaled linearly to full transforms; throughputs added")}
+    cfg = workload_config(args.workload, world)
+    per = cfg["transforms_per_step"]
+    cb = {"value": value, "unit": "transforms/s", "cores": pool.procs, "kind": "oracle",
+          "sample": "each step: " + last["sample"]}
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": "transforms/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(per / value * 1e3, 3),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * statistics.mean(walls), 3),
+            "ms_per_step_basis": "measured wall time of one step (one bounded oracle sample on all host cores)",
+            "ms_per_full_step_extrapolated": round(per / value * 1e3, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded complex Gaussian coefficients)",
-            "config": {"workload": args.workload, "description": desc, "L": L, "spin": spin, "N": N,
-                       "batch_per_gpu": B, "transforms_per_step": per,
-                       "parallelism": f"host cores, {args.cpu_procs} oracle processes"},
-            "cpu_baseline": cb, "wall_s": round(wall, 2),
+            "config": cfg, "cpu_baseline": cb, "wall_s": round(sum(walls), 3),
             "e2e": {"value": value, "unit": "transforms/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -694,7 +822,10 @@ def main():
     ap.add_argument("--budget-gib", type=int, default=16, help="HBM admission budget (serve_* workloads)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-rings", type=int, default=8, help="rings/degrees of the oracle sample")
+    ap.add_argument("--no-l2048", action="store_true",
+                    help="skip the L = 2048 records beside the default workload's line")
+    ap.add_argument("--cpu-rings", type=int, default=4,
+                    help="rings / orders / degrees of one oracle sample (timed at half and at this size)")
     ap.add_argument("--cpu-procs", type=int, default=0,
                     help="oracle processes for the CPU baseline (0: one per host core)")
     args = ap.parse_args()

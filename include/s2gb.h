@@ -256,6 +256,19 @@ int s2gb_inverse_noalloc(s2gb_plan plan, const void* flm, void* f, int batch, vo
  */
 unsigned long long s2gb_kernels_launched(void);
 
+/*
+ * Measurement helper (the paper has no counterpart): enqueues one launch of `blocks` x `threads`
+ * threads (threads a multiple of 32, at most 256) in which every thread runs
+ * s2gb_fma_chain_lanes() independent fused multiply-add chains of `iters` steps in float64
+ * (precision S2GB_FP64) or float32 (S2GB_FP32), and writes one value per thread to `out` (device,
+ * blocks * threads elements of that type).  The launch performs
+ * blocks * threads * s2gb_fma_chain_lanes() * iters FMAs; timed with CUDA events it measures the
+ * FMA pipe's throughput, the denominator of the theta kernels' roofline fraction.  Returns
+ * S2GB_EINVAL on bad sizes.
+ */
+int s2gb_fma_chain(int precision, int blocks, int threads, long long iters, void* out, void* stream);
+int s2gb_fma_chain_lanes(void);
+
 /* Static description of a return code (never NULL). */
 const char* s2gb_strerror(int code);
 

@@ -78,6 +78,10 @@ def lib() -> ctypes.CDLL:
         L.s2gb_inverse_phi.restype = i
         L.s2gb_forward_mrange.argtypes = [vp, vp, vp, i, i, i, vp, sz, vp]
         L.s2gb_forward_mrange.restype = i
+        L.s2gb_fma_chain.argtypes = [i, i, i, ctypes.c_longlong, vp, vp]
+        L.s2gb_fma_chain.restype = i
+        L.s2gb_fma_chain_lanes.argtypes = []
+        L.s2gb_fma_chain_lanes.restype = i
         L.s2gb_strerror.argtypes = [i]
         L.s2gb_strerror.restype = ctypes.c_char_p
         _lib = L
@@ -195,3 +199,14 @@ def inverse_noalloc(plan, flm, f, batch, stream):
     _check(lib().s2gb_inverse_noalloc(ctypes.c_void_p(plan), ctypes.c_void_p(_ptr(flm)),
                                       ctypes.c_void_p(_ptr(f)), batch, ctypes.c_void_p(stream)),
            "s2gb_inverse_noalloc")
+
+
+def fma_chain(precision, blocks, threads, iters, out, stream):
+    """s2gb_fma_chain: one launch of independent FMA chains (the FMA pipe's measured peak)."""
+    _check(lib().s2gb_fma_chain(precision, blocks, threads, iters, ctypes.c_void_p(_ptr(out)),
+                                ctypes.c_void_p(stream)), "s2gb_fma_chain")
+
+
+def fma_chain_lanes():
+    """Independent FMA chains per thread of s2gb_fma_chain."""
+    return lib().s2gb_fma_chain_lanes()

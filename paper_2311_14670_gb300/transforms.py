@@ -72,6 +72,12 @@ class Plan:
     def wigner(self) -> bool:
         return self.N >= 1
 
+    @property
+    def paired(self) -> bool:
+        """The theta kernels pair the columns (m, n) and (-m, -n) (one recursion for both, by
+        d^l_{-m,-n} = (-1)^{m-n} d^l_{m,n}): complex spin-0 sphere plans and Wigner plans."""
+        return not self.real and (self.wigner or self.spin == 0)
+
     def shape(self, batch: int) -> tuple:
         """Shape of f."""
         return (batch, 2 * self.N - 1, self.R, self.P) if self.wigner else (batch, self.R, self.P)

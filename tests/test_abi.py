@@ -93,3 +93,14 @@ def test_build_rebuilds_objects_of_another_host_architecture(tmp_path, libpath):
     other.write_text("some-other-machine\n")
     assert not build._stamp_matches(str(other))
     assert not build._stamp_matches(str(tmp_path / "missing"))
+
+
+def test_fma_chain_rejects_bad_sizes_without_gpu(libpath):
+    """The peak-measurement helper checks its launch shape before touching a device."""
+    from paper_2311_14670_gb300 import _native as nat
+    lib = nat.lib()
+    buf = ctypes.c_void_p(16)
+    assert lib.s2gb_fma_chain_lanes() >= 1
+    for prec, blocks, threads, iters, out in [(0, 0, 256, 10, buf), (0, 4, 300, 10, buf), (0, 4, 48, 10, buf),
+                                              (1, 4, 256, 0, buf), (0, 4, 256, 10, None), (7, 4, 256, 10, buf)]:
+        assert lib.s2gb_fma_chain(prec, blocks, threads, iters, out, None) == nat.S2GB_EINVAL

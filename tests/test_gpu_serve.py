@@ -1,5 +1,5 @@
-"""The continuous-batching server: results equal the same transforms run alone, admission respects
-the memory budget, and every request completes."""
+"""The continuous-batching server: results equal the same transforms run alone (bit for bit),
+admission respects the memory budget, and every request completes."""
 import numpy as np
 import pytest
 
@@ -30,7 +30,8 @@ def test_results_alone_equal_results_in_the_mix():
         p = srv.plan(r.L, r.spin)
         x = r.data.cuda().unsqueeze(0)
         alone = (p.inverse(x) if r.direction == "inverse" else p.forward(x))[0].cpu().numpy()
-        assert rel_max(r.out.numpy(), alone) <= TOL64
+        # every kernel sums each signal in the same order whatever it is batched with: bit for bit
+        assert np.array_equal(r.out.numpy(), alone)
     # and against the oracle for a few of them
     for r in reqs[:6]:
         a = r.data.numpy()

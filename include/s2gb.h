@@ -143,10 +143,20 @@ int s2gb_plan_create_real(s2gb_plan* out, int L, int sampling, int precision, in
  * output index of the contraction, the kernels sum across threads and write per-block partial
  * sums into the workspace (s2gb_workspace_bytes includes them); the theta-only entry points and
  * s2gb_inverse_noalloc return S2GB_EUNSUPPORTED for these plans.
+ *
+ * S2GB_PLAN_FMA_CONTRACTION: float64 plans whose d-functions are generated on the fly (neither
+ * PRECOMPUTE nor MRECURSION) run the theta contraction -- the sum over the degree l of the inverse
+ * stage (Eq. disc_ish_expanded) -- on the tensor cores by default: the float64 recursion values
+ * and the coefficients are split into seven exact base-256 digits each, whose products the
+ * tensor cores sum exactly in float32 (the Ozaki splitting scheme); the digit sums are combined
+ * in 64-bit integers and float64.  The result agrees with a float64 sum to a few units of the
+ * last place.  This flag keeps the contraction on the float64 FMA pipe instead (the kernels of
+ * the recursion alone; for comparison).  Ignored by other plans.
  */
 #define S2GB_PLAN_REAL 1u
 #define S2GB_PLAN_PRECOMPUTE 2u
 #define S2GB_PLAN_MRECURSION 4u
+#define S2GB_PLAN_FMA_CONTRACTION 8u
 int s2gb_plan_create_flags(s2gb_plan* out, int L, int spin, int N, int sampling, int precision,
                            int max_batch, int device, unsigned flags);
 
@@ -268,6 +278,15 @@ unsigned long long s2gb_kernels_launched(void);
  */
 int s2gb_fma_chain(int precision, int blocks, int threads, long long iters, void* out, void* stream);
 int s2gb_fma_chain_lanes(void);
+
+/*
+ * Status of the tensor-core theta kernels on `device` (the paper has no counterpart): 0 when every
+ * such kernel finished normally; otherwise the code recorded by the first kernel whose bounded wait
+ * for tensor-core completion ran out (1) -- that kernel left its output unwritten.  Synchronous
+ * (reads a device variable); `clear` != 0 resets the status to 0.  Negative return: S2GB_EINVAL
+ * (no such device) or S2GB_ECUDA.
+ */
+int s2gb_device_status(int device, int clear);
 
 /* Static description of a return code (never NULL). */
 const char* s2gb_strerror(int code);

@@ -29,6 +29,7 @@ S2GB_FP32 = 1
 S2GB_PLAN_REAL = 1
 S2GB_PLAN_PRECOMPUTE = 2
 S2GB_PLAN_MRECURSION = 4
+S2GB_PLAN_FMA_CONTRACTION = 8
 
 _lib = None
 
@@ -78,6 +79,8 @@ def lib() -> ctypes.CDLL:
         L.s2gb_inverse_phi.restype = i
         L.s2gb_forward_mrange.argtypes = [vp, vp, vp, i, i, i, vp, sz, vp]
         L.s2gb_forward_mrange.restype = i
+        L.s2gb_device_status.argtypes = [i, i]
+        L.s2gb_device_status.restype = i
         L.s2gb_fma_chain.argtypes = [i, i, i, ctypes.c_longlong, vp, vp]
         L.s2gb_fma_chain.restype = i
         L.s2gb_fma_chain_lanes.argtypes = []
@@ -210,3 +213,11 @@ def fma_chain(precision, blocks, threads, iters, out, stream):
 def fma_chain_lanes():
     """Independent FMA chains per thread of s2gb_fma_chain."""
     return lib().s2gb_fma_chain_lanes()
+
+
+def device_status(device, clear=True):
+    """s2gb_device_status: 0, or the code of a tensor-core kernel whose bounded wait ran out."""
+    rc = lib().s2gb_device_status(int(device), 1 if clear else 0)
+    if rc < 0:
+        raise S2GBError(rc, "s2gb_device_status")
+    return rc

@@ -19,7 +19,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libs2gb.so")
 SOURCES = ["api.cu", "plan.cu", "theta_kernels.cu", "theta_kernels_f32.cu", "theta_precompute.cu", "glue.cu",
-           "poles.cu", "theta_mrec.cu", "peak.cu"]
+           "poles.cu", "theta_mrec.cu", "peak.cu", "theta_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I" + os.path.join(ROOT, "include")]

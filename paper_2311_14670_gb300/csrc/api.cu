@@ -456,7 +456,8 @@ extern "C" {
 
 namespace {
 int plan_create_impl(s2gb_plan* out, int L, int spin, int N, int sampling, int precision, int max_batch,
-                     int device, bool real, bool precompute = false, bool mrec = false) {
+                     int device, bool real, bool precompute = false, bool mrec = false,
+                     bool fma_contraction = false) {
   if (!out) return S2GB_EINVAL;
   *out = nullptr;
   if (L < 1 || L > 8192 || N < 0 || N > L || max_batch < 1) return S2GB_EINVAL;
@@ -492,6 +493,7 @@ int plan_create_impl(s2gb_plan* out, int L, int spin, int N, int sampling, int p
   p.real = real;
   p.precompute = precompute;
   p.mrec = mrec;
+  p.tc = precision == S2GB_FP64 && !precompute && !mrec && !fma_contraction;
   int rc;
   {
     s2gb::DeviceGuard g(device);
@@ -520,11 +522,14 @@ int s2gb_plan_create_real(s2gb_plan* out, int L, int sampling, int precision, in
 int s2gb_plan_create_flags(s2gb_plan* out, int L, int spin, int N, int sampling, int precision,
                            int max_batch, int device, unsigned flags) {
   if (out) *out = nullptr;
-  if (flags & ~(unsigned)(S2GB_PLAN_REAL | S2GB_PLAN_PRECOMPUTE | S2GB_PLAN_MRECURSION)) return S2GB_EINVAL;
+  if (flags & ~(unsigned)(S2GB_PLAN_REAL | S2GB_PLAN_PRECOMPUTE | S2GB_PLAN_MRECURSION |
+                          S2GB_PLAN_FMA_CONTRACTION))
+    return S2GB_EINVAL;
   const bool real = (flags & S2GB_PLAN_REAL) != 0;
   if (real && (spin != 0 || N != 0)) return S2GB_EINVAL;
   return plan_create_impl(out, L, spin, N, sampling, precision, max_batch, device, real,
-                          (flags & S2GB_PLAN_PRECOMPUTE) != 0, (flags & S2GB_PLAN_MRECURSION) != 0);
+                          (flags & S2GB_PLAN_PRECOMPUTE) != 0, (flags & S2GB_PLAN_MRECURSION) != 0,
+                          (flags & S2GB_PLAN_FMA_CONTRACTION) != 0);
 }
 
 void s2gb_plan_destroy(s2gb_plan plan) {

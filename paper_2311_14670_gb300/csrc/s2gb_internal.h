@@ -67,6 +67,8 @@ struct Plan {
   int pole_n = -1;  // ring index of theta = 0 handled by the pole kernels, or -1
   int pole_s = -1;  // ring index of theta = pi handled by the pole kernels, or -1
   bool mrec = false;  // theta stages by the recursion over the order m (theta_mrec.cu)
+  bool tc = false;    // float64 on-the-fly plans: the theta contraction on the tensor cores
+                      // (theta_tc.cu); false: on the float64 FMA pipe (theta_kernels.cu)
   int cap_n = 0;    // rings [ring0, cap_n) and [cap_s, ring0 + nint) use the difference form
   int cap_s = 0;
   int fwd_parts = 1;  // forward theta stage in one launch (nint <= kFwdChunk) or in ring chunks
@@ -218,6 +220,8 @@ cudaError_t launch_theta_inverse_pre(const Plan& p, const InvArgs& a, cudaStream
 cudaError_t launch_theta_forward_pre(const Plan& p, const FwdArgs& a, cudaStream_t st);
 cudaError_t launch_theta_forward(const Plan& p, const FwdArgs& a, cudaStream_t st);
 cudaError_t launch_theta_inverse_f32(const Plan& p, const InvArgs& a, cudaStream_t st);
+// float64 theta stages with the contraction on the tensor cores (theta_tc.cu)
+cudaError_t launch_theta_inverse_tc(const Plan& p, const InvArgs& a, cudaStream_t st);
 cudaError_t launch_theta_forward_f32(const Plan& p, const FwdArgs& a, cudaStream_t st);
 
 // ---- glue kernels (glue.cu) ----

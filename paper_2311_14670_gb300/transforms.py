@@ -40,7 +40,7 @@ class Plan:
 
     def __init__(self, L: int, spin: int = 0, N: int = 0, precision: str = "fp64", max_batch: int = 1,
                  device: int | torch.device | None = None, sampling: str = "mw", real: bool = False,
-                 precompute: bool = False, mrecursion: bool = False):
+                 precompute: bool = False, mrecursion: bool = False, fma_contraction: bool = False):
         if sampling not in _SAMPLINGS:
             raise ValueError(f"sampling must be one of {list(_SAMPLINGS)}")
         if precision not in _PRECISIONS:
@@ -55,12 +55,15 @@ class Plan:
         self.real = bool(real)
         self.precompute = bool(precompute)
         self.mrecursion = bool(mrecursion)      # theta stages by the paper's recursion over m
+        # float64 on-the-fly plans contract on the tensor cores unless this asks for the FMA pipe
+        self.fma_contraction = bool(fma_contraction)
         self.sampling = sampling
         self.R, self.P = sampling_shape(self.L, sampling)
         if self.real and (self.spin != 0 or self.N != 0):
             raise ValueError("real-signal plans are spin-0 sphere transforms (spin = 0, N = 0)")
         flags = ((nat.S2GB_PLAN_REAL if self.real else 0) | (nat.S2GB_PLAN_PRECOMPUTE if self.precompute else 0)
-                 | (nat.S2GB_PLAN_MRECURSION if self.mrecursion else 0))
+                 | (nat.S2GB_PLAN_MRECURSION if self.mrecursion else 0)
+                 | (nat.S2GB_PLAN_FMA_CONTRACTION if self.fma_contraction else 0))
         self._h = nat.plan_create_flags(self.L, self.spin, self.N, _SAMPLINGS[sampling], _PRECISIONS[precision][0],
                                         self.max_batch, int(device), flags)
         self.signal_dtype = _REAL_OF[self.dtype] if self.real else self.dtype

@@ -222,6 +222,7 @@ cudaError_t launch_theta_forward(const Plan& p, const FwdArgs& a, cudaStream_t s
 cudaError_t launch_theta_inverse_f32(const Plan& p, const InvArgs& a, cudaStream_t st);
 // float64 theta stages with the contraction on the tensor cores (theta_tc.cu)
 cudaError_t launch_theta_inverse_tc(const Plan& p, const InvArgs& a, cudaStream_t st);
+cudaError_t launch_theta_forward_tc(const Plan& p, const FwdArgs& a, cudaStream_t st);
 cudaError_t launch_theta_forward_f32(const Plan& p, const FwdArgs& a, cudaStream_t st);
 
 // ---- glue kernels (glue.cu) ----

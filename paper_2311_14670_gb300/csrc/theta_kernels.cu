@@ -455,6 +455,14 @@ cudaError_t launch_theta_forward_rings(const Plan& p, const FwdArgs& a, cudaStre
   if (p.mrec) return launch_theta_forward_mrec(p, a, st);
   if (a.dtab) return launch_theta_forward_pre(p, a, st);
   if (p.precision == S2GB_FP32) return launch_theta_forward_f32(p, a, st);
+  if (p.tc && p.nint <= kFwdChunk) {      // contraction on the tensor cores: one cluster per order
+    FwdArgs b = a;
+    b.row0 = p.ring0;
+    b.nrows = p.nint;
+    b.part = nullptr;
+    b.part_off = 0;
+    return launch_theta_forward_tc(p, b, st);
+  }
   if (paired(p)) {
     if (a.nsig >= 2 && p.nint <= 1024) return launch_fwd_nb<2, true>(p, a, st);
     return launch_fwd_nb<1, true>(p, a, st);

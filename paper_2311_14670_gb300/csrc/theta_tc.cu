@@ -5,33 +5,38 @@
 // matrix of d-functions (generated on the fly by the float64 recursion of theta_kernels.cu, one
 // chain per thread) times a degree x column block of coefficients (c = real and imaginary part of
 // each signal slot).  On GB300 the float64 pipe (2 lanes per SM and clock) is the scarce unit: the
-// recursion needs 2 of its FMAs per element, the contraction 2 per element and signal.  Here the
-// recursion alone stays on the float64 pipe; the contraction runs as exact integer arithmetic on
-// the float16 tensor cores, after the splitting of the Ozaki scheme (Ozaki, Ogita, Oishi, Rump,
-// Numer. Algorithms 59, 2012; on float16 tensor cores: Mukunoki, Ozaki, Ogita, Imamura, 2020):
+// recursion needs 2 of its FMAs per element, a float64 contraction 2 more per element and signal.
+// Here the recursion alone stays on the float64 pipe; the contraction runs as exact integer
+// arithmetic on the float16 tensor cores, after the splitting of the Ozaki scheme (Ozaki, Ogita,
+// Oishi, Rump, Numer. Algorithms 59, 2012; on float16 tensor cores: Mukunoki, Ozaki, Ogita,
+// Imamura, 2020):
 //
 //   * every recursion value becomes a fixed-point integer qa = trunc(x 2^(55 - rho_l)), with rho_l a
 //     power-of-two bound of |x| at degree l (|u^l| <= 1/gamma_l for the block-normalised values,
 //     |d| <= 1 in the difference form), and every coefficient qh = trunc(h' 2^(55 - eps_c)) with one
-//     exponent eps_c per column (the largest over the degrees of the CTA's order);
-//     the scale 2^rho_l moves into the coefficient of degree l, so the product is unchanged;
+//     exponent eps_c per column (a bound over the degrees of the CTA's order); the scale 2^rho_l
+//     moves into the coefficient of degree l, so the product is unchanged;
 //   * |q| < 2^54 is written in 7 balanced base-256 digits in [-128, 127] (adding 0x80 to every
 //     byte of the two's complement integer and subtracting it again digit by digit), each digit
 //     exact in float16;
 //   * one tcgen05.mma per digit i of the d-values multiplies the i-th digit matrix (128 rings x
-//     16 degrees) by the digits j <= 6 - i of the coefficients (16 degrees x 8 columns each) and
-//     accumulates in float32 in Tensor Memory.  Every product is an integer below 2^14 in
-//     magnitude, so up to 1024 degrees sum exactly below 2^24; the accumulators are read back every
-//     1024 degrees (and at the end), converted to integers, combined with the weights
-//     256^(12 - i - j) in 64-bit integers and added in float64.  Digit products with i + j > 6
-//     are dropped: their weight is below 2^-48 of the leading ones, under the rounding of the
-//     float64 recursion.
+//     16 degrees) by the digits j = 0 .. 6 - i of the coefficients and accumulates the product of
+//     digits (i, j) into the Tensor Memory columns of level s = i + j: the B operand holds digit j
+//     in rows 16 j .. 16 j + 15 and the accumulator of MMA i starts at column 16 i.  Every digit
+//     product is an integer below 2^14 in magnitude and a level receives at most 7 of them per
+//     degree, so 128 degrees sum exactly below 2^24 in float32;
+//   * every 128 degrees (and at the end) each thread reads its ring's 7 levels back, converts them
+//     to integers and adds the weights 256^(12 - s) exactly in two 64-bit integers per column;
+//     one float64 conversion at the end gives the result.  Levels s > 6 are never formed: their
+//     weight is below 2^-48 of the leading ones, under the rounding of the float64 recursion.
 //
 // Mapping: CTA = (order rank, tile of 128 rings, n, batch group); thread tid = ring = TMEM lane.
 // Per chunk of 16 degrees each thread advances its chain 16 steps, writing its 7 digit rows into
-// shared memory (K-major 8 x 16-byte core matrices); 64 threads write the coefficient digits; after
-// a CTA barrier one thread issues the 7 MMAs and commits them to the chunk's mbarrier.  Three
-// stages of operand buffers let the recursion of the next chunks overlap the tensor cores.
+// shared memory (K-major 8 x 16-byte core matrices); 16 x slots threads write the coefficient
+// digits; after a CTA barrier one thread issues the 7 MMAs and commits them to an mbarrier.  The
+// operand buffers are single: the next chunk's first digits are stored only after that mbarrier
+// completes, which the 8 recursion steps before the store cover.  Four CTAs share an SM (128 TMEM
+// columns, 128 registers per thread, about 36 KiB of shared memory each).
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
@@ -49,33 +54,20 @@ using namespace theta;
 
 constexpr int kTcRings = 128;        // rings per CTA = MMA M = TMEM lanes
 constexpr int kTcK = 16;             // degrees per chunk = MMA K (float16)
-constexpr int kTcStages = 3;         // operand stages in flight
 constexpr int kDigits = 7;           // balanced base-256 digits per operand
-constexpr int kDrainChunks = 64;     // 1024 degrees: |sum of digit products| <= 1024 * 2^14 = 2^24
-constexpr int kATileBytes = kTcRings * kTcK * 2;        // one digit matrix (4 KiB)
-constexpr int kAStageBytes = kDigits * kATileBytes;     // 28 KiB
-
-// Columns of the accumulator of A-digit i: the B digits j = 0 .. 6 - i of C columns each, padded to
-// a multiple of 16 (the MMA's N granularity at M = 128; the padding rows are the zero digit 7).
-template <int C>
-struct TcCols {
-  static constexpr int n(int i) { return ((C * (kDigits - i) + 15) / 16) * 16; }
-  static constexpr int off(int i) { return i == 0 ? 0 : off(i - 1) + n(i - 1); }
-  static constexpr int total = off(kDigits - 1) + n(kDigits - 1);
-  static constexpr int alloc = total <= 32 ? 32 : total <= 64 ? 64 : total <= 128 ? 128 : total <= 256 ? 256 : 512;
-};
-
-template <int C>
-struct TcSmem {
-  static constexpr int kBRows = 8 * C;                    // digits 0..7 (7: zero) x C columns
-  static constexpr int kBStageBytes = kBRows * kTcK * 2;
-  static constexpr int a_off = 0;
-  static constexpr int b_off = a_off + kTcStages * kAStageBytes;
-  static constexpr int cs_off = b_off + kTcStages * kBStageBytes;
-  static constexpr int bar_off = cs_off + 2 * kTcK * kCoefPerStepN * 8;
-  static constexpr int misc_off = bar_off + kTcStages * 8;
-  static constexpr int bytes = misc_off + 4 * (C + 4);
-};
+constexpr int kLevelCols = 16;       // TMEM columns (and B rows) per digit level: up to 8 used
+constexpr int kTmemCols = 128;       // 7 levels of 16 columns, allocated as 128
+constexpr int kDrainChunks = 8;      // 128 degrees: 7 * 128 * 2^14 < 2^24
+constexpr int kATileBytes = kTcRings * kTcK * 2;                 // one digit matrix (4 KiB)
+constexpr int kABytes = kDigits * kATileBytes;                   // 28 KiB
+constexpr int kBBytes = kDigits * kLevelCols * kTcK * 2;         // 3.5 KiB
+constexpr int kCsOff = kABytes + kBBytes;                        // recursion coefficients [2][16][10]
+constexpr int kWOff = kCsOff + 2 * kTcK * kCoefPerStepN * 8;     // coefficient factors w_j [2][16]
+constexpr int kBarOff = kWOff + 2 * kTcK * 8;
+constexpr int kMiscOff = kBarOff + 8;
+constexpr int kSmemBytes = kMiscOff + 64;
+// requested per CTA: at most four CTAs (4 x 128 TMEM columns) on an SM's 228 KiB
+constexpr int kSmemRequest = 47 * 1024;
 
 // Byte offset of element (row, k) in a K-major operand tile of 16 columns: 8-row x 16-byte core
 // matrices, the two K halves 128 bytes apart (LBO), row groups 256 bytes apart (SBO).
@@ -116,20 +108,24 @@ __device__ __forceinline__ unsigned short digit_half(uint2 q, int i) {
 
 __device__ __forceinline__ void set_status(int code) { atomicCAS(&g_s2gb_device_status, 0, code); }
 
-// Coefficient h'_{j,b} of signal slot b at degree j (times 2^rho_j), both parts.
-template <int NB, bool PAIR, bool DIFF>
-__device__ __forceinline__ double2 coef_scaled(const InvArgs& a, const double* coef_m, const double* scale,
-                                               int j, int b, int sig0, int ni, int m, int n, int L) {
+// Per-degree factor of the coefficients: w_j = scale_j (* gamma_j for block-normalised chains)
+// * 2^rho_j, so that h'_{j,c} = h_{j,c} * sign_slot * w_j and x_j h_j = (x_j 2^-rho_j) h'_j.
+template <bool DIFF>
+__device__ __forceinline__ double coef_factor(const double* coef_m, const double* scale, int j) {
+  const double* c = coef_m + (size_t)j * kCoefPerStepN;
+  const int rho = DIFF ? 2 : exp_of(c[9]) + 2;
+  return (DIFF ? scale[j] : scale[j] * c[3]) * pow2i(rho);
+}
+
+// Coefficient h_{j,b} of signal slot b (times the slot's sign), both parts; zero when inactive.
+template <int NB, bool PAIR>
+__device__ __forceinline__ double2 coef_raw(const InvArgs& a, int j, int b, int sig0, int ni, int m, int n, int L) {
   const Slot sl = slot_of<NB, PAIR>(b, sig0, a.nsig, a.nN, ni, m, n, L);
   double2 h = make_double2(0.0, 0.0);
   if (sl.sig_off >= 0) {
     h = reinterpret_cast<const double2*>(a.flm)[((size_t)sl.sig_off * L + j) * a.flm_ld + sl.m + a.flm_c0];
     if (a.mpos && m == 0) h.y = 0.0;
-    const double* c = coef_m + (size_t)j * kCoefPerStepN;
-    const int rho = DIFF ? 2 : exp_of(c[9]) + 2;
-    const double s = sl.sign * (DIFF ? scale[j] : scale[j] * c[3]) * pow2i(rho);
-    h.x *= s;
-    h.y *= s;
+    if (sl.sign < 0) { h.x = -h.x; h.y = -h.y; }
   }
   return h;
 }
@@ -139,57 +135,67 @@ __device__ __forceinline__ void tc_inverse_body(const InvArgs& a, int m, int ni,
                                                 unsigned char* smem) {
   constexpr int NBX = PAIR ? 2 * NB : NB;
   constexpr int C = 2 * NBX;
-  using Cols = TcCols<C>;
-  using Sm = TcSmem<C>;
+  static_assert(C <= 8, "at most 8 columns per level");
   const int L = a.L, T = 2 * L - 1;
   const int tid = threadIdx.x, warp = tid >> 5;
   const int mi = m + L - 1;
   const int sig0 = blockIdx.z * NB;
 
-  unsigned char* sA = smem + Sm::a_off;
-  unsigned char* sB = smem + Sm::b_off;
-  double* cs = reinterpret_cast<double*>(smem + Sm::cs_off);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + Sm::bar_off);
-  int* eps_s = reinterpret_cast<int*>(smem + Sm::misc_off);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(eps_s + C);
-  int* abort_s = reinterpret_cast<int*>(eps_s + C + 1);
+  unsigned char* sA = smem;
+  unsigned char* sB = smem + kABytes;
+  double* cs = reinterpret_cast<double*>(smem + kCsOff);
+  double* ws = reinterpret_cast<double*>(smem + kWOff);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kBarOff);
+  int* eps_s = reinterpret_cast<int*>(smem + kMiscOff);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(eps_s + 8);
+  int* abort_s = reinterpret_cast<int*>(eps_s + 9);
+  const uint32_t bar_a = tc::smem_addr(bar);
 
   const double* coef_m = a.coef + ((size_t)ni * T + mi) * (size_t)L * kCoefPerStepN;
   const double* scale = a.scale + (size_t)ni * L;
 
-  // ---- set-up: barriers, Tensor Memory, zero digit rows, column exponents
+  // ---- set-up: barrier, Tensor Memory, zero B rows, column exponent bounds, first coefficients
   if (tid == 0) {
-    for (int s = 0; s < kTcStages; ++s) tc::mbar_init(tc::smem_addr(&bars[s]), 1);
+    tc::mbar_init(bar_a, 1);
     tc::mbar_init_fence();
     *abort_s = 0;
   }
-  if (warp == 0) tc::tmem_alloc(tc::smem_addr(tmem_slot), Cols::alloc);
-  for (int q = tid; q < kTcStages * Sm::kBStageBytes / 16; q += kTcRings)
-    reinterpret_cast<uint4*>(sB)[q] = make_uint4(0, 0, 0, 0);
-  if (tid < C) eps_s[tid] = -100000;
+  if (warp == 0) tc::tmem_alloc(tc::smem_addr(tmem_slot), kTmemCols);
+  for (int q = tid; q < kBBytes / 16; q += kTcRings) reinterpret_cast<uint4*>(sB)[q] = make_uint4(0, 0, 0, 0);
+  if (tid < 8) eps_s[tid] = -100000;
+  for (int q = tid; q < kTcK * kCoefPerStepN; q += kTcRings) {
+    const int j = l0 + q / kCoefPerStepN;
+    cs[q] = (j < L) ? coef_m[(size_t)l0 * kCoefPerStepN + q] : 0.0;
+  }
+  if (tid < kTcK) ws[tid] = (l0 + tid < L) ? coef_factor<DIFF>(coef_m, scale, l0 + tid) : 0.0;
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = *tmem_slot;
 
+  // |h_{j,c} w_j| < 2^(e_h + 1) 2^(e_w + 1): eps_c = max_j (e_h + e_w) + 3 bounds the column
   const int ndeg = L - l0;
-  for (int q = tid; q < ndeg * NBX; q += kTcRings) {
-    const int j = l0 + q / NBX, b = q % NBX;
-    const double2 h = coef_scaled<NB, PAIR, DIFF>(a, coef_m, scale, j, b, sig0, ni, m, n, L);
-    if (h.x != 0.0) atomicMax(&eps_s[2 * b], exp_of(h.x));
-    if (h.y != 0.0) atomicMax(&eps_s[2 * b + 1], exp_of(h.y));
-  }
-  // coefficients of the first chunk
-  for (int q = tid; q < kTcK * kCoefPerStepN; q += kTcRings) {
-    const int j = l0 + q / kCoefPerStepN;
-    cs[q] = (j < L) ? coef_m[(size_t)l0 * kCoefPerStepN + q] : 0.0;
+  {
+    int emax[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) emax[c] = -100000;
+    for (int j = l0 + tid; j < L; j += kTcRings) {
+      const int ew = exp_of(coef_factor<DIFF>(coef_m, scale, j));
+#pragma unroll
+      for (int b = 0; b < NBX; ++b) {
+        const double2 h = coef_raw<NB, PAIR>(a, j, b, sig0, ni, m, n, L);
+        if (h.x != 0.0) emax[2 * b] = max(emax[2 * b], exp_of(h.x) + ew);
+        if (h.y != 0.0) emax[2 * b + 1] = max(emax[2 * b + 1], exp_of(h.y) + ew);
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      const int e = __reduce_max_sync(0xffffffffu, emax[c]);
+      if ((tid & 31) == 0) atomicMax(&eps_s[c], e);
+    }
   }
   __syncthreads();
-  // column exponents: |h'| < 2^(eps_c - 1) (an all-zero column keeps eps_c = 2)
-  auto col_eps = [&](int c) { const int e = eps_s[c]; return (e < -2000 ? 0 : e) + 2; };
-  int eps[C];
-#pragma unroll
-  for (int c = 0; c < C; ++c) eps[c] = col_eps(c);
+  auto col_eps = [&](int c) { const int e = eps_s[c]; return (e < -4000 ? 0 : e) + 3; };
 
   // ---- the chain of this thread's ring
   const SeedData sd = a.seed[(size_t)ni * T + mi];
@@ -205,37 +211,32 @@ __device__ __forceinline__ void tc_inverse_body(const InvArgs& a, int m, int ni,
   }
   const unsigned nmask = north ? 0x80000000u : 0u;
 
-  double acc[C];
+  // level sums, exactly: X_c = sum 2^24 L0 + 2^16 L1 + 2^8 L2 + L3, Y_c = 2^16 L4 + 2^8 L5 + L6
+  long long X[C], Y[C];
 #pragma unroll
-  for (int c = 0; c < C; ++c) acc[c] = 0.0;
+  for (int c = 0; c < C; ++c) { X[c] = 0; Y[c] = 0; }
 
   const int nchunks = (ndeg + kTcK - 1) / kTcK;
   int since_reset = 0;
   bool ok = true;
   const uint32_t sA_addr = tc::smem_addr(sA), sB_addr = tc::smem_addr(sB);
+  const int hb = tid % NBX, hj = tid / NBX;   // coefficient slot and chunk degree of this thread
   for (int k = 0; k < nchunks; ++k) {
-    const int s = k % kTcStages;
     const int jc = l0 + k * kTcK;
     const double* csk = cs + (k & 1) * kTcK * kCoefPerStepN;
-    // prefetch: the coefficients of the next chunk, and this chunk's h' for the B digits
+    // prefetch: the next chunk's recursion coefficients and this chunk's coefficients h
     double cpre[2] = {0.0, 0.0};
 #pragma unroll
     for (int r = 0; r < 2; ++r) {
       const int q = tid + r * kTcRings;
-      const int j = jc + kTcK + q / kCoefPerStepN;
-      if (q < kTcK * kCoefPerStepN && j < L) cpre[r] = coef_m[(size_t)(jc + kTcK) * kCoefPerStepN + q];
+      if (q < kTcK * kCoefPerStepN && jc + kTcK + q / kCoefPerStepN < L)
+        cpre[r] = coef_m[(size_t)(jc + kTcK) * kCoefPerStepN + q];
     }
+    double wpre = 0.0;
+    if (tid < kTcK && jc + kTcK + tid < L) wpre = coef_factor<DIFF>(coef_m, scale, jc + kTcK + tid);
     double2 hpre = make_double2(0.0, 0.0);
-    const int hb = tid % NBX, hj = jc + tid / NBX;
-    if (tid < kTcK * NBX && hj < L) hpre = coef_scaled<NB, PAIR, DIFF>(a, coef_m, scale, hj, hb, sig0, ni, m, n, L);
+    if (tid < kTcK * NBX && jc + hj < L) hpre = coef_raw<NB, PAIR>(a, jc + hj, hb, sig0, ni, m, n, L);
 
-    // the stage's previous MMAs (chunk k - 3) must be complete before its buffers are rewritten
-    if (k >= kTcStages && !tc::mbar_wait(tc::smem_addr(&bars[s]), (uint32_t)((k / kTcStages - 1) & 1))) {
-      set_status(tc::kStatusMmaWait);
-      *abort_s = 1;
-    }
-
-    unsigned char* aStage = sA + s * kAStageBytes;
 #pragma unroll
     for (int g = 0; g < 2; ++g) {
       uint32_t w[kDigits][4];
@@ -267,29 +268,34 @@ __device__ __forceinline__ void tc_inverse_body(const InvArgs& a, int m, int ni,
         }
       }
       renorm(x, y, E);
+      // the previous chunk's MMAs read these buffers: they must be complete before the first store
+      if (g == 0 && k > 0 && !tc::mbar_wait(bar_a, (uint32_t)((k - 1) & 1))) {
+        set_status(tc::kStatusMmaWait);
+        *abort_s = 1;
+      }
 #pragma unroll
       for (int i = 0; i < kDigits; ++i) {
-        uint4 val = live ? make_uint4(w[i][0], w[i][1], w[i][2], w[i][3]) : make_uint4(0, 0, 0, 0);
-        *reinterpret_cast<uint4*>(aStage + i * kATileBytes + kmajor_off(tid, g * 8)) = val;
+        const uint4 val = live ? make_uint4(w[i][0], w[i][1], w[i][2], w[i][3]) : make_uint4(0, 0, 0, 0);
+        *reinterpret_cast<uint4*>(sA + i * kATileBytes + kmajor_off(tid, g * 8)) = val;
       }
     }
-    // B digits of this chunk: thread (degree jj, slot b) writes rows (i, 2b) and (i, 2b + 1)
+    // B digits of this chunk: thread (degree hj, slot hb) writes rows 16 i + 2 hb and 16 i + 2 hb + 1
     if (tid < kTcK * NBX) {
-      unsigned char* bStage = sB + s * Sm::kBStageBytes;
-      const int jj = tid / NBX;
-      const uint2 qr = offset_digits(hpre.x, col_eps(2 * hb));
-      const uint2 qi = offset_digits(hpre.y, col_eps(2 * hb + 1));
+      const double wj = ws[(k & 1) * kTcK + hj];
+      const uint2 qr = offset_digits(hpre.x * wj, col_eps(2 * hb));
+      const uint2 qi = offset_digits(hpre.y * wj, col_eps(2 * hb + 1));
 #pragma unroll
       for (int i = 0; i < kDigits; ++i) {
-        *reinterpret_cast<unsigned short*>(bStage + kmajor_off(i * C + 2 * hb, jj)) = digit_half(qr, i);
-        *reinterpret_cast<unsigned short*>(bStage + kmajor_off(i * C + 2 * hb + 1, jj)) = digit_half(qi, i);
+        *reinterpret_cast<unsigned short*>(sB + kmajor_off(kLevelCols * i + 2 * hb, hj)) = digit_half(qr, i);
+        *reinterpret_cast<unsigned short*>(sB + kmajor_off(kLevelCols * i + 2 * hb + 1, hj)) = digit_half(qi, i);
       }
     }
-    // the next chunk's recursion coefficients
+    // the next chunk's recursion coefficients and factors
     {
       double* csn = cs + ((k + 1) & 1) * kTcK * kCoefPerStepN;
       csn[tid] = cpre[0];
       if (tid + kTcRings < kTcK * kCoefPerStepN) csn[tid + kTcRings] = cpre[1];
+      if (tid < kTcK) ws[((k + 1) & 1) * kTcK + tid] = wpre;
     }
     tc::fence_proxy_async();
     __syncthreads();
@@ -298,51 +304,38 @@ __device__ __forceinline__ void tc_inverse_body(const InvArgs& a, int m, int ni,
       tc::fence_after_sync();
 #pragma unroll
       for (int i = 0; i < kDigits; ++i) {
-        const uint64_t ad = tc::smem_desc(sA_addr + s * kAStageBytes + i * kATileBytes, 128, 256);
-        const uint64_t bd = tc::smem_desc(sB_addr + s * Sm::kBStageBytes, 128, 256);
-        tc::mma_f16(tmem + Cols::off(i), ad, bd, tc::idesc_f16_f32(kTcRings, Cols::n(i)), since_reset > 0);
+        const uint64_t ad = tc::smem_desc(sA_addr + i * kATileBytes, 128, 256);
+        const uint64_t bd = tc::smem_desc(sB_addr, 128, 256);
+        // MMA 0 covers every level and (re)starts the accumulation after a read-back
+        tc::mma_f16(tmem + kLevelCols * i, ad, bd, tc::idesc_f16_f32(kTcRings, kLevelCols * (kDigits - i)),
+                    since_reset > 0 || i > 0);
       }
-      tc::mma_commit(tc::smem_addr(&bars[s]));
+      tc::mma_commit(bar_a);
     }
     ++since_reset;
     if (since_reset == kDrainChunks || k == nchunks - 1) {
-      // read the accumulators back: integer digit sums per level i + j, combined exactly
-      if (!tc::mbar_wait(tc::smem_addr(&bars[s]), (uint32_t)((k / kTcStages) & 1))) {
+      // read the 7 levels of this ring back and add them exactly into X, Y
+      if (!tc::mbar_wait(bar_a, (uint32_t)(k & 1))) {
         set_status(tc::kStatusMmaWait);
         ok = false;
       }
       tc::fence_after_sync();
       if (__all_sync(0xffffffffu, ok)) {
+        const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);
         int lam[kDigits][C];
 #pragma unroll
-        for (int i = 0; i < kDigits; ++i)
+        for (int s = 0; s < kDigits; ++s) {
+          uint32_t r[8];
+          tc::tmem_ld8(trow + (uint32_t)(kLevelCols * s), r);
+          tc::tmem_ld_wait();
 #pragma unroll
-          for (int c = 0; c < C; ++c) lam[i][c] = 0;
-        const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);
-#pragma unroll
-        for (int i = 0; i < kDigits; ++i) {
-          const int ncol = C * (kDigits - i);
-#pragma unroll
-          for (int q8 = 0; q8 < (C * kDigits + 7) / 8; ++q8) {
-            if (q8 * 8 < ncol) {
-              uint32_t r[8];
-              tc::tmem_ld8(trow + (uint32_t)(Cols::off(i) + 8 * q8), r);
-              tc::tmem_ld_wait();
-#pragma unroll
-              for (int e = 0; e < 8; ++e) {
-                const int col = 8 * q8 + e;
-                if (col < ncol) lam[i + col / C][col % C] += __float2int_rn(__uint_as_float(r[e]));
-              }
-            }
-          }
+          for (int c = 0; c < C; ++c) lam[s][c] = __float2int_rn(__uint_as_float(r[c]));
         }
 #pragma unroll
         for (int c = 0; c < C; ++c) {
-          const long long hv = ((long long)lam[0][c] << 24) + ((long long)lam[1][c] << 16) +
-                               ((long long)lam[2][c] << 8) + (long long)lam[3][c];
-          const long long lv = ((long long)lam[4][c] << 16) + ((long long)lam[5][c] << 8) + (long long)lam[6][c];
-          const double val = fma((double)lv, 0x1p-24, (double)hv);
-          acc[c] += ldexp(val, eps[c] - 38);
+          X[c] += ((long long)lam[0][c] << 24) + ((long long)lam[1][c] << 16) + ((long long)lam[2][c] << 8) +
+                  (long long)lam[3][c];
+          Y[c] += ((long long)lam[4][c] << 16) + ((long long)lam[5][c] << 8) + (long long)lam[6][c];
         }
       }
       tc::fence_before_sync();
@@ -351,27 +344,30 @@ __device__ __forceinline__ void tc_inverse_body(const InvArgs& a, int m, int ni,
     }
   }
 
-  if (ok) {
+  if (ok && t < a.nring) {
+    // value = 2^(eps_c - 110) sum_s 256^(12 - s) L_s = 2^(eps_c - 38) (X + 2^-24 Y)
 #pragma unroll
     for (int b = 0; b < NBX; ++b) {
       const Slot sl = slot_of<NB, PAIR>(b, sig0, a.nsig, a.nN, ni, m, n, L);
-      if (sl.sig_off < 0 || t >= a.nring) continue;
+      if (sl.sig_off < 0) continue;
+      const double re = ldexp(fma((double)Y[2 * b], 0x1p-24, (double)X[2 * b]), col_eps(2 * b) - 38);
+      const double im = ldexp(fma((double)Y[2 * b + 1], 0x1p-24, (double)X[2 * b + 1]), col_eps(2 * b + 1) - 38);
       const long long col = a.m_mod ? (sl.m >= 0 ? sl.m : sl.m + a.mmod) : sl.mi;
-      double2* o = reinterpret_cast<double2*>(a.out) + (size_t)sl.sig_off * a.s_sig + t * a.s_t + col * a.s_m;
-      *o = make_double2(acc[2 * b], acc[2 * b + 1]);
+      reinterpret_cast<double2*>(a.out)[(size_t)sl.sig_off * a.s_sig + t * a.s_t + col * a.s_m] =
+          make_double2(re, im);
     }
   }
   tc::fence_before_sync();
   __syncthreads();
   if (warp == 0) {
     tc::fence_after_sync();
-    tc::tmem_dealloc(tmem, Cols::alloc);
+    tc::tmem_dealloc(tmem, kTmemCols);
   }
 }
 
 // Grid as theta_inverse_kernel: x = (rank of m) * ntiles + tile, y = n index, z = batch group.
 template <int NB, bool PAIR>
-__global__ void __launch_bounds__(kTcRings, 1) theta_inverse_tc_kernel(InvArgs a, int ntiles) {
+__global__ void __launch_bounds__(kTcRings, 4) theta_inverse_tc_kernel(InvArgs a, int ntiles) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int L = a.L;
   const int rank = a.rank0 + (int)(blockIdx.x / ntiles), tile = blockIdx.x % ntiles;
@@ -401,16 +397,461 @@ __global__ void __launch_bounds__(kTcRings, 1) theta_inverse_tc_kernel(InvArgs a
 
 template <int NB, bool PAIR>
 cudaError_t launch_inv_tc(const InvArgs& a, cudaStream_t st) {
-  constexpr int C = 2 * (PAIR ? 2 * NB : NB);
+  static_assert(kSmemBytes <= kSmemRequest, "shared memory layout");
   const int ntiles = (a.nring - a.ring0 + kTcRings - 1) / kTcRings;
   if (ntiles == 0) return cudaSuccess;
-  // at least 76 KiB per CTA, so that at most two CTAs (2 x 256 TMEM columns) share an SM
-  const size_t smem = TcSmem<C>::bytes > 78 * 1024 ? TcSmem<C>::bytes : 78 * 1024;
   auto kern = theta_inverse_tc_kernel<NB, PAIR>;
-  cudaError_t e = set_dynamic_smem((const void*)kern, smem);
+  cudaError_t e = set_dynamic_smem((const void*)kern, kSmemRequest);
   if (e != cudaSuccess) return e;
   dim3 grid(a.nrank * ntiles, PAIR ? (a.nN + 1) / 2 : a.nN, (a.nsig + NB - 1) / NB);
-  kern<<<grid, kTcRings, smem, st>>>(a, ntiles);
+  kern<<<grid, kTcRings, kSmemRequest, st>>>(a, ntiles);
+  return launched();
+}
+
+// =============================================================================================
+// Forward theta stage (Sec. 4.1, Eq. disc_sh_expanded) with the contraction over the rings on the
+// tensor cores: flm[l][c] = scale_l sum_t d^l(theta_t) g'_t[c], g' the ring data times the ring
+// weight and the slot sign.  The sum runs over the rings, across the threads of a CTA (one chain,
+// i.e. one ring, per thread) and across the CTAs of the order (tiles of 128 rings).
+//
+//   * The ring data are split once per CTA into 7 digits per column (rows 8 j + c of the A operand,
+//     M = 64 with the zero digit 7; K = 128 rings), with one exponent per column over all rings of
+//     the order, agreed by the CTAs through distributed shared memory.
+//   * Per chunk of 16 degrees the recursion values are split as in the inverse (B operand, K = 128
+//     rings x N = 112 = (digit i, degree l), stored N-major: each thread writes 16-byte rows) and 8
+//     MMAs (16 rings each) form every digit product S_ij(c, l) in Tensor Memory.  A tile sums at
+//     most 128 rings: |S_ij| <= 2^21, exact in float32.
+//   * Each accumulator row (j, c) folds its products into two exact 64-bit words per degree,
+//     X = sum_{i+j<=3} 256^(3-i-j) S_ij and Y = sum_{4<=i+j<=6} 256^(6-i-j) S_ij; the rows of a
+//     column are added through shared memory, and the tiles of the order through distributed
+//     shared memory of the thread-block cluster (one cluster per order, up to 16 tiles), in
+//     integers: the result does not depend on the order of the additions.  Tiles in the difference
+//     form (d) and in the block-normalised form (u = d / gamma_l) are summed separately and
+//     combined in float64 with their scales.
+// =============================================================================================
+constexpr int kFwdN = kDigits * kTcK;             // 112 = (d digit i, degree l)
+constexpr int kFwdM = 64;                         // rows 8 j + c: coefficient digit j, column c
+constexpr int kFwdMaxTiles = 16;
+constexpr int kFwdTmemCols = 128;
+constexpr int kGBytes = kFwdM * kTcRings * 2;     // 16 KiB
+constexpr int kDBytes = kTcRings * kFwdN * 2;     // 28 KiB
+constexpr int kFwdStageOff = kGBytes + kDBytes;                       // [16 l][7 j][8 c] x (X, Y)
+constexpr int kFwdClOff = kFwdStageOff + 8 * kTcK * kDigits * 16;     // [2][16 l][8 c] x (X, Y)
+constexpr int kFwdCsOff = kFwdClOff + 2 * 8 * kTcK * 16;
+constexpr int kFwdBarOff = kFwdCsOff + 2 * kTcK * kCoefPerStepN * 8;
+constexpr int kFwdMiscOff = kFwdBarOff + 8;       // eps_loc[8], cls, tmem_slot, abort
+constexpr int kFwdSmemBytes = kFwdMiscOff + 64;
+constexpr int kFwdSmemRequest = 70 * 1024;        // at most three CTAs (3 x 128 TMEM columns) per SM
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cluster_arrive() {
+  asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait() {
+  asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ uint32_t peer_addr(uint32_t saddr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ long long ld_peer_s64(uint32_t addr) {
+  long long v;
+  asm volatile("ld.shared::cluster.s64 %0, [%1];" : "=l"(v) : "r"(addr) : "memory");
+  return v;
+}
+__device__ __forceinline__ int ld_peer_s32(uint32_t addr) {
+  int v;
+  asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
+  return v;
+}
+
+// Byte offset of (row r, ring k) in the coefficient-digit tile: K-major, 128 rings per row.
+__device__ __forceinline__ int gtile_off(int r, int k) {
+  return (r >> 3) * 2048 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
+}
+// Byte offset of (ring k, n / 8 = 2 i + degree half) in the d-digit tile: N-major 16-byte rows.
+__device__ __forceinline__ int dtile_off(int k, int n8) {
+  return (k >> 3) * (kFwdN / 8) * 128 + n8 * 128 + (k & 7) * 16;
+}
+
+template <int NB, bool PAIR, bool DIFF>
+__device__ __forceinline__ void tc_forward_body(const FwdArgs& a, int m, int ni, int n, int tile, int ntiles,
+                                                int l0, unsigned char* smem) {
+  constexpr int NBX = PAIR ? 2 * NB : NB;
+  constexpr int C = 2 * NBX;
+  static_assert(C <= 8, "at most 8 columns");
+  const int L = a.L, T = 2 * L - 1;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int mi = m + L - 1;
+  const int sig0 = blockIdx.z * NB;
+  const uint32_t crank = cluster_rank();
+
+  unsigned char* sG = smem;
+  unsigned char* sD = smem + kGBytes;
+  long long* stage = reinterpret_cast<long long*>(smem + kFwdStageOff);
+  long long* cl = reinterpret_cast<long long*>(smem + kFwdClOff);
+  double* cs = reinterpret_cast<double*>(smem + kFwdCsOff);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kFwdBarOff);
+  int* eps_loc = reinterpret_cast<int*>(smem + kFwdMiscOff);
+  int* cls = eps_loc + 8;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(eps_loc + 9);
+  int* abort_s = eps_loc + 10;
+  const uint32_t bar_a = tc::smem_addr(bar);
+  double2* const outb = reinterpret_cast<double2*>(a.flm);
+
+  const double* coef_m = a.coef + ((size_t)ni * T + mi) * (size_t)L * kCoefPerStepN;
+  const double* scale = a.scale + (size_t)ni * L;
+  const int t = a.row0 + tile * kTcRings + tid;
+  const bool tact = t < a.row0 + a.nrows;
+
+  // ---- set-up: barrier, Tensor Memory, the degrees below l0, column exponents over the cluster
+  if (tid == 0) {
+    tc::mbar_init(bar_a, 1);
+    tc::mbar_init_fence();
+    *abort_s = 0;
+    *cls = DIFF ? 1 : 0;
+  }
+  if (warp == 0) tc::tmem_alloc(tc::smem_addr(tmem_slot), kFwdTmemCols);
+  for (int q = tid; q < kGBytes / 16; q += kTcRings) reinterpret_cast<uint4*>(sG)[q] = make_uint4(0, 0, 0, 0);
+  if (tid < 8) eps_loc[tid] = -100000;
+  if (tile == 0) {
+    const int lz = min(l0, L);
+    for (int q = tid; q < NBX * lz; q += kTcRings) {
+      const int b = q / lz, j = q % lz;
+      const Slot sl = slot_of<NB, PAIR>(b, sig0, a.nsig, a.nN, ni, m, n, L);
+      if (sl.sig_off >= 0) outb[((size_t)sl.sig_off * L + j) * a.flm_ld + sl.m + a.flm_c0] = make_double2(0.0, 0.0);
+    }
+  }
+  for (int q = tid; q < kTcK * kCoefPerStepN; q += kTcRings) {
+    const int j = l0 + q / kCoefPerStepN;
+    cs[q] = (j < L) ? coef_m[(size_t)l0 * kCoefPerStepN + q] : 0.0;
+  }
+  double2 gv[NBX];
+  {
+    int emax[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) emax[c] = -100000;
+#pragma unroll
+    for (int b = 0; b < NBX; ++b) {
+      const Slot sl = slot_of<NB, PAIR>(b, sig0, a.nsig, a.nN, ni, m, n, L);
+      double2 g = make_double2(0.0, 0.0);
+      if (tact && sl.sig_off >= 0) {
+        const long long col = a.m_mod ? (sl.m >= 0 ? sl.m : sl.m + a.mmod) : sl.mi;
+        g = reinterpret_cast<const double2*>(a.g)[(size_t)sl.sig_off * a.s_sig + t * a.s_t + col * a.s_m];
+        const double w = (a.use_nu ? a.nu[t] : 1.0) * sl.sign;
+        g.x *= w;
+        g.y *= w;
+      }
+      gv[b] = g;
+      if (g.x != 0.0) emax[2 * b] = exp_of(g.x);
+      if (g.y != 0.0) emax[2 * b + 1] = exp_of(g.y);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      const int e = __reduce_max_sync(0xffffffffu, emax[c]);
+      if (lane == 0) atomicMax(&eps_loc[c], e);
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tmem_slot;
+  cluster_arrive();
+  cluster_wait();                            // every CTA's eps_loc and cls are written
+  int eps[C];
+#pragma unroll
+  for (int c = 0; c < C; ++c) {
+    int e = -100000;
+    for (int q = 0; q < ntiles; ++q) e = max(e, ld_peer_s32(peer_addr(tc::smem_addr(&eps_loc[c]), (uint32_t)q)));
+    eps[c] = (e < -2000 ? 0 : e) + 2;        // |g'| < 2^(eps_c - 1)
+  }
+  auto col_eps = [&](int c) {
+    int e = eps[0];
+#pragma unroll
+    for (int q = 1; q < C; ++q) e = (c == q) ? eps[q] : e;
+    return e;
+  };
+  unsigned diff_tiles = 0;                   // bit q: tile q of the cluster runs the difference form
+  for (int q = 0; q < ntiles; ++q) diff_tiles |= (unsigned)ld_peer_s32(peer_addr(tc::smem_addr(cls), (uint32_t)q)) << q;
+
+  // the A operand: digit j of column c in row 8 j + c, ring tid in column tid
+#pragma unroll
+  for (int b = 0; b < NBX; ++b) {
+    const uint2 qr = offset_digits(gv[b].x, eps[2 * b]);
+    const uint2 qi = offset_digits(gv[b].y, eps[2 * b + 1]);
+#pragma unroll
+    for (int j = 0; j < kDigits; ++j) {
+      *reinterpret_cast<unsigned short*>(sG + gtile_off(8 * j + 2 * b, tid)) = digit_half(qr, j);
+      *reinterpret_cast<unsigned short*>(sG + gtile_off(8 * j + 2 * b + 1, tid)) = digit_half(qi, j);
+    }
+  }
+
+  // ---- the chain of this thread's ring
+  const SeedData sd = a.seed[(size_t)ni * T + mi];
+  double x = 0.0, y = 0.0, v = 0.0;
+  int E = 0;
+  bool north = true;
+  if (tact) {
+    const RingData rd = a.ring[t];
+    seed_value(sd, rd, x, E);
+    v = rd.v;
+    north = rd.north;
+  }
+  const unsigned nmask = north ? 0x80000000u : 0u;
+
+  const int ndeg = L - l0;
+  const int nchunks = (ndeg + kTcK - 1) / kTcK;
+  const uint32_t sG_addr = tc::smem_addr(sG), sD_addr = tc::smem_addr(sD);
+  const uint32_t cl_addr = tc::smem_addr(cl);
+  bool ok = true;
+
+  // sum over the cluster's tiles of chunk kk's (X, Y) and write the owned coefficients
+  auto reduce_chunk = [&](int kk) {
+    const int buf = kk & 1;
+    for (int p = tid * ntiles + (int)crank; p < C * kTcK; p += ntiles * kTcRings) {
+      const int c = p % C, ll = p / C, l = l0 + kk * kTcK + ll;
+      if (l >= L) continue;
+      const int b = c >> 1;
+      const Slot sl = slot_of<NB, PAIR>(b, sig0, a.nsig, a.nN, ni, m, n, L);
+      if (sl.sig_off < 0) continue;
+      long long Xp = 0, Yp = 0, Xd = 0, Yd = 0;
+      const uint32_t off = cl_addr + (uint32_t)(((buf * kTcK + ll) * 8 + c) * 16);
+      for (int q = 0; q < ntiles; ++q) {
+        const uint32_t pa = peer_addr(off, (uint32_t)q);
+        const long long X = ld_peer_s64(pa), Y = ld_peer_s64(pa + 8);
+        if ((diff_tiles >> q) & 1u) { Xd += X; Yd += Y; } else { Xp += X; Yp += Y; }
+      }
+      // plain tiles hold u = d / gamma_l digits at 2^-rho_l: times gamma_l 2^rho_l; difference
+      // tiles d digits at 2^-2
+      const double* cc = coef_m + (size_t)l * kCoefPerStepN;
+      const double vp = fma((double)Yp, 0x1p-24, (double)Xp) * cc[3];
+      const double vd = fma((double)Yd, 0x1p-24, (double)Xd);
+      const int e = col_eps(c);
+      const double val = (ldexp(vp, exp_of(cc[9]) + 2 + e - 38) + ldexp(vd, 2 + e - 38)) * scale[l];
+      reinterpret_cast<double*>(outb + ((size_t)sl.sig_off * L + l) * a.flm_ld + sl.m + a.flm_c0)[c & 1] = val;
+    }
+  };
+
+  // Software pipeline, iteration k (k = 0 .. nchunks): the recursion of chunk k; in its middle
+  // the read-back of chunk k-1's accumulator (its MMAs ran during the first 8 steps); after the
+  // CTA barrier the MMAs of chunk k and this tile's sums of chunk k-1; the cluster's sums of
+  // chunk k-2, whose tile sums every CTA published one iteration earlier.
+  const int row = 16 * warp + lane;          // accumulator row 8 j + c of this thread's lane
+  const int rj = row >> 3, rc = row & 7;
+  const bool rowact = lane < 16 && rj < kDigits && rc < C;
+  for (int k = 0; k <= nchunks; ++k) {
+    const bool comp = k < nchunks;
+    const int jc = l0 + k * kTcK;
+    const double* csk = cs + (k & 1) * kTcK * kCoefPerStepN;
+    double cpre[2] = {0.0, 0.0};
+    if (comp) {
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        const int q = tid + r * kTcRings;
+        if (q < kTcK * kCoefPerStepN && jc + kTcK + q / kCoefPerStepN < L)
+          cpre[r] = coef_m[(size_t)(jc + kTcK) * kCoefPerStepN + q];
+      }
+    }
+#pragma unroll
+    for (int g = 0; g < 2; ++g) {
+      uint32_t w[kDigits][4];
+      const bool live = comp && __any_sync(0xffffffffu, E == 0);
+      uint2 q0 = make_uint2(0, 0);
+      if (comp) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int jj = g * 8 + u, j = jc + jj;
+          const StepN c = stepn_at(csk + jj * kCoefPerStepN);
+          if (live) {
+            const double xl = (E == 0 && j < L) ? x : 0.0;
+            const int rho = DIFF ? 2 : exp_of(c.ig) + 2;
+            const uint2 q = offset_digits(xl, rho);
+            if (u & 1) {
+              w[0][u >> 1] = digit_pair(q0.y, q.y, 2);
+              w[1][u >> 1] = digit_pair(q0.y, q.y, 1);
+              w[2][u >> 1] = digit_pair(q0.y, q.y, 0);
+              w[3][u >> 1] = digit_pair(q0.x, q.x, 3);
+              w[4][u >> 1] = digit_pair(q0.x, q.x, 2);
+              w[5][u >> 1] = digit_pair(q0.x, q.x, 1);
+              w[6][u >> 1] = digit_pair(q0.x, q.x, 0);
+            } else {
+              q0 = q;
+            }
+          }
+          if (j < L - 1) {
+            stepn<DIFF>(x, y, v, nmask, north, c);
+            if (u == kNormBlock - 1) unnormalise<DIFF>(x, y, c);
+          }
+        }
+        renorm(x, y, E);
+      }
+      if (g == 0 && k > 0 && ok) {
+        // chunk k-1's MMAs are done: read its digit products back into the staging area
+        if (!tc::mbar_wait(bar_a, (uint32_t)((k - 1) & 1))) {
+          set_status(tc::kStatusMmaWait);
+          *abort_s = 1;
+        }
+        tc::fence_after_sync();
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          long long Xs[8], Ys[8];
+#pragma unroll
+          for (int e = 0; e < 8; ++e) { Xs[e] = 0; Ys[e] = 0; }
+#pragma unroll
+          for (int i = 0; i < kDigits; ++i) {
+            uint32_t r[8];
+            tc::tmem_ld8(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(kTcK * i + 8 * h), r);
+            tc::tmem_ld_wait();
+            const int sdeg = i + rj;
+            if (sdeg <= 6) {
+#pragma unroll
+              for (int e = 0; e < 8; ++e) {
+                const long long S = (long long)__float2int_rn(__uint_as_float(r[e]));
+                if (sdeg <= 3) Xs[e] += S << (8 * (3 - sdeg));
+                else Ys[e] += S << (8 * (6 - sdeg));
+              }
+            }
+          }
+          if (rowact) {
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+              longlong2* st = reinterpret_cast<longlong2*>(stage) + ((8 * h + e) * kDigits + rj) * 8 + rc;
+              *st = make_longlong2(Xs[e], Ys[e]);
+            }
+          }
+        }
+        tc::fence_before_sync();
+      }
+      if (comp) {
+#pragma unroll
+        for (int i = 0; i < kDigits; ++i) {
+          const uint4 val = live ? make_uint4(w[i][0], w[i][1], w[i][2], w[i][3]) : make_uint4(0, 0, 0, 0);
+          *reinterpret_cast<uint4*>(sD + dtile_off(tid, 2 * i + g)) = val;
+        }
+      }
+    }
+    if (comp) {
+      double* csn = cs + ((k + 1) & 1) * kTcK * kCoefPerStepN;
+      csn[tid] = cpre[0];
+      if (tid + kTcRings < kTcK * kCoefPerStepN) csn[tid + kTcRings] = cpre[1];
+    }
+    tc::fence_proxy_async();
+    __syncthreads();
+    if (*abort_s) ok = false;
+    if (comp && ok && tid == 0) {
+      tc::fence_after_sync();
+#pragma unroll
+      for (int ks = 0; ks < kTcRings / kTcK; ++ks) {
+        const uint64_t ad = tc::smem_desc(sG_addr + ks * 256, 128, 2048);
+        const uint64_t bd = tc::smem_desc(sD_addr + ks * 2 * (kFwdN / 8) * 128, (kFwdN / 8) * 128, 128);
+        tc::mma_f16(tmem, ad, bd, tc::idesc_f16_f32(kFwdM, kFwdN) | (1u << 16), ks > 0);
+      }
+      tc::mma_commit(bar_a);
+    }
+    if (k > 0) {
+      // the cluster's sums of chunk k-2, then this tile's sums of chunk k-1 for the cluster
+      if (k > 1) {
+        cluster_wait();
+        if (ok) reduce_chunk(k - 2);
+      }
+      if (tid < C * kTcK) {
+        const int cc = tid % C, ll = tid / C;
+        long long X = 0, Y = 0;
+#pragma unroll
+        for (int jj = 0; jj < kDigits; ++jj) {
+          const longlong2 sv = reinterpret_cast<const longlong2*>(stage)[(ll * kDigits + jj) * 8 + cc];
+          X += sv.x;
+          Y += sv.y;
+        }
+        reinterpret_cast<longlong2*>(cl)[(((k - 1) & 1) * kTcK + ll) * 8 + cc] = make_longlong2(X, Y);
+      }
+      __syncthreads();                       // the staging area is read: the next read-back may write it
+      cluster_arrive();
+    }
+  }
+  cluster_wait();
+  if (ok) reduce_chunk(nchunks - 1);
+  cluster_arrive();                          // peers may still read this CTA's shared memory
+  cluster_wait();
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem, kFwdTmemCols);
+  }
+}
+
+// Grid: x = (rank of m) * ntiles + tile (a cluster of ntiles CTAs per order), y = n index,
+// z = batch group.  The launch's rings [row0, row0 + nrows) are the tiles of 128.
+template <int NB, bool PAIR>
+__global__ void __launch_bounds__(kTcRings, 3) theta_forward_tc_kernel(FwdArgs a, int ntiles) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const int L = a.L;
+  const int rank = a.rank0 + (int)(blockIdx.x / ntiles), tile = blockIdx.x % ntiles;
+  const int m = a.mpos ? rank : m_of_rank(rank);
+  const int ni = PAIR ? (a.nN - 1) / 2 + (int)blockIdx.y : (int)blockIdx.y;
+  const int n = ni - (a.nN - 1) / 2;
+  const int l0 = a.seed[(size_t)ni * (2 * L - 1) + m + L - 1].l0;
+  // the whole cluster leaves together (uniform over its CTAs)
+  if ((PAIR && n == 0 && m < 0)) return;
+  if (l0 >= L) {
+    if (tile == 0) {
+      constexpr int NBX = PAIR ? 2 * NB : NB;
+      for (int q = threadIdx.x; q < NBX * L; q += blockDim.x) {
+        const int b = q / L, j = q % L;
+        const Slot sl = slot_of<NB, PAIR>(b, blockIdx.z * NB, a.nsig, a.nN, ni, m, n, L);
+        if (sl.sig_off >= 0)
+          reinterpret_cast<double2*>(a.flm)[((size_t)sl.sig_off * L + j) * a.flm_ld + sl.m + a.flm_c0] =
+              make_double2(0.0, 0.0);
+      }
+    }
+    return;
+  }
+  const int t_lo = a.row0 + tile * kTcRings, t_hi = min(a.row0 + a.nrows, t_lo + kTcRings) - 1;
+  const bool diff = a.ring[t_lo].diff || a.ring[t_hi].diff;
+  if (diff) tc_forward_body<NB, PAIR, true>(a, m, ni, n, tile, ntiles, l0, smem);
+  else tc_forward_body<NB, PAIR, false>(a, m, ni, n, tile, ntiles, l0, smem);
+}
+
+template <int NB, bool PAIR>
+cudaError_t launch_fwd_tc(const FwdArgs& a, cudaStream_t st) {
+  static_assert(kFwdSmemBytes <= kFwdSmemRequest, "shared memory layout");
+  const int ntiles = (a.nrows + kTcRings - 1) / kTcRings;
+  if (ntiles == 0) return cudaSuccess;
+  if (ntiles > kFwdMaxTiles) return cudaErrorInvalidValue;
+  auto kern = theta_forward_tc_kernel<NB, PAIR>;
+  cudaError_t e = set_dynamic_smem((const void*)kern, kFwdSmemRequest);
+  if (e != cudaSuccess) return e;
+  if (ntiles > 8) {
+    static bool nonportable_set[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && !nonportable_set[dev]) {
+      e = cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+      if (e != cudaSuccess) return e;
+      nonportable_set[dev] = true;
+    }
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(a.nrank * ntiles, PAIR ? (a.nN + 1) / 2 : a.nN, (a.nsig + NB - 1) / NB);
+  cfg.blockDim = dim3(kTcRings, 1, 1);
+  cfg.dynamicSmemBytes = kFwdSmemRequest;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)ntiles;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  e = cudaLaunchKernelEx(&cfg, kern, a, ntiles);
+  if (e != cudaSuccess) return e;
   return launched();
 }
 
@@ -424,6 +865,19 @@ cudaError_t launch_theta_inverse_tc(const Plan& p, const InvArgs& a, cudaStream_
   if (a.nsig >= 4) return launch_inv_tc<4, false>(a, st);
   if (a.nsig >= 2) return launch_inv_tc<2, false>(a, st);
   return launch_inv_tc<1, false>(a, st);
+}
+
+// Forward theta stage on the tensor cores, for launches of at most 16 tiles of 128 rings (2048
+// rings) written straight to flm; other launches return cudaErrorNotSupported.
+cudaError_t launch_theta_forward_tc(const Plan& p, const FwdArgs& a, cudaStream_t st) {
+  if (a.part || (a.nrows + kTcRings - 1) / kTcRings > kFwdMaxTiles) return cudaErrorNotSupported;
+  if (paired_plan(p)) {
+    if (a.nsig >= 2) return launch_fwd_tc<2, true>(a, st);
+    return launch_fwd_tc<1, true>(a, st);
+  }
+  if (a.nsig >= 4) return launch_fwd_tc<4, false>(a, st);
+  if (a.nsig >= 2) return launch_fwd_tc<2, false>(a, st);
+  return launch_fwd_tc<1, false>(a, st);
 }
 
 int device_status(int device, bool clear, int* status) {

@@ -131,3 +131,57 @@ def test_tc_more_than_1024_degrees_per_order():
     assert rel_max(to_np(f)[:, rings], ref) <= TOL64
     assert rel_max(to_np(f), to_np(fma.inverse(x))) <= 1e-13
     assert status_ok()
+
+
+# ---- the forward theta stage: the contraction over the rings, summed over a cluster of tiles
+@pytest.mark.parametrize("L,spin,batch", [(1, 0, 1), (2, 1, 2), (5, 0, 3), (17, -3, 1), (33, 2, 5),
+                                          (64, 0, 2), (129, 1, 4), (130, 0, 1), (257, -2, 3)])
+def test_tc_forward_theta_matches_oracle_and_fma(L, spin, batch):
+    from oracle.wigner import wigner_d_table
+    tc, fma = plans(L, spin, max_batch=batch)
+    g = synth.signal_gaussian((batch, 2 * L - 1, L), seed=9100 + L)
+    x = to_gpu(g)
+    got = to_np(tc.forward_theta(x))
+    D = wigner_d_table(np.arange(L), -spin, mw_thetas(L))
+    ref = np.einsum("bmt,lmt->blm", g, D) * OT.ell_factor(L, spin)[:, None]
+    ref = np.where(OT.coeff_mask(L, -spin), ref, 0)
+    assert rel_max(got, ref) <= TOL64
+    assert rel_max(got, to_np(fma.forward_theta(x))) <= TOL64
+    assert status_ok()
+
+
+@pytest.mark.parametrize("L,spin", [(16, 0), (33, -1), (64, 2), (96, 0)])
+def test_tc_forward_arbitrary_samples_matches_oracle(L, spin):
+    tc, _ = plans(L, spin, max_batch=2)
+    f = synth.signal_gaussian((2, L, 2 * L - 1), seed=9200 + L)
+    assert rel_max(to_np(tc.forward(to_gpu(f))), OT.forward(f, L, spin)) <= TOL64
+    assert status_ok()
+
+
+@pytest.mark.parametrize("L,spin,B", [(1024, 2, 4), (2048, 0, 1)])
+def test_tc_forward_full_size_agrees_with_fma(L, spin, B):
+    """The bench workload (8 tiles per order) and L = 2048 spin 0 (16 tiles, the largest
+    cluster): tensor-core and FMA-pipe forwards agree, and the tensor-core forward is bitwise
+    repeatable."""
+    tc, fma = plans(L, spin, max_batch=B)
+    f = to_gpu(synth.signal_gaussian((B, L, 2 * L - 1), seed=9300 + L))
+    a = tc.forward(f)
+    assert rel_max(to_np(a), to_np(fma.forward(f))) <= 1e-13
+    assert torch.equal(a, tc.forward(f))
+    assert status_ok()
+
+
+def test_tc_forward_round_trip_wigner_and_samplings():
+    from paper_2311_14670_gb300 import Plan
+    for kw, L in [(dict(N=3), 40), (dict(spin=1, sampling="dh"), 48), (dict(spin=-2, sampling="mwss"), 48),
+                  (dict(real=True), 48)]:
+        p = Plan(L, max_batch=2, **kw)
+        if kw.get("N"):
+            c = synth.flmn_gaussian(L, kw["N"], 2, seed=L)
+        elif kw.get("real"):
+            c = synth.flm_real_gaussian(L, 2, seed=L)
+        else:
+            c = synth.flm_gaussian(L, kw["spin"], 2, seed=L)
+        back = to_np(p.forward(p.inverse(to_gpu(c))))
+        assert rel_max(back, c) <= TOL64, kw
+    assert status_ok()

@@ -90,7 +90,8 @@ FP32_LANES_PER_SM_CLK = 128
 
 
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "theta_traffic.json")
-KERNEL_SOURCES = ["theta_kernels.cu", "theta_common.cuh", "s2gb_internal.h", "dd.cuh"]
+KERNEL_SOURCES = ["theta_kernels.cu", "theta_common.cuh", "s2gb_internal.h", "dd.cuh", "theta_tc.cu",
+                  "tc_common.cuh"]
 
 
 def kernel_source_hash() -> str:
@@ -126,6 +127,14 @@ def algorithmic_flops(L: int, n_list, R: int, batch: int, real: bool = False, pa
     pairs = L * (L + 1) // 2 if real else sum(L * L - n * n for n in n_list)
     chains = (pairs + (L if 0 in n_list else 0)) // 2 if paired else pairs
     return float(R) * (5.0 * chains + 4.0 * batch * pairs)
+
+
+def recursion_flops(L: int, n_list, R: int, real: bool = False, paired: bool = False) -> float:
+    """Per launch of one theta kernel: the recursion alone, 5 flops (FMA = 2) per chain step.
+    With the contraction on the tensor cores this is the work left to the float64 pipe."""
+    pairs = L * (L + 1) // 2 if real else sum(L * L - n * n for n in n_list)
+    chains = (pairs + (L if 0 in n_list else 0)) // 2 if paired else pairs
+    return float(R) * 5.0 * chains
 
 
 def measured_fma_peak(precision: str, dev) -> dict:
@@ -418,7 +427,9 @@ def run_ours(args, world, rank, local):
             torch.cuda.synchronize(dev)
             kms = a.elapsed_time(b) / reps
             flops = algorithmic_flops(L, n_list, R, B, real, paired=plan.paired)
-            kern[name] = {"ms": kms, "flops": flops, "tflops": flops / (kms * 1e-3) / 1e12}
+            rflops = recursion_flops(L, n_list, R, real, paired=plan.paired)
+            kern[name] = {"ms": kms, "flops": flops, "tflops": flops / (kms * 1e-3) / 1e12,
+                          "recursion_flops": rflops, "recursion_tflops": rflops / (kms * 1e-3) / 1e12}
 
     # the step split into the two theta kernels and everything else (phi / theta-direction FFTs on
     # cuFFT, glue kernels): per step, from the separately timed theta kernels
@@ -444,11 +455,18 @@ def run_ours(args, world, rank, local):
     nominal = meas["sms"] * lanes * 2 * sm_max * 1e6 / 1e12    # TFLOP/s
     peak = meas["tflops"]
     roof = None
+    # float64 plans whose contraction runs on the tensor cores: the float64 pipe runs the recursion
+    # only, so the roofline counts the recursion's flops against it; otherwise the whole (5 + 4B)
+    tensor = precision == "fp64" and not plan.precompute and not plan.mrecursion and not plan.fma_contraction
     if kern:
         dom = max(kern, key=lambda k: kern[k]["ms"])
-        ach = kern[dom]["tflops"]
+        ach = kern[dom]["recursion_tflops"] if tensor else kern[dom]["tflops"]
         roof = {"bound": "alu", "kernel": dom, "achieved": round(ach, 4), "peak": round(peak, 4),
                 "unit": "TFLOP/s", "frac": round(ach / peak, 4),
+                "work": ("recursion: 5 flops per (l, m, theta) chain step on the float64 pipe; the "
+                         "contraction (4B flops per element) runs on the tensor cores as exact float16 "
+                         "digit products" if tensor else "(5 + 4B) flops per (l, m, theta) element"),
+                "algorithmic_tflops_5_plus_4B": round(kern[dom]["tflops"], 4),
                 "traffic": profiled_traffic(args.workload, dom) if precision == "fp64" else None,
                 "peak_basis": f"{precision.upper()} FMA pipe, measured on this GPU: {meas['how']}",
                 "peak_nominal": round(nominal, 4),
@@ -531,14 +549,18 @@ def l2048_records(dev, peak_tflops: float, steps: int = 5, warmup: int = 3) -> d
         ms = timed(rt, steps)
         err = float((y - x).abs().max() / x.abs().max())
         flops = algorithmic_flops(L, [-spin], L, 1, paired=plan.paired)
+        rflops = recursion_flops(L, [-spin], L, paired=plan.paired)
         ti = timed(lambda: plan.inverse_theta(x, out=ft), steps)
         tf = timed(lambda: plan.forward_theta(g, out=fl), steps)
         out[f"s{spin}b1"] = {
             "roundtrip_ms": round(ms, 3), "transforms_per_s": round(2 / (ms * 1e-3), 3),
             "theta_inverse_ms": round(ti, 3), "theta_forward_ms": round(tf, 3),
-            "theta_flops_per_launch": flops, "paired": plan.paired,
-            "frac_theta_inverse": round(flops / (ti * 1e-3) / 1e12 / peak_tflops, 4),
-            "frac_theta_forward": round(flops / (tf * 1e-3) / 1e12 / peak_tflops, 4),
+            "theta_flops_per_launch": flops, "recursion_flops_per_launch": rflops, "paired": plan.paired,
+            # the float64 pipe runs the recursion (the contraction is on the tensor cores)
+            "frac_theta_inverse": round(rflops / (ti * 1e-3) / 1e12 / peak_tflops, 4),
+            "frac_theta_forward": round(rflops / (tf * 1e-3) / 1e12 / peak_tflops, 4),
+            "algorithmic_tflops_inverse": round(flops / (ti * 1e-3) / 1e12, 4),
+            "algorithmic_tflops_forward": round(flops / (tf * 1e-3) / 1e12, 4),
             "roundtrip_rel_max_err": err}
         del plan, ws
         torch.cuda.empty_cache()

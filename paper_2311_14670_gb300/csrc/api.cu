@@ -239,6 +239,53 @@ int gamma_dft(Plan& p, const void* in, void* out, int batch, void* work, cudaStr
   return S2GB_OK;
 }
 
+// The forward's theta-direction operator as matrices (tensor-core MW / MWSS plans, R <=
+// kOpMaxRings): the responses of the FFT operator above to unit vectors at every torus point give
+// Op (R x TS, the rows t < R the theta kernel reads); the torus extension then folds Op into the
+// two R x R matrices Q_sigma, kept as float16 digit tiles with one exponent per row.
+int build_theta_operator(Plan& p) {
+  if (!p.tc || p.TS == 0 || p.R > kOpMaxRings) return S2GB_OK;
+  p.op_nt = (p.R + 127) / 128;
+  p.op_nk = (p.R + 15) / 16;
+  const size_t dig_bytes = (size_t)2 * p.op_nt * p.op_nk * 7 * 128 * 16 * sizeof(unsigned short);
+  const size_t rexp_bytes = (size_t)2 * p.op_nt * 128 * sizeof(int);
+  if (cudaMalloc((void**)&p.op_dig, dig_bytes) != cudaSuccess) return S2GB_ENOMEM;
+  if (cudaMalloc((void**)&p.op_rexp, rexp_bytes) != cudaSuccess) return S2GB_ENOMEM;
+  if (cudaMemset(p.op_dig, 0, dig_bytes) != cudaSuccess) return S2GB_ECUDA;
+  void* tmp = nullptr;
+  double* Op = nullptr;
+  const size_t wsb = workspace_bytes(p, 1);
+  if (cudaMalloc(&tmp, wsb) != cudaSuccess) return S2GB_ENOMEM;
+  if (cudaMalloc((void**)&Op, (size_t)p.R * p.TS * sizeof(double)) != cudaSuccess) {
+    cudaFree(tmp);
+    return S2GB_ENOMEM;
+  }
+  int rc = S2GB_OK;
+  {
+    const Workspace w = carve(p, tmp, 1);
+    FftRunner fr{p, 0, w.fft, 1};
+    const int rows = p.nN * p.MR;
+    for (int i0 = 0; i0 < p.TS && rc == S2GB_OK; i0 += rows) {
+      rc = cuda_rc(launch_op_identity(w.B, rows, p.TS, i0, 0));
+      if (rc == S2GB_OK) rc = theta_weight_operator(p, fr, w.A, w.B, p.nN);
+      if (rc == S2GB_OK) rc = cuda_rc(launch_op_collect(w.B, Op, rows, p.R, p.TS, i0, 0));
+    }
+    if (rc == S2GB_OK) rc = cuda_rc(launch_op_digits(p, Op, 0));
+    if (rc == S2GB_OK && cudaDeviceSynchronize() != cudaSuccess) rc = S2GB_ECUDA;
+  }
+  cudaFree(Op);
+  cudaFree(tmp);
+  if (rc != S2GB_OK) return rc;
+  p.tc_op = true;
+  p.device_bytes += dig_bytes + rexp_bytes;
+  return S2GB_OK;
+}
+
+// Scratch for the operator's per-column exponents: past the spectra in region A.
+int* operator_cexp(const Plan& p, const Workspace& w, int S, size_t fw) {
+  return reinterpret_cast<int*>(w.A + align256((size_t)S * p.R * fw * 16));
+}
+
 // Orders |m| in [mlo, mhi) of the forward transform: every stage before the theta kernel runs in
 // full, the theta kernel only for those orders (flm entries of other orders are not written).
 // MW / MWSS: phi DFT, torus extension, theta-direction quadrature operator, theta kernel over the
@@ -259,8 +306,12 @@ int do_forward(Plan& p, const void* f, void* flm, int batch, const Workspace& w,
   if (p.sampling == S2GB_DH) {
     a = fwd_args(p, w.A, flm, batch, p.scale_fwd, (long long)plane, p.P, 1, 1, 1);
   } else {
-    S2GB_TRY(cuda_rc(launch_extend(p, w.A, w.B, S, st)));
-    S2GB_TRY(theta_weight_operator(p, fr, w.A, w.B, S));
+    if (p.tc_op) {
+      S2GB_TRY(cuda_rc(launch_operator_tc(p, w.A, w.B, operator_cexp(p, w, S, p.P), S, st)));
+    } else {
+      S2GB_TRY(cuda_rc(launch_extend(p, w.A, w.B, S, st)));
+      S2GB_TRY(theta_weight_operator(p, fr, w.A, w.B, S));
+    }
     a = fwd_args(p, w.B, flm, batch, p.scale_fwd, (long long)p.MR * p.TS, 1, p.TS, 0, 1);
   }
   a.part = w.D;
@@ -343,8 +394,12 @@ int do_forward_real(Plan& p, const void* f, void* flm, int batch, const Workspac
   if (p.sampling == S2GB_DH) {
     a = fwd_args(p, w.A, flm, batch, p.scale_fwd, (long long)(R * L), (long long)L, 1, 1, 1);
   } else {
-    S2GB_TRY(cuda_rc(launch_extend(p, w.A, w.B, batch, st)));
-    S2GB_TRY(theta_weight_operator(p, fr, w.A, w.B, batch));
+    if (p.tc_op) {
+      S2GB_TRY(cuda_rc(launch_operator_tc(p, w.A, w.B, operator_cexp(p, w, batch, L), batch, st)));
+    } else {
+      S2GB_TRY(cuda_rc(launch_extend(p, w.A, w.B, batch, st)));
+      S2GB_TRY(theta_weight_operator(p, fr, w.A, w.B, batch));
+    }
     a = fwd_args(p, w.B, flm, batch, p.scale_fwd, (long long)(L * TS), 1, (long long)TS, 1, 1);
   }
   a.part = w.D;
@@ -498,6 +553,7 @@ int plan_create_impl(s2gb_plan* out, int L, int spin, int N, int sampling, int p
   {
     s2gb::DeviceGuard g(device);
     rc = s2gb::make_plan(&p);
+    if (rc == S2GB_OK) rc = s2gb::build_theta_operator(p);
     if (rc != S2GB_OK) s2gb::free_plan(&p);
   }
   if (rc != S2GB_OK) {

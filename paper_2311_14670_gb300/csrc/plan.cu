@@ -506,6 +506,8 @@ void free_plan(Plan* p) {
   cudaFree(p->n_of);
   cudaFree(p->mrec_ab);
   cudaFree(p->csc);
+  cudaFree(p->op_dig);
+  cudaFree(p->op_rexp);
   for (int q = 0; q < 2; ++q) {
     if (p->fft_made[q]) {
       cufftDestroy(p->fft_phi[q]);

@@ -49,6 +49,7 @@ constexpr int kCoefPerStep = 6;  // A, C, K_north, K_south, Kd_north, Kd_south (
 constexpr int kCoefPerStepN = 10;
 constexpr int kNormBlock = 8;    // normalisation block length (steps), aligned at l0
 constexpr int kFwdChunk = 2048;  // rings per CTA of the forward theta kernel
+constexpr int kOpMaxRings = 2304;  // rings up to which the theta-direction operator is a matrix
 
 struct Plan {
   int L = 0, spin = 0, N = 0, precision = 0, max_batch = 0, device = 0;
@@ -69,6 +70,15 @@ struct Plan {
   bool mrec = false;  // theta stages by the recursion over the order m (theta_mrec.cu)
   bool tc = false;    // float64 on-the-fly plans: the theta contraction on the tensor cores
                       // (theta_tc.cu); false: on the float64 FMA pipe (theta_kernels.cu)
+  // The forward's theta-direction quadrature operator (torus extension, then the FFT operator of
+  // api.cu's theta_weight_operator, restricted to the R rings) is linear and the same for every
+  // order row up to the parity sigma = (-1)^(m-n): two real R x R matrices Q_sigma.  Tensor-core MW /
+  // MWSS plans with R <= kOpMaxRings keep them as float16 digit tiles and apply them on the tensor
+  // cores (theta_tc.cu) instead of the FFTs.
+  bool tc_op = false;
+  unsigned short* op_dig = nullptr;   // [2][op_nt][op_nk][7][128 x 16] K-major digit tiles
+  int* op_rexp = nullptr;             // [2][op_nt * 128]: |Q_sigma[t][.]| < 2^(op_rexp - 1)
+  int op_nt = 0, op_nk = 0;           // 128-row tiles over t, 16-column chunks over t'
   int cap_n = 0;    // rings [ring0, cap_n) and [cap_s, ring0 + nint) use the difference form
   int cap_s = 0;
   int fwd_parts = 1;  // forward theta stage in one launch (nint <= kFwdChunk) or in ring chunks
@@ -223,6 +233,16 @@ cudaError_t launch_theta_inverse_f32(const Plan& p, const InvArgs& a, cudaStream
 // float64 theta stages with the contraction on the tensor cores (theta_tc.cu)
 cudaError_t launch_theta_inverse_tc(const Plan& p, const InvArgs& a, cudaStream_t st);
 cudaError_t launch_theta_forward_tc(const Plan& p, const FwdArgs& a, cudaStream_t st);
+// plan creation: the operator matrices from the operator's responses (theta_tc.cu)
+//   op_identity: rows r < rows of G [rows][TS] = unit vectors at torus points i0 + r
+//   op_collect:  Op[t][i0 + r] = Re H[r][t] for t < R
+//   op_digits:   Q_sigma rows from Op (R x TS), their exponents and digit tiles into the plan
+cudaError_t launch_op_identity(void* G, int rows, int TS, int i0, cudaStream_t st);
+cudaError_t launch_op_collect(const void* H, double* Op, int rows, int R, int TS, int i0, cudaStream_t st);
+cudaError_t launch_op_digits(const Plan& p, const double* Op, cudaStream_t st);
+// forward: H[s][m + mo][t] (t < R, rows of TS) = sum_t' Q_sigma[t][t'] F[s][t'][k(m)], with the
+// per-column exponents in `cexp` ([S][MR][2] ints of scratch)
+cudaError_t launch_operator_tc(const Plan& p, const void* F, void* H, int* cexp, int S, cudaStream_t st);
 cudaError_t launch_theta_forward_f32(const Plan& p, const FwdArgs& a, cudaStream_t st);
 
 // ---- glue kernels (glue.cu) ----

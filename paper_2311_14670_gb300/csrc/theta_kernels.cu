@@ -455,7 +455,9 @@ cudaError_t launch_theta_forward_rings(const Plan& p, const FwdArgs& a, cudaStre
   if (p.mrec) return launch_theta_forward_mrec(p, a, st);
   if (a.dtab) return launch_theta_forward_pre(p, a, st);
   if (p.precision == S2GB_FP32) return launch_theta_forward_f32(p, a, st);
-  if (p.tc && p.nint <= kFwdChunk) {      // contraction on the tensor cores: one cluster per order
+  // contraction on the tensor cores: one cluster per order (with no recursion rings -- MWSS at
+  // L = 1 -- the FMA-pipe kernel writes the zero sums that the pole kernel then adds to)
+  if (p.tc && p.nint > 0 && p.nint <= kFwdChunk) {
     FwdArgs b = a;
     b.row0 = p.ring0;
     b.nrows = p.nint;

@@ -11,12 +11,12 @@
 // Oishi, Rump, Numer. Algorithms 59, 2012; on float16 tensor cores: Mukunoki, Ozaki, Ogita,
 // Imamura, 2020):
 //
-//   * every recursion value becomes a fixed-point integer qa = trunc(x 2^(55 - rho_l)), with rho_l a
+//   * every recursion value becomes a fixed-point integer qa = round(x 2^(55 - rho_l)), with rho_l a
 //     power-of-two bound of |x| at degree l (|u^l| <= 1/gamma_l for the block-normalised values,
-//     |d| <= 1 in the difference form), and every coefficient qh = trunc(h' 2^(55 - eps_c)) with one
+//     |d| <= 1 in the difference form), and every coefficient qh = round(h' 2^(55 - eps_c)) with one
 //     exponent eps_c per column (a bound over the degrees of the CTA's order); the scale 2^rho_l
 //     moves into the coefficient of degree l, so the product is unchanged;
-//   * |q| < 2^54 is written in 7 balanced base-256 digits in [-128, 127] (adding 0x80 to every
+//   * |q| <= 2^54 is written in 7 balanced base-256 digits in [-128, 127] (adding 0x80 to every
 //     byte of the two's complement integer and subtracting it again digit by digit), each digit
 //     exact in float16;
 //   * one tcgen05.mma per digit i of the d-values multiplies the i-th digit matrix (128 rings x
@@ -75,16 +75,18 @@ __device__ __forceinline__ int kmajor_off(int row, int k) {
   return (row >> 3) * 256 + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2;
 }
 
-// trunc(|x| 2^(55 - rho)) with the sign of x, plus 0x0080808080808080: byte p (p = 0..6) of the
+// round(|x| 2^(55 - rho)) with the sign of x, plus 0x0080808080808080: byte p (p = 0..6) of the
 // result is the balanced base-256 digit of weight 256^p, offset by 128.  Needs |x| < 2^(rho - 1).
-// Zero and subnormal x give the digits of 0.
+// Rounding to nearest (not truncation) keeps the split unbiased, so that the errors of a sum of
+// many split values do not add up in one direction.  Zero and subnormal x give the digits of 0.
 __device__ __forceinline__ uint2 offset_digits(double x, int rho) {
   const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
   const int ex = (int)((hi >> 20) & 0x7ffu);
-  const uint32_t sh = ex == 0 ? 64u : (uint32_t)(1023 + rho - ex);
+  const uint32_t sh = ex == 0 ? 64u : (uint32_t)(1023 + rho - ex);   // >= 2 when |x| < 2^(rho-1)
   const uint64_t m = ((((uint64_t)((hi & 0xfffffu) | 0x100000u)) << 32) | lo) << 3;   // 56 bits
   uint64_t q;
-  asm("shr.b64 %0, %1, %2;" : "=l"(q) : "l"(m), "r"(sh));
+  asm("shr.b64 %0, %1, %2;" : "=l"(q) : "l"(m), "r"(sh - 1));         // one fraction bit kept
+  q = (q + 1) >> 1;
   const uint64_t neg = (uint64_t)(int64_t)((int32_t)hi >> 31);
   q = ((q ^ neg) - neg) + 0x0080808080808080ull;
   return make_uint2((uint32_t)q, (uint32_t)(q >> 32));
@@ -855,6 +857,290 @@ cudaError_t launch_fwd_tc(const FwdArgs& a, cudaStream_t st) {
   return launched();
 }
 
+// =============================================================================================
+// The forward's theta-direction quadrature operator on the tensor cores.
+//
+// For one order row the operator maps the ring values F(theta_t'), t' < R, to the values H(theta_t)
+// the forward theta kernel integrates: the torus extension (Sec. 4.2.2: the reflected ring times
+// sigma = (-1)^(m-n), (1 + sigma)/2 on a self-reflected ring) followed by the FFT operator of the
+// quadrature (weights on a fine grid, projection to the bandlimit), restricted to the R rings.  It
+// is linear, real and the same for every row of a given parity: H = Q_sigma F with two R x R real
+// matrices, built at plan creation from the FFT operator's responses to unit vectors.  Applying
+// them is a GEMM over the rings (K = R): rows t (128 per CTA, the A operand: Q_sigma digits copied
+// per chunk of 16 rings by a TMA bulk copy from the plan's tiles), columns = 8 orders of one parity
+// x (re, im) (the B operand: the spectra split into digits in the CTA), with the digit levels
+// merged in Tensor Memory and read back exactly every 128 rings, as in the inverse theta stage.
+// =============================================================================================
+constexpr int kOpCols = 16;                                   // 8 orders x (re, im)
+constexpr int kOpATile = kDigits * kTcRings * kTcK;           // fp16 elements of one chunk's A
+constexpr int kOpABytes = kOpATile * 2;                       // 28 KiB
+constexpr int kOpBBytes = kDigits * kOpCols * kTcK * 2;       // 3.5 KiB
+constexpr int kOpSmemBytes = 2 * kOpABytes + 2 * kOpBBytes + 256;
+constexpr int kOpSmemRequest = 70 * 1024;                     // three CTAs per SM
+
+__global__ void op_identity_kernel(double2* __restrict__ G, int rows, int TS, int i0) {
+  const size_t total = (size_t)rows * TS;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+    const int c = (int)(idx % TS), r = (int)(idx / TS);
+    G[idx] = make_double2(c == i0 + r ? 1.0 : 0.0, 0.0);
+  }
+}
+
+__global__ void op_collect_kernel(const double2* __restrict__ H, double* __restrict__ Op, int rows, int R, int TS, int i0) {
+  const size_t total = (size_t)rows * R;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+    const int t = (int)(idx % R), r = (int)(idx / R);
+    if (i0 + r < TS) Op[(size_t)t * TS + i0 + r] = H[(size_t)r * TS + t].x;
+  }
+}
+
+// One CTA per (row t, parity): Q_sigma[t][t'] for t' < R from Op, the row's exponent bound, and
+// its digits into the K-major tiles.
+__global__ void __launch_bounds__(128) op_digits_kernel(const double* __restrict__ Op, unsigned short* __restrict__ dig,
+                                                         int* __restrict__ rexp, int R, int TS, int L, int O, int nt, int nk) {
+  const int t = blockIdx.x, par = blockIdx.y;       // par 0: sigma = +1, 1: sigma = -1
+  const double sg = par ? -1.0 : 1.0;
+  __shared__ int emax_s;
+  if (threadIdx.x == 0) emax_s = -100000;
+  __syncthreads();
+  auto q_at = [&](int tp) {
+    if (t >= R) return 0.0;
+    const bool self = (tp == O - tp) || (TS == 2 * L && tp == 0);
+    const double a = Op[(size_t)t * TS + tp];
+    return self ? (par ? 0.0 : a) : fma(sg, Op[(size_t)t * TS + (O - tp)], a);
+  };
+  int e = -100000;
+  for (int tp = threadIdx.x; tp < R; tp += blockDim.x) {
+    const double q = q_at(tp);
+    if (q != 0.0) e = max(e, theta::exp_of(q));
+  }
+  e = __reduce_max_sync(0xffffffffu, e);
+  if ((threadIdx.x & 31) == 0) atomicMax(&emax_s, e);
+  __syncthreads();
+  const int rho = (emax_s < -2000 ? 0 : emax_s) + 2;   // |Q[t][.]| < 2^(rho - 1)
+  if (threadIdx.x == 0) rexp[par * nt * kTcRings + t] = rho;
+  const int tt = t / kTcRings, row = t % kTcRings;
+  for (int tp = threadIdx.x; tp < R; tp += blockDim.x) {
+    const uint2 q = offset_digits(q_at(tp), rho);
+    unsigned short* tile = dig + ((size_t)(par * nt + tt) * nk + tp / kTcK) * kOpATile;
+#pragma unroll
+    for (int i = 0; i < kDigits; ++i)
+      tile[i * kTcRings * kTcK + kmajor_off(row, tp % kTcK) / 2] = digit_half(q, i);
+  }
+}
+
+// cexp[s][r][part] = max over the rings of the exponent of F[s][t'][k(m)] (part 0 re, 1 im)
+__global__ void op_colexp_kernel(const double2* __restrict__ F, int* __restrict__ cexp, int S, int MR, int R,
+                                 int FW, int mo) {
+  const size_t total = (size_t)S * MR;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+    const int r = (int)(idx % MR), s = (int)(idx / MR);
+    const int m = r - mo, k = m >= 0 ? m : m + FW;
+    int er = -100000, ei = -100000;
+    for (int tp = 0; tp < R; ++tp) {
+      const double2 v = F[((size_t)s * R + tp) * FW + k];
+      if (v.x != 0.0) er = max(er, theta::exp_of(v.x));
+      if (v.y != 0.0) ei = max(ei, theta::exp_of(v.y));
+    }
+    cexp[2 * idx] = er;
+    cexp[2 * idx + 1] = ei;
+  }
+}
+
+__device__ __forceinline__ void bulk_copy_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(bar), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               :: "r"(dst), "l"(src), "r"(bytes), "r"(bar) : "memory");
+}
+
+struct OpArgs {
+  const double2* F;        // [S][R][FW] spectra
+  double2* H;              // [S][MR][TS] output rows (t < R written)
+  const int* cexp;         // [S][MR][2]
+  const unsigned short* dig;
+  const int* rexp;
+  const int* n_of;
+  int S, MR, R, FW, TS, mo, nN, L, nt, nk, mlo, mhi, ncol0;   // ncol0: column tiles per parity
+};
+
+// Grid: x = tile of 128 rings t, y = column tile (parity 0 first), z = signal.
+__global__ void __launch_bounds__(kTcRings, 3) theta_operator_tc_kernel(OpArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int tt = blockIdx.x, s = blockIdx.z;
+  const int par = (int)blockIdx.y >= a.ncol0 ? 1 : 0;
+  const int ct = (int)blockIdx.y - par * a.ncol0;
+  const int n = a.n_of[s % a.nN];
+  // orders of this parity class: m = mfirst, mfirst + 2, ...; this CTA's 8 of them
+  const int mfirst = a.mlo + ((((a.mlo - n - par) % 2) + 2) % 2);
+  const int m0 = mfirst + 2 * kOpCols / 2 * ct;
+  if (m0 > a.mhi) return;
+
+  unsigned char* sA = smem;                                   // [2][28 KiB]
+  unsigned char* sB = smem + 2 * kOpABytes;                   // [2][3.5 KiB]
+  uint64_t* full = reinterpret_cast<uint64_t*>(sB + 2 * kOpBBytes);
+  uint64_t* done = full + 2;
+  int* ce_s = reinterpret_cast<int*>(done + 2);               // [16] column exponent bounds
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(ce_s + kOpCols);
+  int* abort_s = reinterpret_cast<int*>(tmem_slot + 1);
+
+  const unsigned short* dig = a.dig + (size_t)(par * a.nt + tt) * a.nk * kOpATile;
+  if (tid == 0) {
+    for (int q = 0; q < 2; ++q) {
+      tc::mbar_init(tc::smem_addr(&full[q]), 1);
+      tc::mbar_init(tc::smem_addr(&done[q]), 1);
+    }
+    tc::mbar_init_fence();
+    *abort_s = 0;
+  }
+  if (warp == 0) tc::tmem_alloc(tc::smem_addr(tmem_slot), kTmemCols);
+  if (tid < kOpCols) {
+    const int m = m0 + 2 * (tid >> 1);
+    int e = -100000;
+    if (m <= a.mhi) e = a.cexp[((size_t)s * a.MR + (m + a.mo)) * 2 + (tid & 1)];
+    ce_s[tid] = (e < -2000 ? 0 : e) + 2;
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t sA_addr = tc::smem_addr(sA), sB_addr = tc::smem_addr(sB);
+  if (tid == 0) bulk_copy_g2s(sA_addr, dig, kOpABytes, tc::smem_addr(&full[0]));
+
+  // this thread's digit-split column and ring half (threads 0..31)
+  const int bn = tid % kOpCols, bh = tid / kOpCols;
+  const int bm = m0 + 2 * (bn >> 1);
+  const bool bact = tid < 2 * kOpCols && bm <= a.mhi;
+  const int bk = bm >= 0 ? bm : bm + a.FW;
+  const double2* Fs = a.F + (size_t)s * a.R * a.FW;
+
+  long long X[kOpCols], Y[kOpCols];
+#pragma unroll
+  for (int c = 0; c < kOpCols; ++c) { X[c] = 0; Y[c] = 0; }
+  int since_reset = 0;
+  bool ok = true;
+  for (int kc = 0; kc < a.nk; ++kc) {
+    const int st = kc & 1;
+    if (tid < 2 * kOpCols) {
+      uint32_t w[kDigits][4];
+      uint2 q0 = make_uint2(0, 0);
+      const int ce = ce_s[bn];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int tp = kc * kTcK + 8 * bh + u;
+        double v = 0.0;
+        if (bact && tp < a.R) {
+          const double2 f = Fs[(size_t)tp * a.FW + bk];
+          v = (bn & 1) ? f.y : f.x;
+        }
+        const uint2 q = offset_digits(v, ce);
+        if (u & 1) {
+          w[0][u >> 1] = digit_pair(q0.y, q.y, 2);
+          w[1][u >> 1] = digit_pair(q0.y, q.y, 1);
+          w[2][u >> 1] = digit_pair(q0.y, q.y, 0);
+          w[3][u >> 1] = digit_pair(q0.x, q.x, 3);
+          w[4][u >> 1] = digit_pair(q0.x, q.x, 2);
+          w[5][u >> 1] = digit_pair(q0.x, q.x, 1);
+          w[6][u >> 1] = digit_pair(q0.x, q.x, 0);
+        } else {
+          q0 = q;
+        }
+      }
+      // this stage's previous MMAs (chunk kc - 2) must be done before it is rewritten
+      if (kc >= 2 && !tc::mbar_wait(tc::smem_addr(&done[st]), (uint32_t)(((kc >> 1) - 1) & 1))) {
+        set_status(tc::kStatusMmaWait);
+        *abort_s = 1;
+      }
+      unsigned char* bst = sB + st * kOpBBytes;
+#pragma unroll
+      for (int i = 0; i < kDigits; ++i)
+        *reinterpret_cast<uint4*>(bst + kmajor_off(kLevelCols * i + bn, 8 * bh)) =
+            make_uint4(w[i][0], w[i][1], w[i][2], w[i][3]);
+    }
+    tc::fence_proxy_async();
+    __syncthreads();
+    if (*abort_s) { ok = false; break; }
+    if (tid == 0) {
+      if (!tc::mbar_wait(tc::smem_addr(&full[st]), (uint32_t)((kc >> 1) & 1))) {
+        set_status(tc::kStatusMmaWait);
+        *abort_s = 1;
+      } else {
+        tc::fence_after_sync();
+#pragma unroll
+        for (int i = 0; i < kDigits; ++i) {
+          const uint64_t ad = tc::smem_desc(sA_addr + st * kOpABytes + i * kATileBytes, 128, 256);
+          const uint64_t bd = tc::smem_desc(sB_addr + st * kOpBBytes, 128, 256);
+          tc::mma_f16(tmem + kLevelCols * i, ad, bd, tc::idesc_f16_f32(kTcRings, kLevelCols * (kDigits - i)),
+                      since_reset > 0 || i > 0);
+        }
+        tc::mma_commit(tc::smem_addr(&done[st]));
+        // the next chunk's matrix digits into the other stage, once that stage's MMAs are done
+        if (kc + 1 < a.nk) {
+          const int sn = (kc + 1) & 1;
+          if (kc >= 1 && !tc::mbar_wait(tc::smem_addr(&done[sn]), (uint32_t)((((kc + 1) >> 1) - 1) & 1))) {
+            set_status(tc::kStatusMmaWait);
+            *abort_s = 1;
+          } else {
+            bulk_copy_g2s(sA_addr + sn * kOpABytes, dig + (size_t)(kc + 1) * kOpATile, kOpABytes,
+                          tc::smem_addr(&full[sn]));
+          }
+        }
+      }
+    }
+    ++since_reset;
+    if (since_reset == kDrainChunks || kc == a.nk - 1) {
+      if (!tc::mbar_wait(tc::smem_addr(&done[st]), (uint32_t)((kc >> 1) & 1))) {
+        set_status(tc::kStatusMmaWait);
+        ok = false;
+      }
+      tc::fence_after_sync();
+      if (__all_sync(0xffffffffu, ok)) {
+        const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          int lam[kDigits][8];
+#pragma unroll
+          for (int lv = 0; lv < kDigits; ++lv) {
+            uint32_t r[8];
+            tc::tmem_ld8(trow + (uint32_t)(kLevelCols * lv + 8 * h), r);
+            tc::tmem_ld_wait();
+#pragma unroll
+            for (int e = 0; e < 8; ++e) lam[lv][e] = __float2int_rn(__uint_as_float(r[e]));
+          }
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            X[8 * h + e] += ((long long)lam[0][e] << 24) + ((long long)lam[1][e] << 16) +
+                            ((long long)lam[2][e] << 8) + (long long)lam[3][e];
+            Y[8 * h + e] += ((long long)lam[4][e] << 16) + ((long long)lam[5][e] << 8) + (long long)lam[6][e];
+          }
+        }
+      }
+      tc::fence_before_sync();
+      since_reset = 0;
+      if (!__syncthreads_and(ok)) { ok = false; break; }
+    }
+  }
+  // H[s][m + mo][t] = 2^(rho_t + eps_c - 38) (X + 2^-24 Y), re and im
+  const int t = tt * kTcRings + tid;
+  if (ok && t < a.R) {
+    const int rho = a.rexp[par * a.nt * kTcRings + t];
+#pragma unroll
+    for (int o = 0; o < kOpCols / 2; ++o) {
+      const int m = m0 + 2 * o;
+      if (m > a.mhi) break;
+      const double re = ldexp(fma((double)Y[2 * o], 0x1p-24, (double)X[2 * o]), rho + ce_s[2 * o] - 38);
+      const double im = ldexp(fma((double)Y[2 * o + 1], 0x1p-24, (double)X[2 * o + 1]), rho + ce_s[2 * o + 1] - 38);
+      a.H[((size_t)s * a.MR + (m + a.mo)) * a.TS + t] = make_double2(re, im);
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem, kTmemCols);
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_theta_inverse_tc(const Plan& p, const InvArgs& a, cudaStream_t st) {
@@ -878,6 +1164,47 @@ cudaError_t launch_theta_forward_tc(const Plan& p, const FwdArgs& a, cudaStream_
   if (a.nsig >= 4) return launch_fwd_tc<4, false>(a, st);
   if (a.nsig >= 2) return launch_fwd_tc<2, false>(a, st);
   return launch_fwd_tc<1, false>(a, st);
+}
+
+cudaError_t launch_op_identity(void* G, int rows, int TS, int i0, cudaStream_t st) {
+  op_identity_kernel<<<1024, 256, 0, st>>>(reinterpret_cast<double2*>(G), rows, TS, i0);
+  return launched();
+}
+
+cudaError_t launch_op_collect(const void* H, double* Op, int rows, int R, int TS, int i0, cudaStream_t st) {
+  op_collect_kernel<<<1024, 256, 0, st>>>(reinterpret_cast<const double2*>(H), Op, rows, R, TS, i0);
+  return launched();
+}
+
+cudaError_t launch_op_digits(const Plan& p, const double* Op, cudaStream_t st) {
+  const int O = p.sampling == S2GB_MWSS ? 2 * p.L : 2 * p.L - 2;
+  op_digits_kernel<<<dim3(p.op_nt * kTcRings, 2), 128, 0, st>>>(Op, p.op_dig, p.op_rexp, p.R, p.TS, p.L, O,
+                                                               p.op_nt, p.op_nk);
+  return launched();
+}
+
+cudaError_t launch_operator_tc(const Plan& p, const void* F, void* H, int* cexp, int S, cudaStream_t st) {
+  static_assert(kOpSmemBytes <= kOpSmemRequest, "shared memory layout");
+  OpArgs a;
+  a.F = reinterpret_cast<const double2*>(F);
+  a.H = reinterpret_cast<double2*>(H);
+  a.cexp = cexp;
+  a.dig = p.op_dig;
+  a.rexp = p.op_rexp;
+  a.n_of = p.n_of;
+  a.S = S; a.MR = p.MR; a.R = p.R; a.TS = p.TS; a.nN = p.nN; a.L = p.L; a.nt = p.op_nt; a.nk = p.op_nk;
+  a.FW = p.real ? p.L : p.P;
+  a.mo = p.real ? 0 : p.L - 1;
+  a.mlo = p.real ? 0 : -(p.L - 1);
+  a.mhi = p.L - 1;
+  a.ncol0 = (p.L + kOpCols / 2 - 1) / (kOpCols / 2);     // >= ceil(#orders of a parity / 8)
+  op_colexp_kernel<<<1024, 256, 0, st>>>(a.F, cexp, S, p.MR, p.R, a.FW, a.mo);
+  cudaError_t e = launched();
+  if (e != cudaSuccess) return e;
+  e = set_dynamic_smem((const void*)theta_operator_tc_kernel, kOpSmemRequest);
+  if (e != cudaSuccess) return e;
+  theta_operator_tc_kernel<<<dim3(p.op_nt, 2 * a.ncol0, S), kTcRings, kOpSmemRequest, st>>>(a);
+  return launched();
 }
 
 int device_status(int device, bool clear, int* status) {

@@ -250,17 +250,20 @@ def test_L8192_round_trip():
 
 def test_kernel_launch_counter_counts_each_stage():
     """s2gb_kernels_launched counts this library's own launches: the sphere inverse is one theta
-    kernel (then cuFFT), the forward four glue kernels plus the theta kernel; above L = 2048 the
-    forward theta stage is several ring-chunk launches and one fixed-order sum."""
+    kernel (then cuFFT); the forward is the theta-direction operator on the tensor cores (column
+    exponents + the operator GEMM) plus the theta kernel, or, with the contraction on the FMA pipe,
+    four glue kernels around the operator's FFTs plus the theta kernel; above L = 2048 the forward
+    theta stage is several ring-chunk launches and one fixed-order sum."""
+    from paper_2311_14670_gb300 import Plan
     from paper_2311_14670_gb300 import _native as nat
-    p = plan(64, 2)
     x = to_gpu(synth.flm_gaussian(64, 2, 1, seed=5))
-    k0 = nat.kernels_launched()
-    f = p.inverse(x)
-    k1 = nat.kernels_launched()
-    p.forward(f)
-    k2 = nat.kernels_launched()
-    assert (k1 - k0, k2 - k1) == (1, 5)
+    for p, counts in [(plan(64, 2), (1, 3)), (Plan(64, spin=2, fma_contraction=True), (1, 5))]:
+        k0 = nat.kernels_launched()
+        f = p.inverse(x)
+        k1 = nat.kernels_launched()
+        p.forward(f)
+        k2 = nat.kernels_launched()
+        assert (k1 - k0, k2 - k1) == counts
     q = plan(2500, 0)
     g = q.inverse(to_gpu(synth.flm_gaussian(2500, 0, 1, seed=6)))
     k3 = nat.kernels_launched()

@@ -413,37 +413,42 @@ cudaError_t launch_inv_tc(const InvArgs& a, cudaStream_t st) {
 // =============================================================================================
 // Forward theta stage (Sec. 4.1, Eq. disc_sh_expanded) with the contraction over the rings on the
 // tensor cores: flm[l][c] = scale_l sum_t d^l(theta_t) g'_t[c], g' the ring data times the ring
-// weight and the slot sign.  The sum runs over the rings, across the threads of a CTA (one chain,
-// i.e. one ring, per thread) and across the CTAs of the order (tiles of 128 rings).
+// weight and the slot sign.  The sum runs over the rings, across the threads of a CTA (two chains,
+// i.e. two rings, per thread: 256 rings per CTA) and across the CTAs of the order.
 //
 //   * The ring data are split once per CTA into 7 digits per column (rows 8 j + c of the A operand,
-//     M = 64 with the zero digit 7; K = 128 rings), with one exponent per column over all rings of
+//     M = 64 with the zero digit 7; K = 256 rings), with one exponent per column over all rings of
 //     the order, agreed by the CTAs through distributed shared memory.
-//   * Per chunk of 16 degrees the recursion values are split as in the inverse (B operand, K = 128
-//     rings x N = 112 = (digit i, degree l), stored N-major: each thread writes 16-byte rows) and 8
+//   * Per chunk of 16 degrees the recursion values are split as in the inverse (B operand, K = 256
+//     rings x N = 112 = (digit i, degree l), stored N-major: each thread writes 16-byte rows) and 16
 //     MMAs (16 rings each) form every digit product S_ij(c, l) in Tensor Memory.  A tile sums at
-//     most 128 rings: |S_ij| <= 2^21, exact in float32.
+//     most 256 rings: |S_ij| <= 2^22, exact in float32.
 //   * Each accumulator row (j, c) folds its products into two exact 64-bit words per degree,
-//     X = sum_{i+j<=3} 256^(3-i-j) S_ij and Y = sum_{4<=i+j<=6} 256^(6-i-j) S_ij; the rows of a
-//     column are added through shared memory, and the tiles of the order through distributed
-//     shared memory of the thread-block cluster (one cluster per order, up to 16 tiles), in
-//     integers: the result does not depend on the order of the additions.  Tiles in the difference
-//     form (d) and in the block-normalised form (u = d / gamma_l) are summed separately and
-//     combined in float64 with their scales.
+//     X = sum_{i+j<=3} 256^(3-i-j) S_ij and Y = sum_{4<=i+j<=6} 256^(6-i-j) S_ij (a warp holds the
+//     rows of digits 2w and 2w + 1 and reads back only the digits i <= 6 - 2w they need); the rows
+//     of a column are added through shared memory, and the tiles of the order through distributed
+//     shared memory of the thread-block cluster (one cluster per order, up to 8 tiles), in
+//     integers: the result does not depend on the order of the additions.  Tiles in the
+//     difference form (d; the tiles holding a polar cap) and in the block-normalised form (u = d /
+//     gamma_l) are summed separately -- their digits carry different scales -- and combined in
+//     float64.
+//   * The loop is software-pipelined: a chunk's accumulator is read back in the middle of the next
+//     chunk's recursion, and the cluster's sums of chunk k are formed during chunk k + 2.
 // =============================================================================================
 constexpr int kFwdN = kDigits * kTcK;             // 112 = (d digit i, degree l)
 constexpr int kFwdM = 64;                         // rows 8 j + c: coefficient digit j, column c
-constexpr int kFwdMaxTiles = 16;
+constexpr int kFwdRings = 2 * kTcRings;           // rings per CTA (two chains per thread)
+constexpr int kFwdMaxTiles = 8;                   // 2048 rings per order
 constexpr int kFwdTmemCols = 128;
-constexpr int kGBytes = kFwdM * kTcRings * 2;     // 16 KiB
-constexpr int kDBytes = kTcRings * kFwdN * 2;     // 28 KiB
+constexpr int kGBytes = kFwdM * kFwdRings * 2;    // 32 KiB
+constexpr int kDBytes = kFwdRings * kFwdN * 2;    // 56 KiB
 constexpr int kFwdStageOff = kGBytes + kDBytes;                       // [16 l][7 j][8 c] x (X, Y)
-constexpr int kFwdClOff = kFwdStageOff + 8 * kTcK * kDigits * 16;     // [2][16 l][8 c] x (X, Y)
+constexpr int kFwdClOff = kFwdStageOff + 8 * kTcK * kDigits * 16;     // [2 buf][16 l][8 c] x (X, Y)
 constexpr int kFwdCsOff = kFwdClOff + 2 * 8 * kTcK * 16;
 constexpr int kFwdBarOff = kFwdCsOff + 2 * kTcK * kCoefPerStepN * 8;
-constexpr int kFwdMiscOff = kFwdBarOff + 8;       // eps_loc[8], cls, tmem_slot, abort
+constexpr int kFwdMiscOff = kFwdBarOff + 8;       // eps_loc[8], tmem_slot, abort, form
 constexpr int kFwdSmemBytes = kFwdMiscOff + 64;
-constexpr int kFwdSmemRequest = 70 * 1024;        // at most three CTAs (3 x 128 TMEM columns) per SM
+constexpr int kFwdSmemRequest = 112 * 1024;       // two CTAs per SM
 
 __device__ __forceinline__ uint32_t cluster_rank() {
   uint32_t r;
@@ -472,16 +477,23 @@ __device__ __forceinline__ int ld_peer_s32(uint32_t addr) {
   return v;
 }
 
-// Byte offset of (row r, ring k) in the coefficient-digit tile: K-major, 128 rings per row.
+// Byte offset of (row r, ring k) in the coefficient-digit tile: K-major, 256 rings per row.
 __device__ __forceinline__ int gtile_off(int r, int k) {
-  return (r >> 3) * 2048 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
+  return (r >> 3) * (kFwdRings / 8 * 128) + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
 }
 // Byte offset of (ring k, n / 8 = 2 i + degree half) in the d-digit tile: N-major 16-byte rows.
 __device__ __forceinline__ int dtile_off(int k, int n8) {
   return (k >> 3) * (kFwdN / 8) * 128 + n8 * 128 + (k & 7) * 16;
 }
 
-template <int NB, bool PAIR, bool DIFF>
+// Exact integer of a float32 holding an integer of magnitude below 2^22.
+__device__ __forceinline__ int small_int(uint32_t bits) {
+  return (int)(__float_as_uint(__uint_as_float(bits) + 12582912.0f) - 0x4B400000u);
+}
+
+// D0 / D1: the rings of chain 0 (the tile's first 128) / chain 1 run the difference form (the
+// kernel launches D0 == D1: the cluster sums tiles of one form together).
+template <int NB, bool PAIR, bool D0, bool D1>
 __device__ __forceinline__ void tc_forward_body(const FwdArgs& a, int m, int ni, int n, int tile, int ntiles,
                                                 int l0, unsigned char* smem) {
   constexpr int NBX = PAIR ? 2 * NB : NB;
@@ -500,23 +512,32 @@ __device__ __forceinline__ void tc_forward_body(const FwdArgs& a, int m, int ni,
   double* cs = reinterpret_cast<double*>(smem + kFwdCsOff);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kFwdBarOff);
   int* eps_loc = reinterpret_cast<int*>(smem + kFwdMiscOff);
-  int* cls = eps_loc + 8;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(eps_loc + 9);
-  int* abort_s = eps_loc + 10;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(eps_loc + 8);
+  int* abort_s = eps_loc + 9;
+  int* form_s = eps_loc + 10;
   const uint32_t bar_a = tc::smem_addr(bar);
   double2* const outb = reinterpret_cast<double2*>(a.flm);
 
   const double* coef_m = a.coef + ((size_t)ni * T + mi) * (size_t)L * kCoefPerStepN;
   const double* scale = a.scale + (size_t)ni * L;
-  const int t = a.row0 + tile * kTcRings + tid;
-  const bool tact = t < a.row0 + a.nrows;
+  // mirrored rings: chain 0 counts from the first ring of the launch, chain 1 from the last, so
+  // that both polar caps (the difference form) fall in the cluster's first tile
+  int tr[2];
+  bool tact[2];
+  {
+    const int half = (a.nrows + 1) / 2, q = tile * kTcRings + tid;
+    tact[0] = q < half;
+    tact[1] = q < a.nrows - half;
+    tr[0] = a.row0 + q;
+    tr[1] = a.row0 + a.nrows - 1 - q;
+  }
 
   // ---- set-up: barrier, Tensor Memory, the degrees below l0, column exponents over the cluster
   if (tid == 0) {
     tc::mbar_init(bar_a, 1);
     tc::mbar_init_fence();
     *abort_s = 0;
-    *cls = DIFF ? 1 : 0;
+    *form_s = D0 ? 1 : 0;
   }
   if (warp == 0) tc::tmem_alloc(tc::smem_addr(tmem_slot), kFwdTmemCols);
   for (int q = tid; q < kGBytes / 16; q += kTcRings) reinterpret_cast<uint4*>(sG)[q] = make_uint4(0, 0, 0, 0);
@@ -533,25 +554,28 @@ __device__ __forceinline__ void tc_forward_body(const FwdArgs& a, int m, int ni,
     const int j = l0 + q / kCoefPerStepN;
     cs[q] = (j < L) ? coef_m[(size_t)l0 * kCoefPerStepN + q] : 0.0;
   }
-  double2 gv[NBX];
+  double2 gv[2][NBX];
   {
     int emax[C];
 #pragma unroll
     for (int c = 0; c < C; ++c) emax[c] = -100000;
 #pragma unroll
-    for (int b = 0; b < NBX; ++b) {
-      const Slot sl = slot_of<NB, PAIR>(b, sig0, a.nsig, a.nN, ni, m, n, L);
-      double2 g = make_double2(0.0, 0.0);
-      if (tact && sl.sig_off >= 0) {
-        const long long col = a.m_mod ? (sl.m >= 0 ? sl.m : sl.m + a.mmod) : sl.mi;
-        g = reinterpret_cast<const double2*>(a.g)[(size_t)sl.sig_off * a.s_sig + t * a.s_t + col * a.s_m];
-        const double w = (a.use_nu ? a.nu[t] : 1.0) * sl.sign;
-        g.x *= w;
-        g.y *= w;
+    for (int ch = 0; ch < 2; ++ch) {
+#pragma unroll
+      for (int b = 0; b < NBX; ++b) {
+        const Slot sl = slot_of<NB, PAIR>(b, sig0, a.nsig, a.nN, ni, m, n, L);
+        double2 g = make_double2(0.0, 0.0);
+        if (tact[ch] && sl.sig_off >= 0) {
+          const long long col = a.m_mod ? (sl.m >= 0 ? sl.m : sl.m + a.mmod) : sl.mi;
+          g = reinterpret_cast<const double2*>(a.g)[(size_t)sl.sig_off * a.s_sig + tr[ch] * a.s_t + col * a.s_m];
+          const double w = (a.use_nu ? a.nu[tr[ch]] : 1.0) * sl.sign;
+          g.x *= w;
+          g.y *= w;
+        }
+        gv[ch][b] = g;
+        if (g.x != 0.0) emax[2 * b] = max(emax[2 * b], exp_of(g.x));
+        if (g.y != 0.0) emax[2 * b + 1] = max(emax[2 * b + 1], exp_of(g.y));
       }
-      gv[b] = g;
-      if (g.x != 0.0) emax[2 * b] = exp_of(g.x);
-      if (g.y != 0.0) emax[2 * b + 1] = exp_of(g.y);
     }
     __syncthreads();
 #pragma unroll
@@ -565,7 +589,7 @@ __device__ __forceinline__ void tc_forward_body(const FwdArgs& a, int m, int ni,
   tc::fence_after_sync();
   const uint32_t tmem = *tmem_slot;
   cluster_arrive();
-  cluster_wait();                            // every CTA's eps_loc and cls are written
+  cluster_wait();                            // every CTA's eps_loc and form are written
   int eps[C];
 #pragma unroll
   for (int c = 0; c < C; ++c) {
@@ -580,32 +604,40 @@ __device__ __forceinline__ void tc_forward_body(const FwdArgs& a, int m, int ni,
     return e;
   };
   unsigned diff_tiles = 0;                   // bit q: tile q of the cluster runs the difference form
-  for (int q = 0; q < ntiles; ++q) diff_tiles |= (unsigned)ld_peer_s32(peer_addr(tc::smem_addr(cls), (uint32_t)q)) << q;
+  for (int q = 0; q < ntiles; ++q) diff_tiles |= (unsigned)ld_peer_s32(peer_addr(tc::smem_addr(form_s), (uint32_t)q)) << q;
 
-  // the A operand: digit j of column c in row 8 j + c, ring tid in column tid
+  // the A operand: digit j of column c in row 8 j + c, ring tid (+ 128) in column tid (+ 128)
 #pragma unroll
-  for (int b = 0; b < NBX; ++b) {
-    const uint2 qr = offset_digits(gv[b].x, eps[2 * b]);
-    const uint2 qi = offset_digits(gv[b].y, eps[2 * b + 1]);
+  for (int ch = 0; ch < 2; ++ch) {
 #pragma unroll
-    for (int j = 0; j < kDigits; ++j) {
-      *reinterpret_cast<unsigned short*>(sG + gtile_off(8 * j + 2 * b, tid)) = digit_half(qr, j);
-      *reinterpret_cast<unsigned short*>(sG + gtile_off(8 * j + 2 * b + 1, tid)) = digit_half(qi, j);
+    for (int b = 0; b < NBX; ++b) {
+      const uint2 qr = offset_digits(gv[ch][b].x, eps[2 * b]);
+      const uint2 qi = offset_digits(gv[ch][b].y, eps[2 * b + 1]);
+#pragma unroll
+      for (int j = 0; j < kDigits; ++j) {
+        *reinterpret_cast<unsigned short*>(sG + gtile_off(8 * j + 2 * b, ch * kTcRings + tid)) = digit_half(qr, j);
+        *reinterpret_cast<unsigned short*>(sG + gtile_off(8 * j + 2 * b + 1, ch * kTcRings + tid)) = digit_half(qi, j);
+      }
     }
   }
 
-  // ---- the chain of this thread's ring
+  // ---- the chains of this thread's two rings
   const SeedData sd = a.seed[(size_t)ni * T + mi];
-  double x = 0.0, y = 0.0, v = 0.0;
-  int E = 0;
-  bool north = true;
-  if (tact) {
-    const RingData rd = a.ring[t];
-    seed_value(sd, rd, x, E);
-    v = rd.v;
-    north = rd.north;
+  double x[2], y[2], v[2];
+  int E[2];
+  bool north[2];
+  unsigned nmask[2];
+#pragma unroll
+  for (int ch = 0; ch < 2; ++ch) {
+    x[ch] = 0.0; y[ch] = 0.0; v[ch] = 0.0; E[ch] = 0; north[ch] = true;
+    if (tact[ch]) {
+      const RingData rd = a.ring[tr[ch]];
+      seed_value(sd, rd, x[ch], E[ch]);
+      v[ch] = rd.v;
+      north[ch] = rd.north;
+    }
+    nmask[ch] = north[ch] ? 0x80000000u : 0u;
   }
-  const unsigned nmask = north ? 0x80000000u : 0u;
 
   const int ndeg = L - l0;
   const int nchunks = (ndeg + kTcK - 1) / kTcK;
@@ -613,7 +645,7 @@ __device__ __forceinline__ void tc_forward_body(const FwdArgs& a, int m, int ni,
   const uint32_t cl_addr = tc::smem_addr(cl);
   bool ok = true;
 
-  // sum over the cluster's tiles of chunk kk's (X, Y) and write the owned coefficients
+  // sum over the cluster's tiles of chunk kk's (X, Y), per form, and write the owned coefficients
   auto reduce_chunk = [&](int kk) {
     const int buf = kk & 1;
     for (int p = tid * ntiles + (int)crank; p < C * kTcK; p += ntiles * kTcRings) {
@@ -629,8 +661,8 @@ __device__ __forceinline__ void tc_forward_body(const FwdArgs& a, int m, int ni,
         const long long X = ld_peer_s64(pa), Y = ld_peer_s64(pa + 8);
         if ((diff_tiles >> q) & 1u) { Xd += X; Yd += Y; } else { Xp += X; Yp += Y; }
       }
-      // plain tiles hold u = d / gamma_l digits at 2^-rho_l: times gamma_l 2^rho_l; difference
-      // tiles d digits at 2^-2
+      // block-normalised chains hold u = d / gamma_l digits at 2^-rho_l: times gamma_l 2^rho_l;
+      // difference-form chains d digits at 2^-2
       const double* cc = coef_m + (size_t)l * kCoefPerStepN;
       const double vp = fma((double)Yp, 0x1p-24, (double)Xp) * cc[3];
       const double vd = fma((double)Yd, 0x1p-24, (double)Xd);
@@ -640,13 +672,12 @@ __device__ __forceinline__ void tc_forward_body(const FwdArgs& a, int m, int ni,
     }
   };
 
-  // Software pipeline, iteration k (k = 0 .. nchunks): the recursion of chunk k; in its middle
-  // the read-back of chunk k-1's accumulator (its MMAs ran during the first 8 steps); after the
-  // CTA barrier the MMAs of chunk k and this tile's sums of chunk k-1; the cluster's sums of
-  // chunk k-2, whose tile sums every CTA published one iteration earlier.
-  const int row = 16 * warp + lane;          // accumulator row 8 j + c of this thread's lane
+  // accumulator rows 8 j + c live in lanes 32 w + r (r < 16) of warp w = row / 16: this warp's
+  // rows have digits j = 2w, 2w + 1 and need the d digits i <= 6 - 2w
+  const int row = 16 * warp + lane;
   const int rj = row >> 3, rc = row & 7;
   const bool rowact = lane < 16 && rj < kDigits && rc < C;
+  const int imax = kDigits - 1 - 2 * warp;
   for (int k = 0; k <= nchunks; ++k) {
     const bool comp = k < nchunks;
     const int jc = l0 + k * kTcK;
@@ -662,62 +693,90 @@ __device__ __forceinline__ void tc_forward_body(const FwdArgs& a, int m, int ni,
     }
 #pragma unroll
     for (int g = 0; g < 2; ++g) {
-      uint32_t w[kDigits][4];
-      const bool live = comp && __any_sync(0xffffffffu, E == 0);
-      uint2 q0 = make_uint2(0, 0);
+      uint32_t w[2][kDigits][4];
+      bool live[2];
       if (comp) {
+        uint2 q0[2] = {make_uint2(0, 0), make_uint2(0, 0)};
+#pragma unroll
+        for (int ch = 0; ch < 2; ++ch) live[ch] = __any_sync(0xffffffffu, E[ch] == 0);
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
           const int jj = g * 8 + u, j = jc + jj;
           const StepN c = stepn_at(csk + jj * kCoefPerStepN);
-          if (live) {
-            const double xl = (E == 0 && j < L) ? x : 0.0;
-            const int rho = DIFF ? 2 : exp_of(c.ig) + 2;
-            const uint2 q = offset_digits(xl, rho);
-            if (u & 1) {
-              w[0][u >> 1] = digit_pair(q0.y, q.y, 2);
-              w[1][u >> 1] = digit_pair(q0.y, q.y, 1);
-              w[2][u >> 1] = digit_pair(q0.y, q.y, 0);
-              w[3][u >> 1] = digit_pair(q0.x, q.x, 3);
-              w[4][u >> 1] = digit_pair(q0.x, q.x, 2);
-              w[5][u >> 1] = digit_pair(q0.x, q.x, 1);
-              w[6][u >> 1] = digit_pair(q0.x, q.x, 0);
-            } else {
-              q0 = q;
+#pragma unroll
+          for (int ch = 0; ch < 2; ++ch) {
+            const bool dform = ch == 0 ? D0 : D1;
+            if (live[ch]) {
+              const double xl = (E[ch] == 0 && j < L) ? x[ch] : 0.0;
+              const int rho = dform ? 2 : exp_of(c.ig) + 2;
+              const uint2 q = offset_digits(xl, rho);
+              if (u & 1) {
+                w[ch][0][u >> 1] = digit_pair(q0[ch].y, q.y, 2);
+                w[ch][1][u >> 1] = digit_pair(q0[ch].y, q.y, 1);
+                w[ch][2][u >> 1] = digit_pair(q0[ch].y, q.y, 0);
+                w[ch][3][u >> 1] = digit_pair(q0[ch].x, q.x, 3);
+                w[ch][4][u >> 1] = digit_pair(q0[ch].x, q.x, 2);
+                w[ch][5][u >> 1] = digit_pair(q0[ch].x, q.x, 1);
+                w[ch][6][u >> 1] = digit_pair(q0[ch].x, q.x, 0);
+              } else {
+                q0[ch] = q;
+              }
             }
           }
           if (j < L - 1) {
-            stepn<DIFF>(x, y, v, nmask, north, c);
-            if (u == kNormBlock - 1) unnormalise<DIFF>(x, y, c);
+            if (D0) stepn<true>(x[0], y[0], v[0], nmask[0], north[0], c);
+            else stepn<false>(x[0], y[0], v[0], nmask[0], north[0], c);
+            if (D1) stepn<true>(x[1], y[1], v[1], nmask[1], north[1], c);
+            else stepn<false>(x[1], y[1], v[1], nmask[1], north[1], c);
+            if (u == kNormBlock - 1) {
+              if (D0) unnormalise<true>(x[0], y[0], c);
+              else unnormalise<false>(x[0], y[0], c);
+              if (D1) unnormalise<true>(x[1], y[1], c);
+              else unnormalise<false>(x[1], y[1], c);
+            }
           }
         }
-        renorm(x, y, E);
+        renorm(x[0], y[0], E[0]);
+        renorm(x[1], y[1], E[1]);
       }
+      // chain k-1's MMAs read the d-digit tile: they must be done before its first store
       if (g == 0 && k > 0 && ok) {
-        // chunk k-1's MMAs are done: read its digit products back into the staging area
         if (!tc::mbar_wait(bar_a, (uint32_t)((k - 1) & 1))) {
           set_status(tc::kStatusMmaWait);
           *abort_s = 1;
         }
         tc::fence_after_sync();
+      }
+      if (comp) {
+#pragma unroll
+        for (int ch = 0; ch < 2; ++ch) {
+#pragma unroll
+          for (int i = 0; i < kDigits; ++i) {
+            const uint4 val = live[ch] ? make_uint4(w[ch][i][0], w[ch][i][1], w[ch][i][2], w[ch][i][3])
+                                       : make_uint4(0, 0, 0, 0);
+            *reinterpret_cast<uint4*>(sD + dtile_off(ch * kTcRings + tid, 2 * i + g)) = val;
+          }
+        }
+      }
+      if (g == 0 && k > 0 && ok) {
+        // read chunk k-1's digit products back into the staging area
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           long long Xs[8], Ys[8];
 #pragma unroll
           for (int e = 0; e < 8; ++e) { Xs[e] = 0; Ys[e] = 0; }
-#pragma unroll
-          for (int i = 0; i < kDigits; ++i) {
+          for (int i = 0; i <= imax; ++i) {
             uint32_t r[8];
             tc::tmem_ld8(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(kTcK * i + 8 * h), r);
             tc::tmem_ld_wait();
             const int sdeg = i + rj;
-            if (sdeg <= 6) {
+            const bool inX = sdeg <= 3, inY = sdeg >= 4 && sdeg <= 6;
+            const int shX = inX ? 8 * (3 - sdeg) : 0, shY = inY ? 8 * (6 - sdeg) : 0;
 #pragma unroll
-              for (int e = 0; e < 8; ++e) {
-                const long long S = (long long)__float2int_rn(__uint_as_float(r[e]));
-                if (sdeg <= 3) Xs[e] += S << (8 * (3 - sdeg));
-                else Ys[e] += S << (8 * (6 - sdeg));
-              }
+            for (int e = 0; e < 8; ++e) {
+              const long long S = (long long)small_int(r[e]);
+              Xs[e] += inX ? (S << shX) : 0;
+              Ys[e] += inY ? (S << shY) : 0;
             }
           }
           if (rowact) {
@@ -729,13 +788,6 @@ __device__ __forceinline__ void tc_forward_body(const FwdArgs& a, int m, int ni,
           }
         }
         tc::fence_before_sync();
-      }
-      if (comp) {
-#pragma unroll
-        for (int i = 0; i < kDigits; ++i) {
-          const uint4 val = live ? make_uint4(w[i][0], w[i][1], w[i][2], w[i][3]) : make_uint4(0, 0, 0, 0);
-          *reinterpret_cast<uint4*>(sD + dtile_off(tid, 2 * i + g)) = val;
-        }
       }
     }
     if (comp) {
@@ -749,8 +801,8 @@ __device__ __forceinline__ void tc_forward_body(const FwdArgs& a, int m, int ni,
     if (comp && ok && tid == 0) {
       tc::fence_after_sync();
 #pragma unroll
-      for (int ks = 0; ks < kTcRings / kTcK; ++ks) {
-        const uint64_t ad = tc::smem_desc(sG_addr + ks * 256, 128, 2048);
+      for (int ks = 0; ks < kFwdRings / kTcK; ++ks) {
+        const uint64_t ad = tc::smem_desc(sG_addr + ks * 256, 128, kFwdRings / 8 * 128);
         const uint64_t bd = tc::smem_desc(sD_addr + ks * 2 * (kFwdN / 8) * 128, (kFwdN / 8) * 128, 128);
         tc::mma_f16(tmem, ad, bd, tc::idesc_f16_f32(kFwdM, kFwdN) | (1u << 16), ks > 0);
       }
@@ -790,9 +842,9 @@ __device__ __forceinline__ void tc_forward_body(const FwdArgs& a, int m, int ni,
 }
 
 // Grid: x = (rank of m) * ntiles + tile (a cluster of ntiles CTAs per order), y = n index,
-// z = batch group.  The launch's rings [row0, row0 + nrows) are the tiles of 128.
+// z = batch group.  Tile q holds the launch's rings q * 128 + tid and, mirrored, nrows - 1 - that.
 template <int NB, bool PAIR>
-__global__ void __launch_bounds__(kTcRings, 3) theta_forward_tc_kernel(FwdArgs a, int ntiles) {
+__global__ void __launch_bounds__(kTcRings, 2) theta_forward_tc_kernel(FwdArgs a, int ntiles) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int L = a.L;
   const int rank = a.rank0 + (int)(blockIdx.x / ntiles), tile = blockIdx.x % ntiles;
@@ -815,31 +867,27 @@ __global__ void __launch_bounds__(kTcRings, 3) theta_forward_tc_kernel(FwdArgs a
     }
     return;
   }
-  const int t_lo = a.row0 + tile * kTcRings, t_hi = min(a.row0 + a.nrows, t_lo + kTcRings) - 1;
-  const bool diff = a.ring[t_lo].diff || a.ring[t_hi].diff;
-  if (diff) tc_forward_body<NB, PAIR, true>(a, m, ni, n, tile, ntiles, l0, smem);
-  else tc_forward_body<NB, PAIR, false>(a, m, ni, n, tile, ntiles, l0, smem);
+  // the form of the tile: the difference form if any of its rings lies in a polar cap (the caps
+  // are contiguous at both ends, so the ends of the tile's two ring ranges decide)
+  const int half = (a.nrows + 1) / 2, q0 = tile * kTcRings, q1 = min(half, q0 + kTcRings) - 1;
+  bool diff = a.ring[a.row0 + q0].diff || a.ring[a.row0 + q1].diff;
+  if (q0 < a.nrows - half) {
+    const int r1 = min(a.nrows - half, q0 + kTcRings) - 1;
+    diff = diff || a.ring[a.row0 + a.nrows - 1 - q0].diff || a.ring[a.row0 + a.nrows - 1 - r1].diff;
+  }
+  if (diff) tc_forward_body<NB, PAIR, true, true>(a, m, ni, n, tile, ntiles, l0, smem);
+  else tc_forward_body<NB, PAIR, false, false>(a, m, ni, n, tile, ntiles, l0, smem);
 }
 
 template <int NB, bool PAIR>
 cudaError_t launch_fwd_tc(const FwdArgs& a, cudaStream_t st) {
   static_assert(kFwdSmemBytes <= kFwdSmemRequest, "shared memory layout");
-  const int ntiles = (a.nrows + kTcRings - 1) / kTcRings;
+  const int ntiles = ((a.nrows + 1) / 2 + kTcRings - 1) / kTcRings;
   if (ntiles == 0) return cudaSuccess;
   if (ntiles > kFwdMaxTiles) return cudaErrorInvalidValue;
   auto kern = theta_forward_tc_kernel<NB, PAIR>;
   cudaError_t e = set_dynamic_smem((const void*)kern, kFwdSmemRequest);
   if (e != cudaSuccess) return e;
-  if (ntiles > 8) {
-    static bool nonportable_set[64] = {};
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev >= 0 && dev < 64 && !nonportable_set[dev]) {
-      e = cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-      if (e != cudaSuccess) return e;
-      nonportable_set[dev] = true;
-    }
-  }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(a.nrank * ntiles, PAIR ? (a.nN + 1) / 2 : a.nN, (a.nsig + NB - 1) / NB);
   cfg.blockDim = dim3(kTcRings, 1, 1);
@@ -929,21 +977,35 @@ __global__ void __launch_bounds__(128) op_digits_kernel(const double* __restrict
   }
 }
 
-// cexp[s][r][part] = max over the rings of the exponent of F[s][t'][k(m)] (part 0 re, 1 im)
-__global__ void op_colexp_kernel(const double2* __restrict__ F, int* __restrict__ cexp, int S, int MR, int R,
-                                 int FW, int mo) {
-  const size_t total = (size_t)S * MR;
-  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
-    const int r = (int)(idx % MR), s = (int)(idx / MR);
+// cexp[s][r][part] = max over the rings of the exponent of F[s][t'][k(m)] (part 0 re, 1 im).
+// Block = 32 consecutive rows of one signal x 8 groups of rings; a warp reads 32 consecutive
+// spectrum entries of one ring.
+__global__ void __launch_bounds__(256) op_colexp_kernel(const double2* __restrict__ F, int* __restrict__ cexp, int S,
+                                                         int MR, int R, int FW, int mo) {
+  __shared__ int red[8][32][2];
+  const int rl = threadIdx.x & 31, grp = threadIdx.x >> 5;
+  const int rblocks = (MR + 31) / 32;
+  const int s = blockIdx.x / rblocks, r = (blockIdx.x % rblocks) * 32 + rl;
+  int er = -100000, ei = -100000;
+  if (r < MR) {
     const int m = r - mo, k = m >= 0 ? m : m + FW;
-    int er = -100000, ei = -100000;
-    for (int tp = 0; tp < R; ++tp) {
-      const double2 v = F[((size_t)s * R + tp) * FW + k];
+    const double2* col = F + (size_t)s * R * FW + k;
+    for (int tp = grp; tp < R; tp += 8) {
+      const double2 v = col[(size_t)tp * FW];
       if (v.x != 0.0) er = max(er, theta::exp_of(v.x));
       if (v.y != 0.0) ei = max(ei, theta::exp_of(v.y));
     }
-    cexp[2 * idx] = er;
-    cexp[2 * idx + 1] = ei;
+  }
+  red[grp][rl][0] = er;
+  red[grp][rl][1] = ei;
+  __syncthreads();
+  if (grp == 0 && r < MR) {
+    for (int q = 1; q < 8; ++q) {
+      er = max(er, red[q][rl][0]);
+      ei = max(ei, red[q][rl][1]);
+    }
+    cexp[2 * ((size_t)s * MR + r)] = er;
+    cexp[2 * ((size_t)s * MR + r) + 1] = ei;
   }
 }
 
@@ -1153,10 +1215,10 @@ cudaError_t launch_theta_inverse_tc(const Plan& p, const InvArgs& a, cudaStream_
   return launch_inv_tc<1, false>(a, st);
 }
 
-// Forward theta stage on the tensor cores, for launches of at most 16 tiles of 128 rings (2048
+// Forward theta stage on the tensor cores, for launches of at most 8 tiles of 256 rings (2048
 // rings) written straight to flm; other launches return cudaErrorNotSupported.
 cudaError_t launch_theta_forward_tc(const Plan& p, const FwdArgs& a, cudaStream_t st) {
-  if (a.part || (a.nrows + kTcRings - 1) / kTcRings > kFwdMaxTiles) return cudaErrorNotSupported;
+  if (a.part || ((a.nrows + 1) / 2 + kTcRings - 1) / kTcRings > kFwdMaxTiles) return cudaErrorNotSupported;
   if (paired_plan(p)) {
     if (a.nsig >= 2) return launch_fwd_tc<2, true>(a, st);
     return launch_fwd_tc<1, true>(a, st);
@@ -1198,7 +1260,7 @@ cudaError_t launch_operator_tc(const Plan& p, const void* F, void* H, int* cexp,
   a.mlo = p.real ? 0 : -(p.L - 1);
   a.mhi = p.L - 1;
   a.ncol0 = (p.L + kOpCols / 2 - 1) / (kOpCols / 2);     // >= ceil(#orders of a parity / 8)
-  op_colexp_kernel<<<1024, 256, 0, st>>>(a.F, cexp, S, p.MR, p.R, a.FW, a.mo);
+  op_colexp_kernel<<<S * ((p.MR + 31) / 32), 256, 0, st>>>(a.F, cexp, S, p.MR, p.R, a.FW, a.mo);
   cudaError_t e = launched();
   if (e != cudaSuccess) return e;
   e = set_dynamic_smem((const void*)theta_operator_tc_kernel, kOpSmemRequest);

@@ -9,8 +9,13 @@ The host loop
     running batch, plus the resident plans) stays under ``budget_bytes``,
   * launches each admitted batch on a free stream of a small stream pool, so that batches overlap
     on the device while newer requests keep arriving and are admitted as slots and memory free up,
-  * polls CUDA events (no blocking waits); on completion the results are in the requests' pinned
-    host buffers, the latency (arrival -> result on the host) is recorded and memory is released.
+  * polls CUDA events (no blocking waits; an iteration that admitted, completed and received
+    nothing sleeps for ``poll_s`` while batches run, or until the next arrival when the device is
+    idle, so that the host loop does not hold a core at 100 %); on completion the results are in
+    the requests' pinned host buffers, the latency (arrival -> result on the host) is recorded and
+    memory is released.
+Latency percentiles are reported over the whole stream and per bandlimit L, so that small
+requests queued behind large batches are visible.
 Every kernel computes each signal in the same order whatever batch it is in, so a request's result
 does not depend on what it was batched with (checked by ``tests/test_gpu_serve.py``).
 """
@@ -89,10 +94,23 @@ def next_admission(pending: dict, free_slots: int, running: int, in_flight: int,
     return kind, batch
 
 
+def latency_stats(requests) -> dict:
+    """p50 / p99 / mean latency (ms) of served requests, overall and per bandlimit L."""
+    lat = np.array([r.latency for r in requests])
+    out = {"p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+           "mean_ms": float(lat.mean() * 1e3), "per_L": {}}
+    for L in sorted({r.L for r in requests}):
+        sub = np.array([r.latency for r in requests if r.L == L])
+        out["per_L"][int(L)] = {"requests": int(sub.size), "p50_ms": float(np.percentile(sub, 50) * 1e3),
+                                "p99_ms": float(np.percentile(sub, 99) * 1e3)}
+    return out
+
+
 class Server:
     def __init__(self, device: int = 0, budget_bytes: int = 16 << 30, streams: int = 4,
-                 max_batch: int = 4, precision: str = "fp64"):
+                 max_batch: int = 4, precision: str = "fp64", poll_s: float = 50e-6):
         self.device = torch.device("cuda", device)
+        self.poll_s = float(poll_s)
         self.budget = int(budget_bytes)
         self.max_batch = int(max_batch)
         self.precision = precision
@@ -143,11 +161,14 @@ class Server:
         done = 0
         n = len(requests)
         t0 = time.perf_counter()
+        idle_sleeps = 0
         while done < n:
             now = time.perf_counter() - t0
+            progress = False
             while arrivals and arrivals[0][0] <= now:
                 _, _, r = heapq.heappop(arrivals)
                 pending.setdefault((r.L, r.spin, r.direction), collections.deque()).append(r)
+                progress = True
             still = []
             for job in running:
                 if job.event.query():
@@ -159,6 +180,7 @@ class Server:
                     self.in_flight -= job.footprint
                     self.busy[job.stream_idx] = False
                     done += len(job.reqs)
+                    progress = True
                 else:
                     still.append(job)
             running = still
@@ -178,13 +200,18 @@ class Server:
                 if not q:
                     del pending[kind]
                 running.append(self._launch(p, reqs, direction, fp, free[0]))
+                progress = True
+            if not progress and done < n:
+                # nothing arrived, finished or started: back off instead of spinning
+                wait = self.poll_s if running else max(0.0, arrivals[0][0] - now) if arrivals else self.poll_s
+                time.sleep(min(wait, 0.002))
+                idle_sleeps += 1
         wall = time.perf_counter() - t0
-        lat = np.array([r.latency for r in requests])
-        return {"requests": n, "wall_s": wall, "throughput_rps": n / wall,
-                "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
-                "mean_ms": float(lat.mean() * 1e3), "launches": self.launches,
-                "peak_in_flight_bytes": self.peak_in_flight, "plan_bytes": self.plan_bytes,
-                "budget_bytes": self.budget}
+        stats = {"requests": n, "wall_s": wall, "throughput_rps": n / wall}
+        stats.update(latency_stats(requests))
+        stats.update({"launches": self.launches, "peak_in_flight_bytes": self.peak_in_flight,
+                      "plan_bytes": self.plan_bytes, "budget_bytes": self.budget, "idle_sleeps": idle_sleeps})
+        return stats
 
     def _launch(self, p: Plan, reqs, direction: str, fp: int, si: int) -> _Running:
         st = self.streams[si]

@@ -120,7 +120,8 @@ def test_tc_bench_workload_round_trip_and_agreement_with_fma():
 
 
 def test_tc_more_than_1024_degrees_per_order():
-    """L = 1500: orders with more than 1024 degrees read their accumulators back twice."""
+    """L = 1500: more than 1024 degrees per order (the accumulators are read back every 128
+    degrees into exact 64-bit sums), against the oracle and the FMA pipe."""
     L, spin = 1500, 1
     tc, fma = plans(L, spin)
     flm = synth.flm_gaussian(L, spin, 1, seed=16, ell_power=1.0)
@@ -160,9 +161,9 @@ def test_tc_forward_arbitrary_samples_matches_oracle(L, spin):
 
 @pytest.mark.parametrize("L,spin,B", [(1024, 2, 4), (2048, 0, 1)])
 def test_tc_forward_full_size_agrees_with_fma(L, spin, B):
-    """The bench workload (8 tiles per order) and L = 2048 spin 0 (16 tiles, the largest
-    cluster): tensor-core and FMA-pipe forwards agree, and the tensor-core forward is bitwise
-    repeatable."""
+    """The bench workload (a cluster of 4 tiles of 256 rings per order) and L = 2048 spin 0 (8
+    tiles, the largest cluster): tensor-core and FMA-pipe forwards agree, and the tensor-core
+    forward is bitwise repeatable."""
     tc, fma = plans(L, spin, max_batch=B)
     f = to_gpu(synth.signal_gaussian((B, L, 2 * L - 1), seed=9300 + L))
     a = tc.forward(f)

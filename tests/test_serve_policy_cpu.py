@@ -55,3 +55,21 @@ def test_plan_bytes_read_after_the_footprint():
     p = _pending((a, 0.0))
     assert next_admission(p, 1, 1, 0, lambda: state["plans"], 109, 4, fp) is None
     assert next_admission(p, 1, 1, 0, lambda: state["plans"], 110, 4, fp) == (a, 1)
+
+
+def test_latency_stats_overall_and_per_bandlimit():
+    """Percentiles per L separate small requests from large ones (numpy percentiles on the
+    latencies, overall and per group)."""
+    import numpy as np
+
+    from paper_2311_14670_gb300.serve import latency_stats
+    reqs = [SimpleNamespace(L=128, latency=0.001 * (i + 1)) for i in range(10)]
+    reqs += [SimpleNamespace(L=2048, latency=0.1 * (i + 1)) for i in range(4)]
+    st = latency_stats(reqs)
+    all_lat = np.array([r.latency for r in reqs])
+    assert abs(st["p50_ms"] - np.percentile(all_lat, 50) * 1e3) < 1e-9
+    assert abs(st["p99_ms"] - np.percentile(all_lat, 99) * 1e3) < 1e-9
+    assert set(st["per_L"]) == {128, 2048}
+    assert st["per_L"][128]["requests"] == 10 and st["per_L"][2048]["requests"] == 4
+    assert abs(st["per_L"][128]["p50_ms"] - 5.5) < 1e-9
+    assert abs(st["per_L"][2048]["p99_ms"] - np.percentile([100, 200, 300, 400], 99)) < 1e-9

@@ -416,17 +416,18 @@ cudaError_t launch_inv_tc(const InvArgs& a, cudaStream_t st) {
 // weight and the slot sign.  The sum runs over the rings, across the threads of a CTA (two chains,
 // i.e. two rings, per thread: 256 rings per CTA) and across the CTAs of the order.
 //
-//   * The ring data are split once per CTA into 7 digits per column (rows 8 j + c of the A operand,
-//     M = 64 with the zero digit 7; K = 256 rings), with one exponent per column over all rings of
-//     the order, agreed by the CTAs through distributed shared memory.
-//   * Per chunk of 16 degrees the recursion values are split as in the inverse (B operand, K = 256
-//     rings x N = 112 = (digit i, degree l), stored N-major: each thread writes 16-byte rows) and 16
-//     MMAs (16 rings each) form every digit product S_ij(c, l) in Tensor Memory.  A tile sums at
-//     most 256 rings: |S_ij| <= 2^22, exact in float32.
-//   * Each accumulator row (j, c) folds its products into two exact 64-bit words per degree,
+//   * The ring data are split once per CTA into 7 digits per column (B operand: columns 8 j + c,
+//     N = 64 with the zero digit 7; K = 256 rings, K-major), with one exponent per column over all
+//     rings of the order, agreed by the CTAs through distributed shared memory.
+//   * Per chunk of 16 degrees the recursion values are split as in the inverse (A operand: rows
+//     16 i + l = (digit i, degree l), M = 128 of which 112 are used, K = 256 rings, stored
+//     N-major: each thread writes 16-byte rows of 8 degrees) and 16 MMAs (16 rings each) form
+//     every digit product S_ij(c, l) in Tensor Memory.  A tile sums at most 256 rings: |S_ij| <=
+//     2^22, exact in float32.
+//   * Each accumulator row (i, l) folds its products into two exact 64-bit words per column,
 //     X = sum_{i+j<=3} 256^(3-i-j) S_ij and Y = sum_{4<=i+j<=6} 256^(6-i-j) S_ij (a warp holds the
-//     rows of digits 2w and 2w + 1 and reads back only the digits i <= 6 - 2w they need); the rows
-//     of a column are added through shared memory, and the tiles of the order through distributed
+//     rows of digits 2w and 2w + 1 and reads back only the columns j <= 6 - 2w they need); the
+//     rows of a degree are added through shared memory, and the tiles of the order through distributed
 //     shared memory of the thread-block cluster (one cluster per order, up to 8 tiles), in
 //     integers: the result does not depend on the order of the additions.  Tiles in the
 //     difference form (d; the tiles holding a polar cap) and in the block-normalised form (u = d /
@@ -436,14 +437,15 @@ cudaError_t launch_inv_tc(const InvArgs& a, cudaStream_t st) {
 //     chunk's recursion, and the cluster's sums of chunk k are formed during chunk k + 2.
 // =============================================================================================
 constexpr int kFwdN = kDigits * kTcK;             // 112 = (d digit i, degree l)
-constexpr int kFwdM = 64;                         // rows 8 j + c: coefficient digit j, column c
+constexpr int kFwdM = 64;                         // 8 j + c: coefficient digit j, column c (MMA N)
 constexpr int kFwdRings = 2 * kTcRings;           // rings per CTA (two chains per thread)
 constexpr int kFwdMaxTiles = 8;                   // 2048 rings per order
-constexpr int kFwdTmemCols = 128;
+constexpr int kFwdTmemCols = 64;
 constexpr int kGBytes = kFwdM * kFwdRings * 2;    // 32 KiB
 constexpr int kDBytes = kFwdRings * kFwdN * 2;    // 56 KiB
-constexpr int kFwdStageOff = kGBytes + kDBytes;                       // [16 l][7 j][8 c] x (X, Y)
-constexpr int kFwdClOff = kFwdStageOff + 8 * kTcK * kDigits * 16;     // [2 buf][16 l][8 c] x (X, Y)
+constexpr int kFwdStageOff = kGBytes + kDBytes;                       // [16 l][7 i][8 c] x (X, Y), l padded
+constexpr int kStageL = kDigits * 8 + 1;                              // entries per degree (bank spread)
+constexpr int kFwdClOff = kFwdStageOff + kTcK * kStageL * 16;         // [2 buf][16 l][8 c] x (X, Y)
 constexpr int kFwdCsOff = kFwdClOff + 2 * 8 * kTcK * 16;
 constexpr int kFwdBarOff = kFwdCsOff + 2 * kTcK * kCoefPerStepN * 8;
 constexpr int kFwdMiscOff = kFwdBarOff + 8;       // eps_loc[8], tmem_slot, abort, form
@@ -672,12 +674,11 @@ __device__ __forceinline__ void tc_forward_body(const FwdArgs& a, int m, int ni,
     }
   };
 
-  // accumulator rows 8 j + c live in lanes 32 w + r (r < 16) of warp w = row / 16: this warp's
-  // rows have digits j = 2w, 2w + 1 and need the d digits i <= 6 - 2w
-  const int row = 16 * warp + lane;
-  const int rj = row >> 3, rc = row & 7;
-  const bool rowact = lane < 16 && rj < kDigits && rc < C;
-  const int imax = kDigits - 1 - 2 * warp;
+  // accumulator row 16 i + l (d digit i, degree l) is TMEM lane 32 w + lane: warp w holds the
+  // digits i = 2w, 2w + 1, which need the coefficient digits j <= 6 - 2w (columns 8 j + c)
+  const int ri = (32 * warp + lane) >> 4, rl = lane & 15;
+  const bool rowact = ri < kDigits;
+  const int jmax = kDigits - 1 - 2 * warp;
   for (int k = 0; k <= nchunks; ++k) {
     const bool comp = k < nchunks;
     const int jc = l0 + k * kTcK;
@@ -759,33 +760,29 @@ __device__ __forceinline__ void tc_forward_body(const FwdArgs& a, int m, int ni,
         }
       }
       if (g == 0 && k > 0 && ok) {
-        // read chunk k-1's digit products back into the staging area
+        // read chunk k-1's digit products back into the staging area: this lane's d digit ri and
+        // degree rl against the coefficient digits j (8 columns c each)
+        long long Xs[8], Ys[8];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          long long Xs[8], Ys[8];
+        for (int c = 0; c < 8; ++c) { Xs[c] = 0; Ys[c] = 0; }
+        for (int j = 0; j <= jmax; ++j) {
+          uint32_t r[8];
+          tc::tmem_ld8(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(8 * j), r);
+          tc::tmem_ld_wait();
+          const int sdeg = ri + j;
+          const bool inX = sdeg <= 3, inY = sdeg >= 4 && sdeg <= 6;
+          const int shX = inX ? 8 * (3 - sdeg) : 0, shY = inY ? 8 * (6 - sdeg) : 0;
 #pragma unroll
-          for (int e = 0; e < 8; ++e) { Xs[e] = 0; Ys[e] = 0; }
-          for (int i = 0; i <= imax; ++i) {
-            uint32_t r[8];
-            tc::tmem_ld8(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(kTcK * i + 8 * h), r);
-            tc::tmem_ld_wait();
-            const int sdeg = i + rj;
-            const bool inX = sdeg <= 3, inY = sdeg >= 4 && sdeg <= 6;
-            const int shX = inX ? 8 * (3 - sdeg) : 0, shY = inY ? 8 * (6 - sdeg) : 0;
-#pragma unroll
-            for (int e = 0; e < 8; ++e) {
-              const long long S = (long long)small_int(r[e]);
-              Xs[e] += inX ? (S << shX) : 0;
-              Ys[e] += inY ? (S << shY) : 0;
-            }
+          for (int c = 0; c < 8; ++c) {
+            const long long S = (long long)small_int(r[c]);
+            Xs[c] += inX ? (S << shX) : 0;
+            Ys[c] += inY ? (S << shY) : 0;
           }
-          if (rowact) {
+        }
+        if (rowact) {
+          longlong2* st = reinterpret_cast<longlong2*>(stage) + rl * kStageL + ri * 8;
 #pragma unroll
-            for (int e = 0; e < 8; ++e) {
-              longlong2* st = reinterpret_cast<longlong2*>(stage) + ((8 * h + e) * kDigits + rj) * 8 + rc;
-              *st = make_longlong2(Xs[e], Ys[e]);
-            }
-          }
+          for (int c = 0; c < 8; ++c) st[c] = make_longlong2(Xs[c], Ys[c]);
         }
         tc::fence_before_sync();
       }
@@ -802,9 +799,11 @@ __device__ __forceinline__ void tc_forward_body(const FwdArgs& a, int m, int ni,
       tc::fence_after_sync();
 #pragma unroll
       for (int ks = 0; ks < kFwdRings / kTcK; ++ks) {
-        const uint64_t ad = tc::smem_desc(sG_addr + ks * 256, 128, kFwdRings / 8 * 128);
-        const uint64_t bd = tc::smem_desc(sD_addr + ks * 2 * (kFwdN / 8) * 128, (kFwdN / 8) * 128, 128);
-        tc::mma_f16(tmem, ad, bd, tc::idesc_f16_f32(kFwdM, kFwdN) | (1u << 16), ks > 0);
+        // A: d digits, M = 128 rows (i, l) (rows 112..127 read the next ring group's bytes and
+        // are never read back), N-major; B: coefficient digits, N = 64 columns (j, c), K-major
+        const uint64_t ad = tc::smem_desc(sD_addr + ks * 2 * (kFwdN / 8) * 128, (kFwdN / 8) * 128, 128);
+        const uint64_t bd = tc::smem_desc(sG_addr + ks * 256, 128, kFwdRings / 8 * 128);
+        tc::mma_f16(tmem, ad, bd, tc::idesc_f16_f32(kTcRings, kFwdM) | (1u << 15), ks > 0);
       }
       tc::mma_commit(bar_a);
     }
@@ -819,7 +818,7 @@ __device__ __forceinline__ void tc_forward_body(const FwdArgs& a, int m, int ni,
         long long X = 0, Y = 0;
 #pragma unroll
         for (int jj = 0; jj < kDigits; ++jj) {
-          const longlong2 sv = reinterpret_cast<const longlong2*>(stage)[(ll * kDigits + jj) * 8 + cc];
+          const longlong2 sv = reinterpret_cast<const longlong2*>(stage)[ll * kStageL + jj * 8 + cc];
           X += sv.x;
           Y += sv.y;
         }

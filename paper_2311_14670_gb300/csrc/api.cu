@@ -242,15 +242,21 @@ int gamma_dft(Plan& p, const void* in, void* out, int batch, void* work, cudaStr
 // The forward's theta-direction operator as matrices (tensor-core MW / MWSS plans, R <=
 // kOpMaxRings): the responses of the FFT operator above to unit vectors at every torus point give
 // Op (R x TS, the rows t < R the theta kernel reads); the torus extension then folds Op into the
-// two R x R matrices Q_sigma, kept as float16 digit tiles with one exponent per row.
+// two R x R matrices Q_sigma.  Q_sigma is close to diagonal (about |sin theta_t| times the
+// quadrature step on the diagonal, off-diagonal rows some 1e-3 of it away from the poles), and the
+// digit GEMM's error per term is set by the row's largest entry, so the diagonal is kept in
+// float64 (op_diag, applied in the GEMM's epilogue) and only the off-diagonal part E_sigma goes to
+// float16 digit tiles with one exponent per row.
 int build_theta_operator(Plan& p) {
   if (!p.tc || p.TS == 0 || p.R > kOpMaxRings) return S2GB_OK;
   p.op_nt = (p.R + 127) / 128;
   p.op_nk = (p.R + 15) / 16;
   const size_t dig_bytes = (size_t)2 * p.op_nt * p.op_nk * 7 * 128 * 16 * sizeof(unsigned short);
   const size_t rexp_bytes = (size_t)2 * p.op_nt * 128 * sizeof(int);
+  const size_t diag_bytes = (size_t)2 * p.op_nt * 128 * sizeof(double);
   if (cudaMalloc((void**)&p.op_dig, dig_bytes) != cudaSuccess) return S2GB_ENOMEM;
   if (cudaMalloc((void**)&p.op_rexp, rexp_bytes) != cudaSuccess) return S2GB_ENOMEM;
+  if (cudaMalloc((void**)&p.op_diag, diag_bytes) != cudaSuccess) return S2GB_ENOMEM;
   if (cudaMemset(p.op_dig, 0, dig_bytes) != cudaSuccess) return S2GB_ECUDA;
   void* tmp = nullptr;
   double* Op = nullptr;
@@ -277,7 +283,7 @@ int build_theta_operator(Plan& p) {
   cudaFree(tmp);
   if (rc != S2GB_OK) return rc;
   p.tc_op = true;
-  p.device_bytes += dig_bytes + rexp_bytes;
+  p.device_bytes += dig_bytes + rexp_bytes + diag_bytes;
   return S2GB_OK;
 }
 

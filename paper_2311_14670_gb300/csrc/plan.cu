@@ -508,6 +508,7 @@ void free_plan(Plan* p) {
   cudaFree(p->csc);
   cudaFree(p->op_dig);
   cudaFree(p->op_rexp);
+  cudaFree(p->op_diag);
   for (int q = 0; q < 2; ++q) {
     if (p->fft_made[q]) {
       cufftDestroy(p->fft_phi[q]);

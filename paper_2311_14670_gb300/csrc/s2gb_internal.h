@@ -77,7 +77,8 @@ struct Plan {
   // cores (theta_tc.cu) instead of the FFTs.
   bool tc_op = false;
   unsigned short* op_dig = nullptr;   // [2][op_nt][op_nk][7][128 x 16] K-major digit tiles
-  int* op_rexp = nullptr;             // [2][op_nt * 128]: |Q_sigma[t][.]| < 2^(op_rexp - 1)
+  int* op_rexp = nullptr;             // [2][op_nt * 128]: |E_sigma[t][.]| < 2^(op_rexp - 1)
+  double* op_diag = nullptr;          // [2][op_nt * 128]: Q_sigma[t][t] (0 past R)
   int op_nt = 0, op_nk = 0;           // 128-row tiles over t, 16-column chunks over t'
   int cap_n = 0;    // rings [ring0, cap_n) and [cap_s, ring0 + nint) use the difference form
   int cap_s = 0;
@@ -236,7 +237,8 @@ cudaError_t launch_theta_forward_tc(const Plan& p, const FwdArgs& a, cudaStream_
 // plan creation: the operator matrices from the operator's responses (theta_tc.cu)
 //   op_identity: rows r < rows of G [rows][TS] = unit vectors at torus points i0 + r
 //   op_collect:  Op[t][i0 + r] = Re H[r][t] for t < R
-//   op_digits:   Q_sigma rows from Op (R x TS), their exponents and digit tiles into the plan
+//   op_digits:   Q_sigma rows from Op (R x TS); the diagonal into op_diag, the off-diagonal part
+//                E_sigma as exponents and digit tiles into the plan
 cudaError_t launch_op_identity(void* G, int rows, int TS, int i0, cudaStream_t st);
 cudaError_t launch_op_collect(const void* H, double* Op, int rows, int R, int TS, int i0, cudaStream_t st);
 cudaError_t launch_op_digits(const Plan& p, const double* Op, cudaStream_t st);

@@ -941,10 +941,12 @@ __global__ void op_collect_kernel(const double2* __restrict__ H, double* __restr
   }
 }
 
-// One CTA per (row t, parity): Q_sigma[t][t'] for t' < R from Op, the row's exponent bound, and
-// its digits into the K-major tiles.
+// One CTA per (row t, parity): Q_sigma[t][t'] for t' < R from Op; the diagonal entry into `diag`,
+// the exponent bound of the off-diagonal entries and their digits (0 at t' = t) into the K-major
+// tiles.
 __global__ void __launch_bounds__(128) op_digits_kernel(const double* __restrict__ Op, unsigned short* __restrict__ dig,
-                                                         int* __restrict__ rexp, int R, int TS, int L, int O, int nt, int nk) {
+                                                         int* __restrict__ rexp, double* __restrict__ diag, int R,
+                                                         int TS, int L, int O, int nt, int nk) {
   const int t = blockIdx.x, par = blockIdx.y;       // par 0: sigma = +1, 1: sigma = -1
   const double sg = par ? -1.0 : 1.0;
   __shared__ int emax_s;
@@ -959,8 +961,10 @@ __global__ void __launch_bounds__(128) op_digits_kernel(const double* __restrict
   int e = -100000;
   for (int tp = threadIdx.x; tp < R; tp += blockDim.x) {
     const double q = q_at(tp);
-    if (q != 0.0) e = max(e, theta::exp_of(q));
+    if (tp == t) diag[par * nt * kTcRings + t] = q;
+    else if (q != 0.0) e = max(e, theta::exp_of(q));
   }
+  if (t >= R && threadIdx.x == 0) diag[par * nt * kTcRings + t] = 0.0;
   e = __reduce_max_sync(0xffffffffu, e);
   if ((threadIdx.x & 31) == 0) atomicMax(&emax_s, e);
   __syncthreads();
@@ -968,7 +972,7 @@ __global__ void __launch_bounds__(128) op_digits_kernel(const double* __restrict
   if (threadIdx.x == 0) rexp[par * nt * kTcRings + t] = rho;
   const int tt = t / kTcRings, row = t % kTcRings;
   for (int tp = threadIdx.x; tp < R; tp += blockDim.x) {
-    const uint2 q = offset_digits(q_at(tp), rho);
+    const uint2 q = offset_digits(tp == t ? 0.0 : q_at(tp), rho);
     unsigned short* tile = dig + ((size_t)(par * nt + tt) * nk + tp / kTcK) * kOpATile;
 #pragma unroll
     for (int i = 0; i < kDigits; ++i)
@@ -1020,6 +1024,7 @@ struct OpArgs {
   const int* cexp;         // [S][MR][2]
   const unsigned short* dig;
   const int* rexp;
+  const double* diag;      // [2][nt * 128] Q_sigma[t][t]
   const int* n_of;
   int S, MR, R, FW, TS, mo, nN, L, nt, nk, mlo, mhi, ncol0;   // ncol0: column tiles per parity
 };
@@ -1181,17 +1186,19 @@ __global__ void __launch_bounds__(kTcRings, 3) theta_operator_tc_kernel(OpArgs a
       if (!__syncthreads_and(ok)) { ok = false; break; }
     }
   }
-  // H[s][m + mo][t] = 2^(rho_t + eps_c - 38) (X + 2^-24 Y), re and im
+  // H[s][m + mo][t] = Q_sigma[t][t] F[s][t][k(m)] + 2^(rho_t + eps_c - 38) (X + 2^-24 Y), re and im
   const int t = tt * kTcRings + tid;
   if (ok && t < a.R) {
     const int rho = a.rexp[par * a.nt * kTcRings + t];
+    const double qd = a.diag[par * a.nt * kTcRings + t];
 #pragma unroll
     for (int o = 0; o < kOpCols / 2; ++o) {
       const int m = m0 + 2 * o;
       if (m > a.mhi) break;
+      const double2 f = Fs[(size_t)t * a.FW + (m >= 0 ? m : m + a.FW)];
       const double re = ldexp(fma((double)Y[2 * o], 0x1p-24, (double)X[2 * o]), rho + ce_s[2 * o] - 38);
       const double im = ldexp(fma((double)Y[2 * o + 1], 0x1p-24, (double)X[2 * o + 1]), rho + ce_s[2 * o + 1] - 38);
-      a.H[((size_t)s * a.MR + (m + a.mo)) * a.TS + t] = make_double2(re, im);
+      a.H[((size_t)s * a.MR + (m + a.mo)) * a.TS + t] = make_double2(fma(qd, f.x, re), fma(qd, f.y, im));
     }
   }
   tc::fence_before_sync();
@@ -1239,8 +1246,8 @@ cudaError_t launch_op_collect(const void* H, double* Op, int rows, int R, int TS
 
 cudaError_t launch_op_digits(const Plan& p, const double* Op, cudaStream_t st) {
   const int O = p.sampling == S2GB_MWSS ? 2 * p.L : 2 * p.L - 2;
-  op_digits_kernel<<<dim3(p.op_nt * kTcRings, 2), 128, 0, st>>>(Op, p.op_dig, p.op_rexp, p.R, p.TS, p.L, O,
-                                                               p.op_nt, p.op_nk);
+  op_digits_kernel<<<dim3(p.op_nt * kTcRings, 2), 128, 0, st>>>(Op, p.op_dig, p.op_rexp, p.op_diag, p.R, p.TS,
+                                                               p.L, O, p.op_nt, p.op_nk);
   return launched();
 }
 
@@ -1252,6 +1259,7 @@ cudaError_t launch_operator_tc(const Plan& p, const void* F, void* H, int* cexp,
   a.cexp = cexp;
   a.dig = p.op_dig;
   a.rexp = p.op_rexp;
+  a.diag = p.op_diag;
   a.n_of = p.n_of;
   a.S = S; a.MR = p.MR; a.R = p.R; a.TS = p.TS; a.nN = p.nN; a.L = p.L; a.nt = p.op_nt; a.nk = p.op_nk;
   a.FW = p.real ? p.L : p.P;

@@ -413,8 +413,8 @@ cudaError_t launch_inv_tc(const InvArgs& a, cudaStream_t st) {
 // =============================================================================================
 // Forward theta stage (Sec. 4.1, Eq. disc_sh_expanded) with the contraction over the rings on the
 // tensor cores: flm[l][c] = scale_l sum_t d^l(theta_t) g'_t[c], g' the ring data times the ring
-// weight and the slot sign.  The sum runs over the rings, across the threads of a CTA (two chains,
-// i.e. two rings, per thread: 256 rings per CTA) and across the CTAs of the order.
+// weight and the slot sign.  The sum runs over the rings, across the threads of a CTA (one chain,
+// i.e. one ring, per thread: 256 threads and 256 rings per CTA) and across the CTAs of the order.
 //
 //   * The ring data are split once per CTA into 7 digits per column (B operand: columns 8 j + c,
 //     N = 64 with the zero digit 7; K = 256 rings, K-major), with one exponent per column over all
@@ -425,32 +425,37 @@ cudaError_t launch_inv_tc(const InvArgs& a, cudaStream_t st) {
 //     every digit product S_ij(c, l) in Tensor Memory.  A tile sums at most 256 rings: |S_ij| <=
 //     2^22, exact in float32.
 //   * Each accumulator row (i, l) folds its products into two exact 64-bit words per column,
-//     X = sum_{i+j<=3} 256^(3-i-j) S_ij and Y = sum_{4<=i+j<=6} 256^(6-i-j) S_ij (a warp holds the
-//     rows of digits 2w and 2w + 1 and reads back only the columns j <= 6 - 2w they need); the
-//     rows of a degree are added through shared memory, and the tiles of the order through distributed
-//     shared memory of the thread-block cluster (one cluster per order, up to 8 tiles), in
-//     integers: the result does not depend on the order of the additions.  Tiles in the
-//     difference form (d; the tiles holding a polar cap) and in the block-normalised form (u = d /
-//     gamma_l) are summed separately -- their digits carry different scales -- and combined in
-//     float64.
+//     X = sum_{i+j<=3} 256^(3-i-j) S_ij and Y = sum_{4<=i+j<=6} 256^(6-i-j) S_ij.  The rows of
+//     digits 2q and 2q + 1 lie in TMEM lane quadrant q, which warps q and q + 4 share: they read
+//     back complementary ranges of the coefficient digits j <= 6 - 2q.  Each warp adds its two
+//     digit rows of a degree with one shuffle; the warps' words of a degree are added through
+//     shared memory, and the tiles of the order through distributed shared memory of the
+//     thread-block cluster (one cluster per order, up to 8 tiles), in integers: the result does
+//     not depend on the order of the additions.  Tiles in the difference form (d; the tiles
+//     holding a polar cap) and in the block-normalised form (u = d / gamma_l) are summed
+//     separately -- their digits carry different scales -- and combined in float64.
 //   * The loop is software-pipelined: a chunk's accumulator is read back in the middle of the next
 //     chunk's recursion, and the cluster's sums of chunk k are formed during chunk k + 2.
+//   * Two CTAs (16 warps) share an SM: 110 KiB of shared memory and at most 128 registers per
+//     thread each.
 // =============================================================================================
 constexpr int kFwdN = kDigits * kTcK;             // 112 = (d digit i, degree l)
 constexpr int kFwdM = 64;                         // 8 j + c: coefficient digit j, column c (MMA N)
-constexpr int kFwdRings = 2 * kTcRings;           // rings per CTA (two chains per thread)
+constexpr int kFwdThreads = 2 * kTcRings;         // one ring per thread
+constexpr int kFwdRings = kFwdThreads;            // rings per CTA
+constexpr int kFwdWarps = kFwdThreads / 32;
 constexpr int kFwdMaxTiles = 8;                   // 2048 rings per order
 constexpr int kFwdTmemCols = 64;
 constexpr int kGBytes = kFwdM * kFwdRings * 2;    // 32 KiB
 constexpr int kDBytes = kFwdRings * kFwdN * 2;    // 56 KiB
-constexpr int kFwdStageOff = kGBytes + kDBytes;                       // [16 l][7 i][8 c] x (X, Y), l padded
-constexpr int kStageL = kDigits * 8 + 1;                              // entries per degree (bank spread)
-constexpr int kFwdClOff = kFwdStageOff + kTcK * kStageL * 16;         // [2 buf][16 l][8 c] x (X, Y)
+constexpr int kFwdStageOff = kGBytes + kDBytes;                       // [8 warps][8 c][16 l] x (X, Y)
+constexpr int kFwdClOff = kFwdStageOff + kFwdWarps * 8 * kTcK * 16;   // [2 buf][8 c][16 l] x (X, Y)
 constexpr int kFwdCsOff = kFwdClOff + 2 * 8 * kTcK * 16;
 constexpr int kFwdBarOff = kFwdCsOff + 2 * kTcK * kCoefPerStepN * 8;
 constexpr int kFwdMiscOff = kFwdBarOff + 8;       // eps_loc[8], tmem_slot, abort, form
 constexpr int kFwdSmemBytes = kFwdMiscOff + 64;
 constexpr int kFwdSmemRequest = 112 * 1024;       // two CTAs per SM
+static_assert(kTcK * kCoefPerStepN <= kFwdThreads, "one coefficient prefetch per thread");
 
 __device__ __forceinline__ uint32_t cluster_rank() {
   uint32_t r;
@@ -493,9 +498,8 @@ __device__ __forceinline__ int small_int(uint32_t bits) {
   return (int)(__float_as_uint(__uint_as_float(bits) + 12582912.0f) - 0x4B400000u);
 }
 
-// D0 / D1: the rings of chain 0 (the tile's first 128) / chain 1 run the difference form (the
-// kernel launches D0 == D1: the cluster sums tiles of one form together).
-template <int NB, bool PAIR, bool D0, bool D1>
+// DIFF: every ring of the tile runs the difference form (the tiles holding a polar cap).
+template <int NB, bool PAIR, bool DIFF>
 __device__ __forceinline__ void tc_forward_body(const FwdArgs& a, int m, int ni, int n, int tile, int ntiles,
                                                 int l0, unsigned char* smem) {
   constexpr int NBX = PAIR ? 2 * NB : NB;
@@ -509,8 +513,8 @@ __device__ __forceinline__ void tc_forward_body(const FwdArgs& a, int m, int ni,
 
   unsigned char* sG = smem;
   unsigned char* sD = smem + kGBytes;
-  long long* stage = reinterpret_cast<long long*>(smem + kFwdStageOff);
-  long long* cl = reinterpret_cast<long long*>(smem + kFwdClOff);
+  longlong2* stage = reinterpret_cast<longlong2*>(smem + kFwdStageOff);
+  longlong2* cl = reinterpret_cast<longlong2*>(smem + kFwdClOff);
   double* cs = reinterpret_cast<double*>(smem + kFwdCsOff);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kFwdBarOff);
   int* eps_loc = reinterpret_cast<int*>(smem + kFwdMiscOff);
@@ -522,16 +526,15 @@ __device__ __forceinline__ void tc_forward_body(const FwdArgs& a, int m, int ni,
 
   const double* coef_m = a.coef + ((size_t)ni * T + mi) * (size_t)L * kCoefPerStepN;
   const double* scale = a.scale + (size_t)ni * L;
-  // mirrored rings: chain 0 counts from the first ring of the launch, chain 1 from the last, so
-  // that both polar caps (the difference form) fall in the cluster's first tile
-  int tr[2];
-  bool tact[2];
+  // mirrored rings: threads 0..127 count from the first ring of the launch, threads 128..255 from
+  // the last, so that both polar caps (the difference form) fall in the cluster's first tile
+  int tr;
+  bool tact;
   {
-    const int half = (a.nrows + 1) / 2, q = tile * kTcRings + tid;
-    tact[0] = q < half;
-    tact[1] = q < a.nrows - half;
-    tr[0] = a.row0 + q;
-    tr[1] = a.row0 + a.nrows - 1 - q;
+    const int half = (a.nrows + 1) / 2, q = tile * kTcRings + (tid & (kTcRings - 1));
+    const bool mirror = tid >= kTcRings;
+    tact = mirror ? q < a.nrows - half : q < half;
+    tr = mirror ? a.row0 + a.nrows - 1 - q : a.row0 + q;
   }
 
   // ---- set-up: barrier, Tensor Memory, the degrees below l0, column exponents over the cluster
@@ -539,45 +542,42 @@ __device__ __forceinline__ void tc_forward_body(const FwdArgs& a, int m, int ni,
     tc::mbar_init(bar_a, 1);
     tc::mbar_init_fence();
     *abort_s = 0;
-    *form_s = D0 ? 1 : 0;
+    *form_s = DIFF ? 1 : 0;
   }
   if (warp == 0) tc::tmem_alloc(tc::smem_addr(tmem_slot), kFwdTmemCols);
-  for (int q = tid; q < kGBytes / 16; q += kTcRings) reinterpret_cast<uint4*>(sG)[q] = make_uint4(0, 0, 0, 0);
+  for (int q = tid; q < kGBytes / 16; q += kFwdThreads) reinterpret_cast<uint4*>(sG)[q] = make_uint4(0, 0, 0, 0);
   if (tid < 8) eps_loc[tid] = -100000;
   if (tile == 0) {
     const int lz = min(l0, L);
-    for (int q = tid; q < NBX * lz; q += kTcRings) {
+    for (int q = tid; q < NBX * lz; q += kFwdThreads) {
       const int b = q / lz, j = q % lz;
       const Slot sl = slot_of<NB, PAIR>(b, sig0, a.nsig, a.nN, ni, m, n, L);
       if (sl.sig_off >= 0) outb[((size_t)sl.sig_off * L + j) * a.flm_ld + sl.m + a.flm_c0] = make_double2(0.0, 0.0);
     }
   }
-  for (int q = tid; q < kTcK * kCoefPerStepN; q += kTcRings) {
-    const int j = l0 + q / kCoefPerStepN;
-    cs[q] = (j < L) ? coef_m[(size_t)l0 * kCoefPerStepN + q] : 0.0;
+  if (tid < kTcK * kCoefPerStepN) {
+    const int j = l0 + tid / kCoefPerStepN;
+    cs[tid] = (j < L) ? coef_m[(size_t)l0 * kCoefPerStepN + tid] : 0.0;
   }
-  double2 gv[2][NBX];
+  double2 gv[NBX];
   {
     int emax[C];
 #pragma unroll
     for (int c = 0; c < C; ++c) emax[c] = -100000;
 #pragma unroll
-    for (int ch = 0; ch < 2; ++ch) {
-#pragma unroll
-      for (int b = 0; b < NBX; ++b) {
-        const Slot sl = slot_of<NB, PAIR>(b, sig0, a.nsig, a.nN, ni, m, n, L);
-        double2 g = make_double2(0.0, 0.0);
-        if (tact[ch] && sl.sig_off >= 0) {
-          const long long col = a.m_mod ? (sl.m >= 0 ? sl.m : sl.m + a.mmod) : sl.mi;
-          g = reinterpret_cast<const double2*>(a.g)[(size_t)sl.sig_off * a.s_sig + tr[ch] * a.s_t + col * a.s_m];
-          const double w = (a.use_nu ? a.nu[tr[ch]] : 1.0) * sl.sign;
-          g.x *= w;
-          g.y *= w;
-        }
-        gv[ch][b] = g;
-        if (g.x != 0.0) emax[2 * b] = max(emax[2 * b], exp_of(g.x));
-        if (g.y != 0.0) emax[2 * b + 1] = max(emax[2 * b + 1], exp_of(g.y));
+    for (int b = 0; b < NBX; ++b) {
+      const Slot sl = slot_of<NB, PAIR>(b, sig0, a.nsig, a.nN, ni, m, n, L);
+      double2 g = make_double2(0.0, 0.0);
+      if (tact && sl.sig_off >= 0) {
+        const long long col = a.m_mod ? (sl.m >= 0 ? sl.m : sl.m + a.mmod) : sl.mi;
+        g = reinterpret_cast<const double2*>(a.g)[(size_t)sl.sig_off * a.s_sig + tr * a.s_t + col * a.s_m];
+        const double w = (a.use_nu ? a.nu[tr] : 1.0) * sl.sign;
+        g.x *= w;
+        g.y *= w;
       }
+      gv[b] = g;
+      if (g.x != 0.0) emax[2 * b] = max(emax[2 * b], exp_of(g.x));
+      if (g.y != 0.0) emax[2 * b + 1] = max(emax[2 * b + 1], exp_of(g.y));
     }
     __syncthreads();
 #pragma unroll
@@ -608,38 +608,30 @@ __device__ __forceinline__ void tc_forward_body(const FwdArgs& a, int m, int ni,
   unsigned diff_tiles = 0;                   // bit q: tile q of the cluster runs the difference form
   for (int q = 0; q < ntiles; ++q) diff_tiles |= (unsigned)ld_peer_s32(peer_addr(tc::smem_addr(form_s), (uint32_t)q)) << q;
 
-  // the A operand: digit j of column c in row 8 j + c, ring tid (+ 128) in column tid (+ 128)
+  // the B operand: digit j of column c in row 8 j + c, this thread's ring in column tid
 #pragma unroll
-  for (int ch = 0; ch < 2; ++ch) {
+  for (int b = 0; b < NBX; ++b) {
+    const uint2 qr = offset_digits(gv[b].x, eps[2 * b]);
+    const uint2 qi = offset_digits(gv[b].y, eps[2 * b + 1]);
 #pragma unroll
-    for (int b = 0; b < NBX; ++b) {
-      const uint2 qr = offset_digits(gv[ch][b].x, eps[2 * b]);
-      const uint2 qi = offset_digits(gv[ch][b].y, eps[2 * b + 1]);
-#pragma unroll
-      for (int j = 0; j < kDigits; ++j) {
-        *reinterpret_cast<unsigned short*>(sG + gtile_off(8 * j + 2 * b, ch * kTcRings + tid)) = digit_half(qr, j);
-        *reinterpret_cast<unsigned short*>(sG + gtile_off(8 * j + 2 * b + 1, ch * kTcRings + tid)) = digit_half(qi, j);
-      }
+    for (int j = 0; j < kDigits; ++j) {
+      *reinterpret_cast<unsigned short*>(sG + gtile_off(8 * j + 2 * b, tid)) = digit_half(qr, j);
+      *reinterpret_cast<unsigned short*>(sG + gtile_off(8 * j + 2 * b + 1, tid)) = digit_half(qi, j);
     }
   }
 
-  // ---- the chains of this thread's two rings
+  // ---- the chain of this thread's ring
   const SeedData sd = a.seed[(size_t)ni * T + mi];
-  double x[2], y[2], v[2];
-  int E[2];
-  bool north[2];
-  unsigned nmask[2];
-#pragma unroll
-  for (int ch = 0; ch < 2; ++ch) {
-    x[ch] = 0.0; y[ch] = 0.0; v[ch] = 0.0; E[ch] = 0; north[ch] = true;
-    if (tact[ch]) {
-      const RingData rd = a.ring[tr[ch]];
-      seed_value(sd, rd, x[ch], E[ch]);
-      v[ch] = rd.v;
-      north[ch] = rd.north;
-    }
-    nmask[ch] = north[ch] ? 0x80000000u : 0u;
+  double x = 0.0, y = 0.0, v = 0.0;
+  int E = 0;
+  bool north = true;
+  if (tact) {
+    const RingData rd = a.ring[tr];
+    seed_value(sd, rd, x, E);
+    v = rd.v;
+    north = rd.north;
   }
+  const unsigned nmask = north ? 0x80000000u : 0u;
 
   const int ndeg = L - l0;
   const int nchunks = (ndeg + kTcK - 1) / kTcK;
@@ -650,14 +642,14 @@ __device__ __forceinline__ void tc_forward_body(const FwdArgs& a, int m, int ni,
   // sum over the cluster's tiles of chunk kk's (X, Y), per form, and write the owned coefficients
   auto reduce_chunk = [&](int kk) {
     const int buf = kk & 1;
-    for (int p = tid * ntiles + (int)crank; p < C * kTcK; p += ntiles * kTcRings) {
+    for (int p = tid * ntiles + (int)crank; p < C * kTcK; p += ntiles * kFwdThreads) {
       const int c = p % C, ll = p / C, l = l0 + kk * kTcK + ll;
       if (l >= L) continue;
       const int b = c >> 1;
       const Slot sl = slot_of<NB, PAIR>(b, sig0, a.nsig, a.nN, ni, m, n, L);
       if (sl.sig_off < 0) continue;
       long long Xp = 0, Yp = 0, Xd = 0, Yd = 0;
-      const uint32_t off = cl_addr + (uint32_t)(((buf * kTcK + ll) * 8 + c) * 16);
+      const uint32_t off = cl_addr + (uint32_t)(((buf * 8 + c) * kTcK + ll) * 16);
       for (int q = 0; q < ntiles; ++q) {
         const uint32_t pa = peer_addr(off, (uint32_t)q);
         const long long X = ld_peer_s64(pa), Y = ld_peer_s64(pa + 8);
@@ -674,73 +666,56 @@ __device__ __forceinline__ void tc_forward_body(const FwdArgs& a, int m, int ni,
     }
   };
 
-  // accumulator row 16 i + l (d digit i, degree l) is TMEM lane 32 w + lane: warp w holds the
-  // digits i = 2w, 2w + 1, which need the coefficient digits j <= 6 - 2w (columns 8 j + c)
-  const int ri = (32 * warp + lane) >> 4, rl = lane & 15;
-  const bool rowact = ri < kDigits;
-  const int jmax = kDigits - 1 - 2 * warp;
+  // accumulator row 16 i + l (d digit i, degree l) is TMEM lane 32 q + lane, q = warp % 4: lane
+  // quadrant q holds the digits i = 2q, 2q + 1, which need the coefficient digits j <= 6 - 2q
+  // (columns 8 j + c); warp q reads j < jsplit, warp q + 4 the rest
+  const int quad = warp & 3;
+  const int ri = (32 * quad + lane) >> 4, rl = lane & 15;
+  const int jmax = kDigits - 1 - 2 * quad;
+  const int jsplit = (jmax + 2) / 2;
+  const int jlo = warp < 4 ? 0 : jsplit, jhi = warp < 4 ? jsplit - 1 : jmax;
   for (int k = 0; k <= nchunks; ++k) {
     const bool comp = k < nchunks;
     const int jc = l0 + k * kTcK;
     const double* csk = cs + (k & 1) * kTcK * kCoefPerStepN;
-    double cpre[2] = {0.0, 0.0};
-    if (comp) {
-#pragma unroll
-      for (int r = 0; r < 2; ++r) {
-        const int q = tid + r * kTcRings;
-        if (q < kTcK * kCoefPerStepN && jc + kTcK + q / kCoefPerStepN < L)
-          cpre[r] = coef_m[(size_t)(jc + kTcK) * kCoefPerStepN + q];
-      }
-    }
+    double cpre = 0.0;
+    if (comp && tid < kTcK * kCoefPerStepN && jc + kTcK + tid / kCoefPerStepN < L)
+      cpre = coef_m[(size_t)(jc + kTcK) * kCoefPerStepN + tid];
 #pragma unroll
     for (int g = 0; g < 2; ++g) {
-      uint32_t w[2][kDigits][4];
-      bool live[2];
+      uint32_t w[kDigits][4];
+      bool live = false;
       if (comp) {
-        uint2 q0[2] = {make_uint2(0, 0), make_uint2(0, 0)};
-#pragma unroll
-        for (int ch = 0; ch < 2; ++ch) live[ch] = __any_sync(0xffffffffu, E[ch] == 0);
+        uint2 q0 = make_uint2(0, 0);
+        live = __any_sync(0xffffffffu, E == 0);
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
           const int jj = g * 8 + u, j = jc + jj;
           const StepN c = stepn_at(csk + jj * kCoefPerStepN);
-#pragma unroll
-          for (int ch = 0; ch < 2; ++ch) {
-            const bool dform = ch == 0 ? D0 : D1;
-            if (live[ch]) {
-              const double xl = (E[ch] == 0 && j < L) ? x[ch] : 0.0;
-              const int rho = dform ? 2 : exp_of(c.ig) + 2;
-              const uint2 q = offset_digits(xl, rho);
-              if (u & 1) {
-                w[ch][0][u >> 1] = digit_pair(q0[ch].y, q.y, 2);
-                w[ch][1][u >> 1] = digit_pair(q0[ch].y, q.y, 1);
-                w[ch][2][u >> 1] = digit_pair(q0[ch].y, q.y, 0);
-                w[ch][3][u >> 1] = digit_pair(q0[ch].x, q.x, 3);
-                w[ch][4][u >> 1] = digit_pair(q0[ch].x, q.x, 2);
-                w[ch][5][u >> 1] = digit_pair(q0[ch].x, q.x, 1);
-                w[ch][6][u >> 1] = digit_pair(q0[ch].x, q.x, 0);
-              } else {
-                q0[ch] = q;
-              }
+          if (live) {
+            const double xl = (E == 0 && j < L) ? x : 0.0;
+            const int rho = DIFF ? 2 : exp_of(c.ig) + 2;
+            const uint2 q = offset_digits(xl, rho);
+            if (u & 1) {
+              w[0][u >> 1] = digit_pair(q0.y, q.y, 2);
+              w[1][u >> 1] = digit_pair(q0.y, q.y, 1);
+              w[2][u >> 1] = digit_pair(q0.y, q.y, 0);
+              w[3][u >> 1] = digit_pair(q0.x, q.x, 3);
+              w[4][u >> 1] = digit_pair(q0.x, q.x, 2);
+              w[5][u >> 1] = digit_pair(q0.x, q.x, 1);
+              w[6][u >> 1] = digit_pair(q0.x, q.x, 0);
+            } else {
+              q0 = q;
             }
           }
           if (j < L - 1) {
-            if (D0) stepn<true>(x[0], y[0], v[0], nmask[0], north[0], c);
-            else stepn<false>(x[0], y[0], v[0], nmask[0], north[0], c);
-            if (D1) stepn<true>(x[1], y[1], v[1], nmask[1], north[1], c);
-            else stepn<false>(x[1], y[1], v[1], nmask[1], north[1], c);
-            if (u == kNormBlock - 1) {
-              if (D0) unnormalise<true>(x[0], y[0], c);
-              else unnormalise<false>(x[0], y[0], c);
-              if (D1) unnormalise<true>(x[1], y[1], c);
-              else unnormalise<false>(x[1], y[1], c);
-            }
+            stepn<DIFF>(x, y, v, nmask, north, c);
+            if (u == kNormBlock - 1) unnormalise<DIFF>(x, y, c);
           }
         }
-        renorm(x[0], y[0], E[0]);
-        renorm(x[1], y[1], E[1]);
+        renorm(x, y, E);
       }
-      // chain k-1's MMAs read the d-digit tile: they must be done before its first store
+      // chunk k-1's MMAs read the d-digit tile: they must be done before its first store
       if (g == 0 && k > 0 && ok) {
         if (!tc::mbar_wait(bar_a, (uint32_t)((k - 1) & 1))) {
           set_status(tc::kStatusMmaWait);
@@ -750,24 +725,20 @@ __device__ __forceinline__ void tc_forward_body(const FwdArgs& a, int m, int ni,
       }
       if (comp) {
 #pragma unroll
-        for (int ch = 0; ch < 2; ++ch) {
-#pragma unroll
-          for (int i = 0; i < kDigits; ++i) {
-            const uint4 val = live[ch] ? make_uint4(w[ch][i][0], w[ch][i][1], w[ch][i][2], w[ch][i][3])
-                                       : make_uint4(0, 0, 0, 0);
-            *reinterpret_cast<uint4*>(sD + dtile_off(ch * kTcRings + tid, 2 * i + g)) = val;
-          }
+        for (int i = 0; i < kDigits; ++i) {
+          const uint4 val = live ? make_uint4(w[i][0], w[i][1], w[i][2], w[i][3]) : make_uint4(0, 0, 0, 0);
+          *reinterpret_cast<uint4*>(sD + dtile_off(tid, 2 * i + g)) = val;
         }
       }
       if (g == 0 && k > 0 && ok) {
-        // read chunk k-1's digit products back into the staging area: this lane's d digit ri and
-        // degree rl against the coefficient digits j (8 columns c each)
+        // read chunk k-1's digit products back: this lane's d digit ri and degree rl against the
+        // coefficient digits j of this warp's range (8 columns c each)
         long long Xs[8], Ys[8];
 #pragma unroll
         for (int c = 0; c < 8; ++c) { Xs[c] = 0; Ys[c] = 0; }
-        for (int j = 0; j <= jmax; ++j) {
+        for (int j = jlo; j <= jhi; ++j) {
           uint32_t r[8];
-          tc::tmem_ld8(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(8 * j), r);
+          tc::tmem_ld8(tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(8 * j), r);
           tc::tmem_ld_wait();
           const int sdeg = ri + j;
           const bool inX = sdeg <= 3, inY = sdeg >= 4 && sdeg <= 6;
@@ -779,19 +750,20 @@ __device__ __forceinline__ void tc_forward_body(const FwdArgs& a, int m, int ni,
             Ys[c] += inY ? (S << shY) : 0;
           }
         }
-        if (rowact) {
-          longlong2* st = reinterpret_cast<longlong2*>(stage) + rl * kStageL + ri * 8;
+        // the two digit rows of a degree (lanes rl and rl + 16), then one word pair per warp
 #pragma unroll
-          for (int c = 0; c < 8; ++c) st[c] = make_longlong2(Xs[c], Ys[c]);
+        for (int c = 0; c < 8; ++c) {
+          Xs[c] += __shfl_xor_sync(0xffffffffu, Xs[c], 16);
+          Ys[c] += __shfl_xor_sync(0xffffffffu, Ys[c], 16);
+        }
+        if (lane < kTcK) {
+#pragma unroll
+          for (int c = 0; c < 8; ++c) stage[(warp * 8 + c) * kTcK + rl] = make_longlong2(Xs[c], Ys[c]);
         }
         tc::fence_before_sync();
       }
     }
-    if (comp) {
-      double* csn = cs + ((k + 1) & 1) * kTcK * kCoefPerStepN;
-      csn[tid] = cpre[0];
-      if (tid + kTcRings < kTcK * kCoefPerStepN) csn[tid + kTcRings] = cpre[1];
-    }
+    if (comp && tid < kTcK * kCoefPerStepN) cs[((k + 1) & 1) * kTcK * kCoefPerStepN + tid] = cpre;
     tc::fence_proxy_async();
     __syncthreads();
     if (*abort_s) ok = false;
@@ -813,16 +785,16 @@ __device__ __forceinline__ void tc_forward_body(const FwdArgs& a, int m, int ni,
         cluster_wait();
         if (ok) reduce_chunk(k - 2);
       }
-      if (tid < C * kTcK) {
-        const int cc = tid % C, ll = tid / C;
+      if (tid < 8 * kTcK) {
+        const int cc = tid / kTcK, ll = tid % kTcK;
         long long X = 0, Y = 0;
 #pragma unroll
-        for (int jj = 0; jj < kDigits; ++jj) {
-          const longlong2 sv = reinterpret_cast<const longlong2*>(stage)[ll * kStageL + jj * 8 + cc];
+        for (int w8 = 0; w8 < kFwdWarps; ++w8) {
+          const longlong2 sv = stage[(w8 * 8 + cc) * kTcK + ll];
           X += sv.x;
           Y += sv.y;
         }
-        reinterpret_cast<longlong2*>(cl)[(((k - 1) & 1) * kTcK + ll) * 8 + cc] = make_longlong2(X, Y);
+        cl[(((k - 1) & 1) * 8 + cc) * kTcK + ll] = make_longlong2(X, Y);
       }
       __syncthreads();                       // the staging area is read: the next read-back may write it
       cluster_arrive();
@@ -841,9 +813,10 @@ __device__ __forceinline__ void tc_forward_body(const FwdArgs& a, int m, int ni,
 }
 
 // Grid: x = (rank of m) * ntiles + tile (a cluster of ntiles CTAs per order), y = n index,
-// z = batch group.  Tile q holds the launch's rings q * 128 + tid and, mirrored, nrows - 1 - that.
+// z = batch group.  Tile q holds the launch's rings q * 128 + (tid mod 128) and, mirrored (tid >=
+// 128), nrows - 1 - that.
 template <int NB, bool PAIR>
-__global__ void __launch_bounds__(kTcRings, 2) theta_forward_tc_kernel(FwdArgs a, int ntiles) {
+__global__ void __launch_bounds__(kFwdThreads, 2) theta_forward_tc_kernel(FwdArgs a, int ntiles) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int L = a.L;
   const int rank = a.rank0 + (int)(blockIdx.x / ntiles), tile = blockIdx.x % ntiles;
@@ -874,8 +847,8 @@ __global__ void __launch_bounds__(kTcRings, 2) theta_forward_tc_kernel(FwdArgs a
     const int r1 = min(a.nrows - half, q0 + kTcRings) - 1;
     diff = diff || a.ring[a.row0 + a.nrows - 1 - q0].diff || a.ring[a.row0 + a.nrows - 1 - r1].diff;
   }
-  if (diff) tc_forward_body<NB, PAIR, true, true>(a, m, ni, n, tile, ntiles, l0, smem);
-  else tc_forward_body<NB, PAIR, false, false>(a, m, ni, n, tile, ntiles, l0, smem);
+  if (diff) tc_forward_body<NB, PAIR, true>(a, m, ni, n, tile, ntiles, l0, smem);
+  else tc_forward_body<NB, PAIR, false>(a, m, ni, n, tile, ntiles, l0, smem);
 }
 
 template <int NB, bool PAIR>
@@ -889,7 +862,7 @@ cudaError_t launch_fwd_tc(const FwdArgs& a, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(a.nrank * ntiles, PAIR ? (a.nN + 1) / 2 : a.nN, (a.nsig + NB - 1) / NB);
-  cfg.blockDim = dim3(kTcRings, 1, 1);
+  cfg.blockDim = dim3(kFwdThreads, 1, 1);
   cfg.dynamicSmemBytes = kFwdSmemRequest;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];

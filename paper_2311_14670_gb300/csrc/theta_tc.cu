@@ -30,7 +30,9 @@
 //     one float64 conversion at the end gives the result.  Levels s > 6 are never formed: their
 //     weight is below 2^-48 of the leading ones, under the rounding of the float64 recursion.
 //
-// Mapping: CTA = (order rank, tile of 128 rings, n, batch group); thread tid = ring = TMEM lane.
+// Mapping: CTA = (order rank, tile of 128 rings, n, batch group); thread tid = ring = TMEM lane; a
+// tile holds 64 rings counted from the first ring and the 64 mirrored ones counted from the last,
+// so that the polar caps, which need the difference form, share the first tiles.
 // Per chunk of 16 degrees each thread advances its chain 16 steps, writing its 7 digit rows into
 // shared memory (K-major 8 x 16-byte core matrices); 16 x slots threads write the coefficient
 // digits; after a CTA barrier one thread issues the 7 MMAs and commits them to an mbarrier.  The
@@ -109,6 +111,17 @@ __device__ __forceinline__ unsigned short digit_half(uint2 q, int i) {
 }
 
 __device__ __forceinline__ void set_status(int code) { atomicCAS(&g_s2gb_device_status, 0, code); }
+
+// Ring of thread `tid` in inverse tile `tile`, or -1: threads 0..63 take the tile's rings counted
+// from the first ring of the launch, threads 64..127 the mirrored rings counted from the last, so
+// that both polar caps (the difference form) fall into the first tiles.
+__device__ __forceinline__ int inv_ring(const InvArgs& a, int tile, int tid) {
+  constexpr int H = kTcRings / 2;
+  const int nr = a.nring - a.ring0, half = (nr + 1) / 2;
+  const int q = tile * H + (tid & (H - 1));
+  if (tid < H) return q < half ? a.ring0 + q : -1;
+  return q < nr - half ? a.nring - 1 - q : -1;
+}
 
 // Per-degree factor of the coefficients: w_j = scale_j (* gamma_j for block-normalised chains)
 // * 2^rho_j, so that h'_{j,c} = h_{j,c} * sign_slot * w_j and x_j h_j = (x_j 2^-rho_j) h'_j.
@@ -201,11 +214,11 @@ __device__ __forceinline__ void tc_inverse_body(const InvArgs& a, int m, int ni,
 
   // ---- the chain of this thread's ring
   const SeedData sd = a.seed[(size_t)ni * T + mi];
-  const int t = a.ring0 + tile * kTcRings + tid;
+  const int t = inv_ring(a, tile, tid);
   double x = 0.0, y = 0.0, v = 0.0;
   int E = 0;
   bool north = true;
-  if (t < a.nring) {
+  if (t >= 0) {
     const RingData rd = a.ring[t];
     seed_value(sd, rd, x, E);
     v = rd.v;
@@ -346,7 +359,7 @@ __device__ __forceinline__ void tc_inverse_body(const InvArgs& a, int m, int ni,
     }
   }
 
-  if (ok && t < a.nring) {
+  if (ok && t >= 0) {
     // value = 2^(eps_c - 110) sum_s 256^(12 - s) L_s = 2^(eps_c - 38) (X + 2^-24 Y)
 #pragma unroll
     for (int b = 0; b < NBX; ++b) {
@@ -380,8 +393,8 @@ __global__ void __launch_bounds__(kTcRings, 4) theta_inverse_tc_kernel(InvArgs a
   const int l0 = a.seed[(size_t)ni * (2 * L - 1) + m + L - 1].l0;
   if (l0 >= L) {                 // no degree of this order: its ring values are 0
     constexpr int NBX = PAIR ? 2 * NB : NB;
-    const int t = a.ring0 + tile * kTcRings + (int)threadIdx.x;
-    if (t >= a.nring) return;
+    const int t = inv_ring(a, tile, (int)threadIdx.x);
+    if (t < 0) return;
     for (int b = 0; b < NBX; ++b) {
       const Slot sl = slot_of<NB, PAIR>(b, blockIdx.z * NB, a.nsig, a.nN, ni, m, n, L);
       if (sl.sig_off < 0) continue;
@@ -391,8 +404,15 @@ __global__ void __launch_bounds__(kTcRings, 4) theta_inverse_tc_kernel(InvArgs a
     }
     return;
   }
-  const int t_lo = a.ring0 + tile * kTcRings, t_hi = min(a.nring, t_lo + kTcRings) - 1;
-  const bool diff = a.ring[t_lo].diff || a.ring[t_hi].diff;
+  // the form of the tile: the difference form if any of its rings lies in a polar cap (the caps
+  // are contiguous at both ends, so the ends of the tile's two ring ranges decide)
+  const int nr = a.nring - a.ring0, half = (nr + 1) / 2;
+  const int q0 = tile * (kTcRings / 2), q1 = min(half, q0 + kTcRings / 2) - 1;
+  bool diff = a.ring[a.ring0 + q0].diff || a.ring[a.ring0 + q1].diff;
+  if (q0 < nr - half) {
+    const int r1 = min(nr - half, q0 + kTcRings / 2) - 1;
+    diff = diff || a.ring[a.nring - 1 - q0].diff || a.ring[a.nring - 1 - r1].diff;
+  }
   if (diff) tc_inverse_body<NB, PAIR, true>(a, m, ni, n, tile, l0, smem);
   else tc_inverse_body<NB, PAIR, false>(a, m, ni, n, tile, l0, smem);
 }
@@ -400,7 +420,7 @@ __global__ void __launch_bounds__(kTcRings, 4) theta_inverse_tc_kernel(InvArgs a
 template <int NB, bool PAIR>
 cudaError_t launch_inv_tc(const InvArgs& a, cudaStream_t st) {
   static_assert(kSmemBytes <= kSmemRequest, "shared memory layout");
-  const int ntiles = (a.nring - a.ring0 + kTcRings - 1) / kTcRings;
+  const int ntiles = ((a.nring - a.ring0 + 1) / 2 + kTcRings / 2 - 1) / (kTcRings / 2);
   if (ntiles == 0) return cudaSuccess;
   auto kern = theta_inverse_tc_kernel<NB, PAIR>;
   cudaError_t e = set_dynamic_smem((const void*)kern, kSmemRequest);
@@ -1046,10 +1066,10 @@ __global__ void __launch_bounds__(kTcRings, 3) theta_operator_tc_kernel(OpArgs a
   const uint32_t sA_addr = tc::smem_addr(sA), sB_addr = tc::smem_addr(sB);
   if (tid == 0) bulk_copy_g2s(sA_addr, dig, kOpABytes, tc::smem_addr(&full[0]));
 
-  // this thread's digit-split column and ring half (threads 0..31)
-  const int bn = tid % kOpCols, bh = tid / kOpCols;
+  // this thread's digit-split column and ring pair of every chunk (all 128 threads)
+  const int bn = tid % kOpCols, bq = tid / kOpCols;
   const int bm = m0 + 2 * (bn >> 1);
-  const bool bact = tid < 2 * kOpCols && bm <= a.mhi;
+  const bool bact = bm <= a.mhi;
   const int bk = bm >= 0 ? bm : bm + a.FW;
   const double2* Fs = a.F + (size_t)s * a.R * a.FW;
 
@@ -1060,31 +1080,27 @@ __global__ void __launch_bounds__(kTcRings, 3) theta_operator_tc_kernel(OpArgs a
   bool ok = true;
   for (int kc = 0; kc < a.nk; ++kc) {
     const int st = kc & 1;
-    if (tid < 2 * kOpCols) {
-      uint32_t w[kDigits][4];
-      uint2 q0 = make_uint2(0, 0);
+    {
+      uint2 q[2];
       const int ce = ce_s[bn];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int tp = kc * kTcK + 8 * bh + u;
+      for (int u = 0; u < 2; ++u) {
+        const int tp = kc * kTcK + 2 * bq + u;
         double v = 0.0;
         if (bact && tp < a.R) {
-          const double2 f = Fs[(size_t)tp * a.FW + bk];
-          v = (bn & 1) ? f.y : f.x;
+          const double* f = reinterpret_cast<const double*>(Fs + (size_t)tp * a.FW + bk);
+          v = f[bn & 1];
         }
-        const uint2 q = offset_digits(v, ce);
-        if (u & 1) {
-          w[0][u >> 1] = digit_pair(q0.y, q.y, 2);
-          w[1][u >> 1] = digit_pair(q0.y, q.y, 1);
-          w[2][u >> 1] = digit_pair(q0.y, q.y, 0);
-          w[3][u >> 1] = digit_pair(q0.x, q.x, 3);
-          w[4][u >> 1] = digit_pair(q0.x, q.x, 2);
-          w[5][u >> 1] = digit_pair(q0.x, q.x, 1);
-          w[6][u >> 1] = digit_pair(q0.x, q.x, 0);
-        } else {
-          q0 = q;
-        }
+        q[u] = offset_digits(v, ce);
       }
+      uint32_t w[kDigits];
+      w[0] = digit_pair(q[0].y, q[1].y, 2);
+      w[1] = digit_pair(q[0].y, q[1].y, 1);
+      w[2] = digit_pair(q[0].y, q[1].y, 0);
+      w[3] = digit_pair(q[0].x, q[1].x, 3);
+      w[4] = digit_pair(q[0].x, q[1].x, 2);
+      w[5] = digit_pair(q[0].x, q[1].x, 1);
+      w[6] = digit_pair(q[0].x, q[1].x, 0);
       // this stage's previous MMAs (chunk kc - 2) must be done before it is rewritten
       if (kc >= 2 && !tc::mbar_wait(tc::smem_addr(&done[st]), (uint32_t)(((kc >> 1) - 1) & 1))) {
         set_status(tc::kStatusMmaWait);
@@ -1093,8 +1109,7 @@ __global__ void __launch_bounds__(kTcRings, 3) theta_operator_tc_kernel(OpArgs a
       unsigned char* bst = sB + st * kOpBBytes;
 #pragma unroll
       for (int i = 0; i < kDigits; ++i)
-        *reinterpret_cast<uint4*>(bst + kmajor_off(kLevelCols * i + bn, 8 * bh)) =
-            make_uint4(w[i][0], w[i][1], w[i][2], w[i][3]);
+        *reinterpret_cast<uint32_t*>(bst + kmajor_off(kLevelCols * i + bn, 2 * bq)) = w[i];
     }
     tc::fence_proxy_async();
     __syncthreads();

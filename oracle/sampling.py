@@ -63,20 +63,34 @@ def w_hat(mp: np.ndarray) -> np.ndarray:
     return out
 
 
-def mw_theta_weights(Lp: int) -> np.ndarray:
+def mw_theta_weights(Lp: int, dtype=np.float64) -> np.ndarray:
     """Theta quadrature weights q_t, t < Lp, of the MW sampling theorem at bandlimit Lp.
 
     sum_t q_t g(theta_t) = int_0^pi g(theta) sin(theta) dtheta for every g whose torus extension
     is even about pi and has frequencies |k| <= Lp-1 (module readings: fold +1, constant 1/T).
+    ``dtype`` float64, or np.longdouble for the extended-precision mode (the same sums, with the
+    positions, phases and w_hat in extended precision).
     """
     T = 2 * Lp - 1
-    th = mw_torus_thetas(Lp, dtype=np.float64)           # theta_t on the torus, t < T
     k = np.arange(-(Lp - 1), Lp)
-    wk = w_hat(k)
-    # w(theta_t) = sum_k w_hat(k) e^{-i k theta_t}   (reading: sign of the synthesis)
-    E = np.exp(-1j * np.outer(th, k))
+    if dtype == np.longdouble:
+        th = mw_torus_thetas(Lp)                          # extended precision
+        wk = np.zeros(len(k), dtype=np.clongdouble)
+        even = (k % 2) == 0
+        wk[even] = np.longdouble(2) / (np.longdouble(1) - k[even].astype(np.longdouble) ** 2)
+        wk[k == 1] = 1j * (PI_LD / 2)
+        wk[k == -1] = -1j * (PI_LD / 2)
+        ang = -np.outer(th, k.astype(np.longdouble))
+        E = np.empty(ang.shape, dtype=np.clongdouble)
+        E.real = np.cos(ang)
+        E.imag = np.sin(ang)
+    else:
+        th = mw_torus_thetas(Lp, dtype=np.float64)       # theta_t on the torus, t < T
+        wk = w_hat(k)
+        # w(theta_t) = sum_k w_hat(k) e^{-i k theta_t}   (reading: sign of the synthesis)
+        E = np.exp(-1j * np.outer(th, k))
     w = E @ wk
-    q = np.empty(Lp, dtype=np.complex128)
+    q = np.empty(Lp, dtype=w.dtype)
     for t in range(Lp):
         zeta = 0.0 if t == Lp - 1 else 1.0
         q[t] = (w[t] + zeta * w[2 * Lp - 2 - t]) / T      # reflect: theta_{2L'-2-t} = 2 pi - theta_t

@@ -1,7 +1,10 @@
 """Spin-s spherical-harmonic and Wigner transforms on MW sampling -- the oracle (test infrastructure).
 
 Everything is a direct sum in float64 (no FFT); exponentials are built from exactly reduced
-integer phases.  Array conventions (shared with the GPU library's boundary, written out here
+integer phases.  ``exact=True`` (MW sphere and Wigner transforms) runs the same algorithm with the
+d-functions, weights, phases and every sum in numpy's extended precision (np.longdouble: 80-bit on
+x86-64, binary128 on aarch64) and rounds once to complex128 at the end (``keep=True`` returns the
+extended-precision result).  Array conventions (shared with the GPU library's boundary, written out here
 independently):
 
 * sphere signal   f[..., t, p]           t < L rings (theta_t), p < 2L-1 (phi_p)
@@ -33,25 +36,33 @@ from .wigner import PI_LD, wigner_d_table
 _CHUNK_BYTES = 256 << 20
 
 
-def _expi_pi(num, den: int) -> np.ndarray:
+def _cdtype(dtype):
+    """The complex type of a real type (float64 -> complex128, longdouble -> clongdouble)."""
+    return np.clongdouble if dtype == np.longdouble else np.complex128
+
+
+def _expi_pi(num, den: int, dtype=np.float64) -> np.ndarray:
     """exp(i pi num/den) for integer arrays num, reduced exactly modulo 2 den."""
     r = np.mod(np.asarray(num, dtype=np.int64), 2 * den)
     ang = r.astype(np.longdouble) * PI_LD / np.longdouble(den)
-    return (np.cos(ang) + 1j * np.sin(ang)).astype(np.complex128)
+    out = np.empty(ang.shape, dtype=np.clongdouble)
+    out.real = np.cos(ang)
+    out.imag = np.sin(ang)
+    return out.astype(_cdtype(dtype))
 
 
-def phi_dft_matrix(L: int, sign: int) -> np.ndarray:
+def phi_dft_matrix(L: int, sign: int, dtype=np.float64) -> np.ndarray:
     """E[p, j] = exp(sign * i m_j phi_p), m_j = j - (L-1), phi_p = 2 pi p/(2L-1)."""
     T = 2 * L - 1
     p = np.arange(T)[:, None]
     m = np.arange(-(L - 1), L)[None, :]
-    return _expi_pi(sign * 2 * p * m, T)
+    return _expi_pi(sign * 2 * p * m, T, dtype)
 
 
-def ell_factor(L: int, spin: int) -> np.ndarray:
+def ell_factor(L: int, spin: int, dtype=np.float64) -> np.ndarray:
     """c_l = (-1)^s sqrt((2l+1)/(4 pi)), l < L (Eq. disc_sh_expanded)."""
-    ell = np.arange(L)
-    return (-1.0) ** spin * np.sqrt((2 * ell + 1) / (4 * np.pi))
+    ell = np.arange(L).astype(np.longdouble)
+    return ((-1.0) ** spin * np.sqrt((2 * ell + 1) / (4 * PI_LD))).astype(dtype)
 
 
 def coeff_mask(L: int, n: int) -> np.ndarray:
@@ -62,48 +73,55 @@ def coeff_mask(L: int, n: int) -> np.ndarray:
 
 
 # ----------------------------------------------------------------------------- inverse
-def _theta_inverse(flm: np.ndarray, L: int, n: int, scale: np.ndarray, thetas) -> np.ndarray:
+def _theta_inverse(flm: np.ndarray, L: int, n: int, scale: np.ndarray, thetas, dtype=np.float64) -> np.ndarray:
     """f~[..., t, m] = sum_l scale_l flm[..., l, m] d^l_{m,n}(theta_t) (Eq. disc_ish_expanded)."""
     flm = np.where(coeff_mask(L, n), flm, 0) * scale[:, None]
-    out = np.zeros(flm.shape[:-2] + (len(thetas), 2 * L - 1), dtype=np.complex128)
-    per_ring = L * (2 * L - 1) * 8
+    out = np.zeros(flm.shape[:-2] + (len(thetas), 2 * L - 1), dtype=_cdtype(dtype))
+    per_ring = L * (2 * L - 1) * np.dtype(dtype).itemsize
     step = max(1, _CHUNK_BYTES // per_ring)
     for a in range(0, len(thetas), step):
-        D = wigner_d_table(np.arange(L), n, thetas[a:a + step])          # [l, m, t]
+        D = wigner_d_table(np.arange(L), n, thetas[a:a + step], dtype)   # [l, m, t]
         out[..., a:a + step, :] = np.einsum("...lm,lmt->...tm", flm, D)
     return out
 
 
-def inverse(flm: np.ndarray, L: int, spin: int, rings=None) -> np.ndarray:
-    """Inverse spin-s SHT on the MW grid; ``rings`` selects theta indices (default: all L)."""
+def _finish(x: np.ndarray, keep: bool) -> np.ndarray:
+    """The result as complex128, or as computed when ``keep``."""
+    return x if keep else x.astype(np.complex128)
+
+
+def inverse(flm: np.ndarray, L: int, spin: int, rings=None, exact: bool = False, keep: bool = False) -> np.ndarray:
+    """Inverse spin-s SHT on the MW grid; ``rings`` selects theta indices (default: all L).
+    ``exact``: extended-precision d-functions and sums (module docstring)."""
+    dt = np.longdouble if exact else np.float64
     th = mw_thetas(L)
     if rings is not None:
         th = th[np.asarray(rings)]
-    ft = _theta_inverse(np.asarray(flm, dtype=np.complex128), L, -spin, ell_factor(L, spin), th)
-    return ft @ phi_dft_matrix(L, +1).T                                   # Eq. disc_ish_fft
+    ft = _theta_inverse(np.asarray(flm).astype(_cdtype(dt)), L, -spin, ell_factor(L, spin, dt), th, dt)
+    return _finish(ft @ phi_dft_matrix(L, +1, dt).T, keep)               # Eq. disc_ish_fft
 
 
 # ----------------------------------------------------------------------------- forward
-def _upsample_matrices(L: int):
+def _upsample_matrices(L: int, dtype=np.float64):
     """Matrices of the theta torus extension / Fourier coefficients / upsampled evaluation."""
     T = 2 * L - 1
     Tu = 4 * L - 1                       # torus length of the MW grid at bandlimit 2L
     k = np.arange(-(L - 1), L)
     tt = np.arange(T)
     uu = np.arange(2 * L)
-    coef = _expi_pi(-np.outer(k, 2 * tt + 1), T) / T                      # [k, t'] e^{-ik theta_t'}/T
-    up = _expi_pi(np.outer(2 * uu + 1, k), Tu)                              # [u, k]  e^{+ik theta'_u}
+    coef = _expi_pi(-np.outer(k, 2 * tt + 1), T, dtype) / dtype(T)        # [k, t'] e^{-ik theta_t'}/T
+    up = _expi_pi(np.outer(2 * uu + 1, k), Tu, dtype)                       # [u, k]  e^{+ik theta'_u}
     return coef, up
 
 
-def _phi_forward(f: np.ndarray, L: int, orders=None) -> np.ndarray:
+def _phi_forward(f: np.ndarray, L: int, orders=None, dtype=np.float64) -> np.ndarray:
     """F[..., t, m] = sum_p f[..., t, p] e^{-i m phi_p} (Eq. disc_sh_fft without q_Phi).
 
     ``orders``: optional subset of the orders m (default: all |m| < L, in increasing order)."""
-    E = phi_dft_matrix(L, -1)
+    E = phi_dft_matrix(L, -1, dtype)
     if orders is not None:
         E = E[:, np.asarray(orders) + L - 1]
-    return np.asarray(f, dtype=np.complex128) @ E
+    return np.asarray(f).astype(_cdtype(dtype)) @ E
 
 
 def _extend(F: np.ndarray, L: int, n: int, orders=None) -> np.ndarray:
@@ -115,7 +133,7 @@ def _extend(F: np.ndarray, L: int, n: int, orders=None) -> np.ndarray:
     parity (-1)^{m+s}, so that every exact theta quadrature gives the same result."""
     m = np.arange(-(L - 1), L) if orders is None else np.asarray(orders)
     sigma = (-1.0) ** ((m - n) % 2)                                         # (-1)^{m+s}
-    G = np.zeros(F.shape[:-2] + (2 * L - 1, F.shape[-1]), dtype=np.complex128)
+    G = np.zeros(F.shape[:-2] + (2 * L - 1, F.shape[-1]), dtype=F.dtype)
     G[..., :L, :] = F
     G[..., L - 1, :] = F[..., L - 1, :] * (1 + sigma) / 2
     G[..., L:, :] = (F[..., :L - 1, :] * sigma)[..., ::-1, :]               # G[2L-2-t] = sigma F[t]
@@ -123,20 +141,20 @@ def _extend(F: np.ndarray, L: int, n: int, orders=None) -> np.ndarray:
 
 
 def _theta_forward_upsampled(Gu: np.ndarray, L: int, n: int, scale: np.ndarray, ells,
-                             orders=None) -> np.ndarray:
+                             orders=None, dtype=np.float64) -> np.ndarray:
     """flm[..., i, m] = scale_l sum_u q_u d^l_{m,n}(theta'_u) q_Phi Gu[..., u, m], l = ells[i]."""
     ells = np.asarray(ells)
     mcols = np.arange(2 * L - 1) if orders is None else np.asarray(orders) + L - 1
-    q = mw_theta_weights(2 * L)
-    qphi = 2 * np.pi / (2 * L - 1)
+    q = mw_theta_weights(2 * L, dtype)
+    qphi = (2 * PI_LD / (2 * L - 1)).astype(dtype)
     thu = mw_thetas(2 * L)
     W = Gu * (q * qphi)[:, None]
-    out = np.zeros(Gu.shape[:-2] + (len(ells), len(mcols)), dtype=np.complex128)
-    per_l = (2 * L - 1) * 2 * L * 8 * 2
+    out = np.zeros(Gu.shape[:-2] + (len(ells), len(mcols)), dtype=_cdtype(dtype))
+    per_l = (2 * L - 1) * 2 * L * np.dtype(dtype).itemsize * 2
     step = max(1, _CHUNK_BYTES // per_l)
     for a in range(0, len(ells), step):
         sel = ells[a:a + step]
-        D = wigner_d_table(sel, n, thu)                                      # [i, m', u], m' width max(sel)
+        D = wigner_d_table(sel, n, thu, dtype)                               # [i, m', u], m' width max(sel)
         M = int(sel.max())
         D = D[:, M - (L - 1):M + L, :] if M >= L - 1 else np.pad(D, ((0, 0), (L - 1 - M, L - 1 - M), (0, 0)))
         out[..., a:a + step, :] = np.einsum("...um,imu->...im", W, D[:, mcols, :]) * scale[sel][:, None]
@@ -144,15 +162,18 @@ def _theta_forward_upsampled(Gu: np.ndarray, L: int, n: int, scale: np.ndarray, 
     return np.where(mask, out, 0)
 
 
-def forward(f: np.ndarray, L: int, spin: int, ells=None, orders=None) -> np.ndarray:
+def forward(f: np.ndarray, L: int, spin: int, ells=None, orders=None, exact: bool = False,
+            keep: bool = False) -> np.ndarray:
     """Forward spin-s SHT on the MW grid; ``ells`` selects output rows (default: all l < L) and
-    ``orders`` output columns by order m (default: all |m| < L)."""
+    ``orders`` output columns by order m (default: all |m| < L).  ``exact``: extended-precision
+    d-functions, weights and sums (module docstring)."""
+    dt = np.longdouble if exact else np.float64
     if ells is None:
         ells = np.arange(L)
-    coef, up = _upsample_matrices(L)
-    G = _extend(_phi_forward(f, L, orders), L, -spin, orders)
+    coef, up = _upsample_matrices(L, dt)
+    G = _extend(_phi_forward(f, L, orders, dt), L, -spin, orders)
     Gu = up @ (coef @ G)
-    return _theta_forward_upsampled(Gu, L, -spin, ell_factor(L, spin), ells, orders)
+    return _finish(_theta_forward_upsampled(Gu, L, -spin, ell_factor(L, spin, dt), ells, orders, dt), keep)
 
 
 # ----------------------------------------------------------------------------- adjoints (Sec. 5.2)
@@ -337,41 +358,48 @@ def adjoint_forward_real(flm_bar_pos: np.ndarray, L: int) -> np.ndarray:
 
 
 # ----------------------------------------------------------------------------- Wigner (Sec. 2.3, 4.5)
-def _gamma_matrix(N: int, sign: int) -> np.ndarray:
+def _gamma_matrix(N: int, sign: int, dtype=np.float64) -> np.ndarray:
     """E[k, j] = exp(sign i n_j gamma_k), n_j = j-(N-1), gamma_k = 2 pi k/(2N-1)."""
     K = 2 * N - 1
     k = np.arange(K)[:, None]
     nn = np.arange(-(N - 1), N)[None, :]
-    return _expi_pi(sign * 2 * k * nn, K)
+    return _expi_pi(sign * 2 * k * nn, K, dtype)
 
 
-def wigner_inverse(flmn: np.ndarray, L: int, N: int, rings=None) -> np.ndarray:
-    """Inverse Wigner transform: f(alpha, beta, gamma) = sum (2l+1)/(8 pi^2) flmn D^{l*}_{mn}."""
-    flmn = np.asarray(flmn, dtype=np.complex128)
+def wigner_inverse(flmn: np.ndarray, L: int, N: int, rings=None, exact: bool = False,
+                   keep: bool = False) -> np.ndarray:
+    """Inverse Wigner transform: f(alpha, beta, gamma) = sum (2l+1)/(8 pi^2) flmn D^{l*}_{mn}.
+    ``exact``: extended-precision d-functions and sums (module docstring)."""
+    dt = np.longdouble if exact else np.float64
+    flmn = np.asarray(flmn).astype(_cdtype(dt))
     th = mw_thetas(L) if rings is None else mw_thetas(L)[np.asarray(rings)]
-    scale = (2 * np.arange(L) + 1) / (8 * np.pi ** 2)
+    scale = ((2 * np.arange(L).astype(np.longdouble) + 1) / (8 * PI_LD ** 2)).astype(dt)
+    E = phi_dft_matrix(L, +1, dt)
     fn = []
     for j, n in enumerate(range(-(N - 1), N)):
-        ft = _theta_inverse(flmn[..., j, :, :], L, n, scale, th)
-        fn.append(ft @ phi_dft_matrix(L, +1).T)                              # sum_m e^{i m alpha}
+        ft = _theta_inverse(flmn[..., j, :, :], L, n, scale, th, dt)
+        fn.append(ft @ E.T)                                                  # sum_m e^{i m alpha}
     fn = np.stack(fn, axis=-3)                                               # [..., n, t, p]
-    return np.einsum("kn,...ntp->...ktp", _gamma_matrix(N, +1), fn)         # sum_n e^{i n gamma}
+    return _finish(np.einsum("kn,...ntp->...ktp", _gamma_matrix(N, +1, dt), fn), keep)   # sum_n e^{i n gamma}
 
 
-def wigner_forward(f: np.ndarray, L: int, N: int, ells=None) -> np.ndarray:
-    """Forward Wigner transform: flmn = int f D^l_{mn}, as gamma-DFT plus spin-(-n) theta stages."""
-    f = np.asarray(f, dtype=np.complex128)
+def wigner_forward(f: np.ndarray, L: int, N: int, ells=None, exact: bool = False,
+                   keep: bool = False) -> np.ndarray:
+    """Forward Wigner transform: flmn = int f D^l_{mn}, as gamma-DFT plus spin-(-n) theta stages.
+    ``exact``: extended-precision d-functions, weights and sums (module docstring)."""
+    dt = np.longdouble if exact else np.float64
+    f = np.asarray(f).astype(_cdtype(dt))
     if ells is None:
         ells = np.arange(L)
-    qgam = 2 * np.pi / (2 * N - 1)
-    fn = np.einsum("kn,...ktp->...ntp", _gamma_matrix(N, -1), f) * qgam     # f_n(alpha, beta)
-    coef, up = _upsample_matrices(L)
-    ones = np.ones(L)
+    qgam = (2 * PI_LD / (2 * N - 1)).astype(dt)
+    fn = np.einsum("kn,...ktp->...ntp", _gamma_matrix(N, -1, dt), f) * qgam # f_n(alpha, beta)
+    coef, up = _upsample_matrices(L, dt)
+    ones = np.ones(L, dtype=dt)
     out = []
     for j, n in enumerate(range(-(N - 1), N)):
-        G = _extend(_phi_forward(fn[..., j, :, :], L), L, n)
-        out.append(_theta_forward_upsampled(up @ (coef @ G), L, n, ones, ells))
-    return np.stack(out, axis=-3)
+        G = _extend(_phi_forward(fn[..., j, :, :], L, None, dt), L, n)
+        out.append(_theta_forward_upsampled(up @ (coef @ G), L, n, ones, ells, None, dt))
+    return _finish(np.stack(out, axis=-3), keep)
 
 
 def wigner_inverse_s(flmn: np.ndarray, L: int, N: int, sampling: str = "mw") -> np.ndarray:

@@ -80,15 +80,18 @@ def _log_factorials(kmax: int) -> np.ndarray:
     return out
 
 
-def _descending_chain(ells: np.ndarray, n: int, b: np.ndarray, m_stop: np.ndarray, width: int) -> np.ndarray:
+def _descending_chain(ells: np.ndarray, n: int, b: np.ndarray, m_stop: np.ndarray, width: int,
+                      dtype=np.float64) -> np.ndarray:
     """Run Eq. "wigner-d-recursion" downward in m for every ell and angle b (0 < b < pi).
 
     ells: (nl,) ints with ell >= |n|.  b: (nb,) longdouble.  m_stop: (nl, nb) lowest m kept.
     Returns V of shape (nl, 2*width+1, nb) with V[i, m+width, j] = d^{ell_i}_{m,n}(b_j) for
-    m_stop[i,j] <= m <= ell_i and 0 elsewhere.
+    m_stop[i,j] <= m <= ell_i and 0 elsewhere.  ``dtype`` is the arithmetic of the recursion
+    (float64, or np.longdouble for the extended-precision mode); the seeds are always evaluated
+    in extended precision.
     """
     nl, nb = len(ells), len(b)
-    out = np.zeros((nl, 2 * width + 1, nb))
+    out = np.zeros((nl, 2 * width + 1, nb), dtype=dtype)
     if nl == 0 or nb == 0:
         return out
     L2 = np.asarray(ells, dtype=np.int64)[:, None] * np.ones((1, nb), dtype=np.int64)  # ell, (nl, nb)
@@ -102,8 +105,8 @@ def _descending_chain(ells: np.ndarray, n: int, b: np.ndarray, m_stop: np.ndarra
             + (L2 - n).astype(np.longdouble) * log_s + (L2 + n).astype(np.longdouble) * log_c)
     lg2 = logd / LN2_LD
     E = np.floor(lg2).astype(np.int64)                      # exact power-of-two part
-    mant = np.exp2(lg2 - E.astype(np.longdouble)).astype(np.float64)  # in [1, 2)
-    sign = np.where((L2 - n) % 2 == 0, 1.0, -1.0)             # (-sin(b/2))^{l-n}
+    mant = np.exp2(lg2 - E.astype(np.longdouble)).astype(dtype)      # in [1, 2)
+    sign = np.where((L2 - n) % 2 == 0, 1.0, -1.0).astype(dtype)   # (-sin(b/2))^{l-n}
     u_cur = sign * mant                                       # d_m   = u_cur * 2**E
     u_next = np.zeros_like(u_cur)                             # d_{m+1} (= 0 at m = l)
 
@@ -113,7 +116,7 @@ def _descending_chain(ells: np.ndarray, n: int, b: np.ndarray, m_stop: np.ndarra
     # sum_m d^2 at l = 2047 near the poles); rounded once, the error stays ~1e-15.
     M = int(np.max(ells))
     mm_all = np.arange(-M - 1, M + 2).astype(np.longdouble)[:, None]
-    lam_table = ((np.longdouble(n) - mm_all * np.cos(b)[None, :]) / np.sin(b)[None, :]).astype(np.float64)
+    lam_table = ((np.longdouble(n) - mm_all * np.cos(b)[None, :]) / np.sin(b)[None, :]).astype(dtype)
     rows = np.arange(nl)[:, None]
     cols = np.arange(nb)[None, :]
     out[rows, L2 + width, cols] = np.where(L2 >= m_stop, np.ldexp(u_cur, E), 0.0)
@@ -124,14 +127,14 @@ def _descending_chain(ells: np.ndarray, n: int, b: np.ndarray, m_stop: np.ndarra
         live = (m - 1 >= m_stop) & (m - 1 >= -L2)
         p1 = np.where(live, (L2 - m + 1) * (L2 + m), 1).astype(np.longdouble)  # (l-m+1)(l+m)
         p0 = np.where(live, (L2 - m) * (L2 + m + 1), 0).astype(np.longdouble)  # (l-m)(l+m+1)
-        a_m1 = (np.longdouble(2) / np.sqrt(p1)).astype(np.float64)              # a_{m-1}
-        ratio = np.sqrt(p0 / p1).astype(np.float64)                              # a_{m-1}/a_m (0 at m=l)
+        a_m1 = (np.longdouble(2) / np.sqrt(p1)).astype(dtype)                   # a_{m-1}
+        ratio = np.sqrt(p0 / p1).astype(dtype)                                   # a_{m-1}/a_m (0 at m=l)
         lam = lam_table[np.clip(m, -M - 1, M + 1) + M + 1, cols]                 # lambda_m
         u_new = lam * a_m1 * u_cur - ratio * u_next
-        u_new = np.where(live, u_new, 0.0)
+        u_new = np.where(live, u_new, dtype(0))
         # running renormalisation (Sec. 3.4): rescale the live pair to unit size, exactly.
         r = np.maximum(np.abs(u_new), np.abs(u_cur))
-        _, e = np.frexp(np.where(live & (r > 0), r, 1.0))
+        _, e = np.frexp(np.where(live & (r > 0), r, dtype(1)))
         e = np.where(live & (r > 0), e, 0)
         u_new = np.ldexp(u_new, -e)
         u_cur = np.ldexp(u_cur, -e)
@@ -144,18 +147,19 @@ def _descending_chain(ells: np.ndarray, n: int, b: np.ndarray, m_stop: np.ndarra
     return out
 
 
-def wigner_d_table(ells, n: int, betas) -> np.ndarray:
+def wigner_d_table(ells, n: int, betas, dtype=np.float64) -> np.ndarray:
     """d^l_{m,n}(beta) for every l in ``ells``, every |m| <= l and every beta in ``betas``.
 
-    Returns D of shape (len(ells), 2*M+1, len(betas)) in float64, M = max(ells), with
-    D[i, m+M, j] = d^{ells[i]}_{m,n}(betas[j]); entries with |m| > l or l < |n| are 0.
-    ``betas`` in [0, pi]; pass ``np.longdouble`` values for full accuracy of the seeds.
+    Returns D of shape (len(ells), 2*M+1, len(betas)) in ``dtype`` (float64, or np.longdouble for
+    the extended-precision mode), M = max(ells), with D[i, m+M, j] = d^{ells[i]}_{m,n}(betas[j]);
+    entries with |m| > l or l < |n| are 0.  ``betas`` in [0, pi]; pass ``np.longdouble`` values for
+    full accuracy of the seeds.
     """
     ells = np.atleast_1d(np.asarray(ells, dtype=np.int64))
     betas = np.atleast_1d(np.asarray(betas)).astype(np.longdouble)
     M = int(ells.max()) if len(ells) else 0
     nl, nb = len(ells), len(betas)
-    D = np.zeros((nl, 2 * M + 1, nb))
+    D = np.zeros((nl, 2 * M + 1, nb), dtype=dtype)
     tol = np.longdouble(8) * np.longdouble(np.finfo(np.float64).eps)
     north = betas <= tol
     south = np.abs(betas - PI_LD) <= tol
@@ -177,14 +181,14 @@ def wigner_d_table(ells, n: int, betas) -> np.ndarray:
     # Split point m* = round(n cos beta), clipped to [-l, l] (Sec. 3.3 reading, module docstring).
     mstar = np.rint(n * np.cos(b.astype(np.float64))).astype(np.int64)[None, :]
     mstar = np.clip(mstar, -L_ok[:, None], L_ok[:, None])
-    A = _descending_chain(L_ok, n, b, mstar, M)                      # m in [m*, l] at beta
-    B = _descending_chain(L_ok, n, PI_LD - b, 1 - mstar, M)          # m' in [1-m*, l] at pi-beta
-    sgn = np.where((L_ok + n) % 2 == 0, 1.0, -1.0)[:, None, None]
+    A = _descending_chain(L_ok, n, b, mstar, M, dtype)               # m in [m*, l] at beta
+    B = _descending_chain(L_ok, n, PI_LD - b, 1 - mstar, M, dtype)   # m' in [1-m*, l] at pi-beta
+    sgn = np.where((L_ok + n) % 2 == 0, 1.0, -1.0).astype(dtype)[:, None, None]
     B_reflected = sgn * B[:, ::-1, :]                                  # m = -m'
     mgrid = np.arange(-M, M + 1)[None, :, None]
     useA = mgrid >= mstar[:, None, :]
     blockD = np.where(useA, A, B_reflected)
-    blockD = np.where(np.abs(mgrid) <= L_ok[:, None, None], blockD, 0.0)
+    blockD = np.where(np.abs(mgrid) <= L_ok[:, None, None], blockD, dtype(0))
     D[np.ix_(idx_l, np.arange(2 * M + 1), idx_b)] = blockD
     return D
 

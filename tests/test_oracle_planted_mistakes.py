@@ -16,6 +16,7 @@ Mistakes planted, with the pin that must catch them:
   * ln((k+1)!) for ln(k!) in the seeds                      -> closed-form d^1, d^2
   * the DH weight's sine series one term too long           -> exact integration of P_n, n < 2L
   * the MWSS pole rings counted twice                       -> exact integration of cos^n
+  * float64 MW weights inside the extended-precision mode   -> its round trip at extended rounding
 The pins of the d-functions, the samplings and the transforms live in ``test_oracle_wigner``,
 ``test_oracle_samplings`` and ``test_oracle_transforms``.
 """
@@ -43,15 +44,16 @@ def test_the_pins_pass_without_a_planted_mistake():
 
 
 def test_dropped_spin_sign_in_c_l(monkeypatch):
-    monkeypatch.setattr(T, "ell_factor", lambda L, spin: np.sqrt((2 * np.arange(L) + 1) / (4 * np.pi)))
+    monkeypatch.setattr(T, "ell_factor", lambda L, spin, dtype=np.float64:
+                        np.sqrt((2 * np.arange(L) + 1) / (4 * np.pi)).astype(dtype))
     _fails(pins.test_inverse_brute_force_from_jacobi, 4, 1)
 
 
 def test_transposed_d_function(monkeypatch):
     orig = T.wigner_d_table
 
-    def transposed(ells, n, thetas):
-        D = orig(ells, n, thetas)                       # [l, m, t], m centred on the middle column
+    def transposed(ells, n, thetas, dtype=np.float64):
+        D = orig(ells, n, thetas, dtype)                       # [l, m, t], m centred on the middle column
         w = D.shape[1]
         m = np.arange(w) - (w - 1) // 2
         return D * ((-1.0) ** ((m - n) % 2))[None, :, None]    # d^l_{n,m} = (-1)^{m-n} d^l_{m,n}
@@ -62,7 +64,7 @@ def test_transposed_d_function(monkeypatch):
 
 def test_flipped_phi_dft_sign(monkeypatch):
     orig = T.phi_dft_matrix
-    monkeypatch.setattr(T, "phi_dft_matrix", lambda L, sign: orig(L, -sign))
+    monkeypatch.setattr(T, "phi_dft_matrix", lambda L, sign, dtype=np.float64: orig(L, -sign, dtype))
     pins.test_round_trip(8, 0)                          # the round trip alone cannot see it
     _fails(pins.test_inverse_gives_closed_form_Ylm, 2, 1)
 
@@ -79,7 +81,7 @@ def test_dropped_torus_extension_parity(monkeypatch):
 
 
 def test_uniform_theta_weights(monkeypatch):
-    monkeypatch.setattr(T, "mw_theta_weights", lambda Lp: np.full(Lp, 2.0 / Lp))
+    monkeypatch.setattr(T, "mw_theta_weights", lambda Lp, dtype=np.float64: np.full(Lp, 2.0 / Lp, dtype=dtype))
     _fails(pins.test_round_trip, 17, 1)
 
 
@@ -91,15 +93,15 @@ def test_wrong_ring_positions(monkeypatch):
 
 def test_flipped_gamma_dft_sign(monkeypatch):
     orig = T._gamma_matrix
-    monkeypatch.setattr(T, "_gamma_matrix", lambda N, sign: orig(N, -sign))
+    monkeypatch.setattr(T, "_gamma_matrix", lambda N, sign, dtype=np.float64: orig(N, -sign, dtype))
     _fails(pins.test_wigner_inverse_of_unit_is_conjugate_D)
 
 
 def test_sphere_factor_in_the_wigner_inverse(monkeypatch):
     orig = T._theta_inverse
 
-    def sphere_scaled(flm, L, n, scale, thetas):
-        return orig(flm, L, n, (-1.0) ** n * np.sqrt((2 * np.arange(L) + 1) / (4 * np.pi)), thetas)
+    def sphere_scaled(flm, L, n, scale, thetas, dtype=np.float64):
+        return orig(flm, L, n, (-1.0) ** n * np.sqrt((2 * np.arange(L) + 1) / (4 * np.pi)), thetas, dtype)
 
     monkeypatch.setattr(T, "_theta_inverse", sphere_scaled)
     _fails(pins.test_wigner_inverse_of_unit_is_conjugate_D)
@@ -145,3 +147,13 @@ def test_mwss_poles_counted_twice(monkeypatch):
 
     monkeypatch.setattr(spins, "mwss_theta_weights", doubled)
     _fails(spins.test_mwss_weights_integrate_even_torus_functions, 12)
+
+
+def test_float64_weights_inside_the_extended_mode(monkeypatch):
+    """The extended-precision mode fed the float64 MW weights: its round-trip pin must fail."""
+    import test_oracle_exact as epins
+    if epins.EPS_LD > 1e-17:
+        pytest.skip("np.longdouble is not wider than float64 here")
+    orig = T.mw_theta_weights
+    monkeypatch.setattr(T, "mw_theta_weights", lambda Lp, dtype=np.float64: orig(Lp).astype(dtype))
+    _fails(epins.test_exact_round_trip_at_extended_rounding_level, 8, 0)

@@ -22,7 +22,7 @@ def _built():
     build.build()
 
 
-@pytest.mark.parametrize("L,spin,B", [(64, 0, 1), (48, 2, 2)])
+@pytest.mark.parametrize("L,spin,B", [(64, 0, 1), (32, 2, 2)])
 def test_sphere_inverse_and_forward_match_extended_oracle(L, spin, B):
     from paper_2311_14670_gb300 import Plan
     p = Plan(L, spin=spin, max_batch=B)

@@ -86,15 +86,17 @@ __global__ void coef_kernel(double* coef, const int* n_of, int nN, int L) {
   }
 }
 
-// Block-normalised coefficients for the float64 kernels.  Within a block of kNormBlock steps that
-// starts at b0 = l0 + kNormBlock k, the plain recurrence is carried for u^j = d^j / gamma_j with
-//   gamma_{b0-1} = gamma_{b0} = 1,  gamma_{j+1} = C_j gamma_{j-1}  (= 1 where C_j = 0, i.e. j = l0),
+// Normalised coefficients for the float64 kernels.  Along the chain of an order, from l0 =
+// max(|m|, |n|), the plain recurrence is carried for u^j = d^j / gamma_j with
+//   gamma_{l0-1} = gamma_{l0} = 1,  gamma_{j+1} = C_j gamma_{j-1}  (= 1 where C_j = 0, i.e. j = l0),
 // which turns d^{j+1} = P_j d^j - C_j d^{j-1} into u^{j+1} = (P_j gamma_j/gamma_{j+1}) u^j - u^{j-1}
 // (2 FMA per step instead of 3).  The difference form carries e^j = eta_j ehat^j with
-//   eta_{b0} = 1,  eta_{j+1} = C_j eta_j  (= 1 where C_j = 0),
+//   eta_{l0} = 1,  eta_{j+1} = C_j eta_j  (= 1 where C_j = 0),
 // so ehat^{j+1} = (Q_j / eta_{j+1}) d^j + sigma ehat^j and d^{j+1} = sigma d^j + eta_{j+1} ehat^{j+1}.
-// At the end of a block the kernels convert back (d = gamma u, e = eta ehat).  All factors are
-// products of at most kNormBlock / 2 values C_k = O(1), so no range problem arises.
+// The kernels never convert back: the contraction takes gamma_j into the coefficient (inverse) or
+// the output scale (forward).  C_k = (k+1) sqrt((k^2-m^2)(k^2-n^2)) / (k sqrt(((k+1)^2-m^2)((k+1)^2-n^2)))
+// telescopes, so the products stay close to 1: gamma in [2^-7, 1] and eta in [2^-13, 1] for every
+// order up to L = 8192.
 __device__ void coef_terms(long long j, long long m, long long n, dd& A, dd& B, dd& C) {
   const long long j1 = j + 1;
   const long long X1 = (j1 * j1 - m * m) * (j1 * j1 - n * n);
@@ -110,57 +112,54 @@ __device__ void coef_terms(long long j, long long m, long long n, dd& A, dd& B, 
   }
 }
 
+// One thread per (n, m): the chain's steps in order, the products gamma and eta carried in
+// double-double and every table entry rounded once.
 __global__ void coefn_kernel(double* coef, const int* n_of, int nN, int L) {
   const int T = 2 * L - 1;
-  long long total = (long long)nN * T * L;
+  const long long total = (long long)nN * T;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;
        idx += (long long)gridDim.x * blockDim.x) {
-    const int j = (int)(idx % L);
-    const int mi = (int)((idx / L) % T);
-    const int ni = (int)(idx / ((long long)L * T));
+    const int mi = (int)(idx % T);
+    const int ni = (int)(idx / T);
     const long long m = mi - (L - 1);
     const long long n = n_of[ni];
-    double* out = coef + idx * kCoefPerStepN;
+    double* out = coef + idx * (long long)L * kCoefPerStepN;
     const long long am = m < 0 ? -m : m, an = n < 0 ? -n : n;
     const long long l0 = am > an ? am : an;
-    if (j < l0) {
-      for (int q = 0; q < kCoefPerStepN; ++q) out[q] = 0.0;
-      continue;
-    }
-    const long long b0 = l0 + kNormBlock * ((j - l0) / kNormBlock);
     const dd one = {1.0, 0.0};
-    dd g_prev = one, g_cur = one, g_next = one, e_cur = one, e_next = one;
-    dd A, B, C;
-    for (long long k = b0; k <= j; ++k) {
-      coef_terms(k, m, n, A, B, C);
-      const bool cz = (C.hi == 0.0);
-      g_next = cz ? one : dd_mul(C, g_prev);
-      e_next = cz ? one : dd_mul(C, e_cur);
-      if (k < j) {
-        g_prev = g_cur;
-        g_cur = g_next;
-        e_cur = e_next;
+    dd g_prev = one, g_cur = one, e_cur = one;     // gamma_{j-1}, gamma_j, eta_j
+    for (long long j = 0; j < L; ++j, out += kCoefPerStepN) {
+      if (j < l0) {
+        for (int q = 0; q < kCoefPerStepN; ++q) out[q] = 0.0;
+        continue;
       }
+      dd A, B, C;
+      coef_terms(j, m, n, A, B, C);
+      const bool cz = (C.hi == 0.0);
+      const dd g_next = cz ? one : dd_mul(C, g_prev);   // gamma_{j+1}
+      const dd e_next = cz ? one : dd_mul(C, e_cur);    // eta_{j+1}
+      const dd r = dd_div(g_cur, g_next);
+      const dd Kn = dd_mul(A, dd_sub(one, B));
+      const dd Ks = dd_neg(dd_mul(A, dd_add(one, B)));
+      const dd Kdn = dd_sub(dd_sub(Kn, one), C);
+      const dd Kds = dd_add(dd_add(Ks, one), C);
+      const dd Ap = dd_mul(A, r), Knp = dd_mul(Kn, r), Ksp = dd_mul(Ks, r);
+      const dd App = dd_div(A, e_next), Kdnp = dd_div(Kdn, e_next), Kdsp = dd_div(Kds, e_next);
+      const dd ig = dd_div(one, g_cur);
+      out[0] = Ap.hi + Ap.lo;
+      out[1] = Knp.hi + Knp.lo;
+      out[2] = Ksp.hi + Ksp.lo;
+      out[3] = g_cur.hi + g_cur.lo;
+      out[4] = g_next.hi + g_next.lo;
+      out[5] = App.hi + App.lo;
+      out[6] = Kdnp.hi + Kdnp.lo;
+      out[7] = Kdsp.hi + Kdsp.lo;
+      out[8] = e_next.hi + e_next.lo;
+      out[9] = ig.hi + ig.lo;
+      g_prev = g_cur;
+      g_cur = g_next;
+      e_cur = e_next;
     }
-    // A, B, C now belong to step j; g_cur = gamma_j, g_next = gamma_{j+1}, e_next = eta_{j+1}
-    const dd r = dd_div(g_cur, g_next);
-    const dd Kn = dd_mul(A, dd_sub(one, B));
-    const dd Ks = dd_neg(dd_mul(A, dd_add(one, B)));
-    const dd Kdn = dd_sub(dd_sub(Kn, one), C);
-    const dd Kds = dd_add(dd_add(Ks, one), C);
-    const dd Ap = dd_mul(A, r), Knp = dd_mul(Kn, r), Ksp = dd_mul(Ks, r);
-    const dd App = dd_div(A, e_next), Kdnp = dd_div(Kdn, e_next), Kdsp = dd_div(Kds, e_next);
-    const dd ig = dd_div(one, g_cur);
-    out[0] = Ap.hi + Ap.lo;
-    out[1] = Knp.hi + Knp.lo;
-    out[2] = Ksp.hi + Ksp.lo;
-    out[3] = g_cur.hi + g_cur.lo;
-    out[4] = g_next.hi + g_next.lo;
-    out[5] = App.hi + App.lo;
-    out[6] = Kdnp.hi + Kdnp.lo;
-    out[7] = Kdsp.hi + Kdsp.lo;
-    out[8] = e_next.hi + e_next.lo;
-    out[9] = ig.hi + ig.lo;
   }
 }
 
@@ -429,7 +428,7 @@ int make_plan(Plan* p) {
   bytes += coef_bytes;
   p->device_bytes = bytes;
   if (p->precision == S2GB_FP64)
-    coefn_kernel<<<1024, 256>>>(p->coef, p->n_of, nN, L);
+    coefn_kernel<<<(nN * T + 127) / 128, 128>>>(p->coef, p->n_of, nN, L);
   else
     coef_kernel<<<1024, 256>>>(p->coef, p->n_of, nN, L);
   if (launched() != cudaSuccess) return S2GB_ECUDA;

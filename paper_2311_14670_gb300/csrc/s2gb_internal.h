@@ -44,10 +44,9 @@ struct SeedData {
 
 // Recursion step j -> j+1 coefficients for one (n, m), see theta_kernels.cu.
 constexpr int kCoefPerStep = 6;  // A, C, K_north, K_south, Kd_north, Kd_south (float32 kernels)
-// Block-normalised form used by the float64 kernels (plan.cu, coefn_kernel):
+// Normalised form used by the float64 kernels (plan.cu, coefn_kernel):
 // A', K_n', K_s', gamma_j, gamma_{j+1}, A'', Kd_n'', Kd_s'', eta_{j+1}, 1/gamma_j
 constexpr int kCoefPerStepN = 10;
-constexpr int kNormBlock = 8;    // normalisation block length (steps), aligned at l0
 constexpr int kFwdChunk = 2048;  // rings per CTA of the forward theta kernel
 constexpr int kOpMaxRings = 2304;  // rings up to which the theta-direction operator is a matrix
 

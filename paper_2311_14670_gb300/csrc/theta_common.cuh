@@ -64,7 +64,7 @@ __device__ __forceinline__ void renorm(double& x, double& y, int& E) {
   }
 }
 
-// Coefficients of one step of the block-normalised recursion (layout of plan.cu's coefn_kernel).
+// Coefficients of one step of the normalised recursion (layout of plan.cu's coefn_kernel).
 struct StepN {
   double Ap, Knp, Ksp, g, gn, App, Kdnp, Kdsp, en, ig;
 };
@@ -73,8 +73,8 @@ __device__ __forceinline__ StepN stepn_at(const double* c) {
   return {c[0], c[1], c[2], c[3], c[4], c[5], c[6], c[7], c[8], c[9]};
 }
 
-// One step of the block-normalised recursion (2 FP64 instructions plain, 3 in the difference
-// form); x, y are (u^j, u^{j-1}) plain or (d^j, ehat^j) in the difference form.
+// One step of the normalised recursion (2 FP64 instructions plain, 3 in the difference form);
+// x, y are (u^j, u^{j-1}) plain (u^j = d^j / gamma_j) or (d^j, ehat^j) in the difference form.
 template <bool DIFF>
 __device__ __forceinline__ void stepn(double& x, double& y, double v, unsigned nmask, bool north, const StepN& c) {
   if (!DIFF) {
@@ -88,17 +88,6 @@ __device__ __forceinline__ void stepn(double& x, double& y, double v, unsigned n
     const double en = fma(Q, x, flip_sign(y, smask));     // Q' d + sigma ehat
     x = fma(c.en, en, flip_sign(x, smask));                // sigma d + eta ehat'
     y = en;
-  }
-}
-
-// End of a normalisation block (after the step j -> j+1): back to (d^{j+1}, d^j) / (d^{j+1}, e^{j+1}).
-template <bool DIFF>
-__device__ __forceinline__ void unnormalise(double& x, double& y, const StepN& c) {
-  if (!DIFF) {
-    x *= c.gn;
-    y *= c.g;
-  } else {
-    y *= c.en;
   }
 }
 

@@ -15,6 +15,9 @@
 // -1 south):
 //     e^{j+1} = (P_j - sigma (1 + C_j)) d^j + sigma C_j e^j,    d^{j+1} = sigma d^j + e^{j+1},
 // whose coefficient P_j - sigma(1+C_j) = Kd - (+-A_j v) is small and precomputed accurately.
+// Both forms are carried normalised along the whole chain (u^j = d^j / gamma_j plain, e^j / eta_j
+// in the difference form; products of the C_k, plan.cu), which leaves 2 FMA per plain step and
+// 3 per difference step; gamma_j goes into the contraction's coefficient or output scale.
 //
 // Range.  Starting values d^{l0} (Eq. "initial_values" via the symmetries of Sec. 3.3) can be as
 // small as 2^-20000.  A chain keeps its value as x * 2^-E with an integer E >= 0.  While E > 0 the
@@ -125,10 +128,6 @@ __device__ __forceinline__ void inverse_body(const InvArgs& a, int m, int ni, in
             const StepN c = stepn_at(cs + jj * kCoefPerStepN);
 #pragma unroll
             for (int i = 0; i < KT; ++i) stepn<DIFF>(x[i], y[i], v[i], nmask[i], north[i], c);
-            if (u == kNormBlock - 1) {
-#pragma unroll
-              for (int i = 0; i < KT; ++i) unnormalise<DIFF>(x[i], y[i], c);
-            }
           }
         }
       }
@@ -316,14 +315,6 @@ __global__ void __launch_bounds__(128) theta_forward_kernel(FwdArgs a) {
             const bool dslot = (PAT == 1) || (PAT == 0 && (i == 0 || i == KT - 1));
             if (dslot) stepn<true>(x[i], y[i], v, nmask[i], north[i], c);
             else stepn<false>(x[i], y[i], v, nmask[i], north[i], c);
-          }
-          if (((j - l0) & (kNormBlock - 1)) == kNormBlock - 1) {     // end of a normalisation block
-#pragma unroll
-            for (int i = 0; i < KT; ++i) {
-              const bool dslot = (PAT == 1) || (PAT == 0 && (i == 0 || i == KT - 1));
-              if (dslot) unnormalise<true>(x[i], y[i], c);
-              else unnormalise<false>(x[i], y[i], c);
-            }
           }
         }
       }

@@ -97,10 +97,6 @@ __device__ __forceinline__ void table_body(const TabArgs& a, int ni, int mi, int
             const StepN c = stepn_at(cs + jj * kCoefPerStepN);
 #pragma unroll
             for (int i = 0; i < KT; ++i) stepn<DIFF>(x[i], y[i], v[i], nmask[i], north[i], c);
-            if (u == kNormBlock - 1) {
-#pragma unroll
-              for (int i = 0; i < KT; ++i) unnormalise<DIFF>(x[i], y[i], c);
-            }
           }
         }
       }

@@ -12,7 +12,7 @@
 // Imamura, 2020):
 //
 //   * every recursion value becomes a fixed-point integer qa = round(x 2^(55 - rho_l)), with rho_l a
-//     power-of-two bound of |x| at degree l (|u^l| <= 1/gamma_l for the block-normalised values,
+//     power-of-two bound of |x| at degree l (|u^l| <= 1/gamma_l for the normalised values,
 //     |d| <= 1 in the difference form), and every coefficient qh = round(h' 2^(55 - eps_c)) with one
 //     exponent eps_c per column (a bound over the degrees of the CTA's order); the scale 2^rho_l
 //     moves into the coefficient of degree l, so the product is unchanged;
@@ -123,7 +123,7 @@ __device__ __forceinline__ int inv_ring(const InvArgs& a, int tile, int tid) {
   return q < nr - half ? a.nring - 1 - q : -1;
 }
 
-// Per-degree factor of the coefficients: w_j = scale_j (* gamma_j for block-normalised chains)
+// Per-degree factor of the coefficients: w_j = scale_j (* gamma_j for normalised chains)
 // * 2^rho_j, so that h'_{j,c} = h_{j,c} * sign_slot * w_j and x_j h_j = (x_j 2^-rho_j) h'_j.
 template <bool DIFF>
 __device__ __forceinline__ double coef_factor(const double* coef_m, const double* scale, int j) {
@@ -277,10 +277,7 @@ __device__ __forceinline__ void tc_inverse_body(const InvArgs& a, int m, int ni,
             q0 = q;
           }
         }
-        if (j < L - 1) {
-          stepn<DIFF>(x, y, v, nmask, north, c);
-          if (u == kNormBlock - 1) unnormalise<DIFF>(x, y, c);
-        }
+        if (j < L - 1) stepn<DIFF>(x, y, v, nmask, north, c);
       }
       renorm(x, y, E);
       // the previous chunk's MMAs read these buffers: they must be complete before the first store
@@ -451,9 +448,13 @@ cudaError_t launch_inv_tc(const InvArgs& a, cudaStream_t st) {
 //     digit rows of a degree with one shuffle; the warps' words of a degree are added through
 //     shared memory, and the tiles of the order through distributed shared memory of the
 //     thread-block cluster (one cluster per order, up to 8 tiles), in integers: the result does
-//     not depend on the order of the additions.  Tiles in the difference form (d; the tiles
-//     holding a polar cap) and in the block-normalised form (u = d / gamma_l) are summed
-//     separately -- their digits carry different scales -- and combined in float64.
+//     not depend on the order of the additions.
+//   * Every tile gets an equal share of the polar-cap rings, which run the difference form, in
+//     its first warps (the same number in every tile), and of the other rings in the rest, so the
+//     CTAs of a cluster do the same work and none paces the others at the cluster barriers.  The
+//     difference form carries d itself; its values are scaled by 1 / gamma_l before the split, so
+//     that every ring's digits share the scale of the normalised values u = d / gamma_l and one
+//     accumulator serves both forms.
 //   * The loop is software-pipelined: a chunk's accumulator is read back in the middle of the next
 //     chunk's recursion, and the cluster's sums of chunk k are formed during chunk k + 2.
 //   * Two CTAs (16 warps) share an SM: 110 KiB of shared memory and at most 128 registers per
@@ -471,11 +472,12 @@ constexpr int kDBytes = kFwdRings * kFwdN * 2;    // 56 KiB
 constexpr int kFwdStageOff = kGBytes + kDBytes;                       // [8 warps][8 c][16 l] x (X, Y)
 constexpr int kFwdClOff = kFwdStageOff + kFwdWarps * 8 * kTcK * 16;   // [2 buf][8 c][16 l] x (X, Y)
 constexpr int kFwdCsOff = kFwdClOff + 2 * 8 * kTcK * 16;
-constexpr int kFwdBarOff = kFwdCsOff + 2 * kTcK * kCoefPerStepN * 8;
-constexpr int kFwdMiscOff = kFwdBarOff + 8;       // eps_loc[8], tmem_slot, abort, form
+constexpr int kFwdFuOff = kFwdCsOff + 2 * kTcK * kCoefPerStepN * 8;   // [4 chunks][16 l] output factors
+constexpr int kFwdBarOff = kFwdFuOff + 4 * kTcK * 8;
+constexpr int kFwdMiscOff = kFwdBarOff + 8;       // eps_loc[8], tmem_slot, abort
 constexpr int kFwdSmemBytes = kFwdMiscOff + 64;
 constexpr int kFwdSmemRequest = 112 * 1024;       // two CTAs per SM
-static_assert(kTcK * kCoefPerStepN <= kFwdThreads, "one coefficient prefetch per thread");
+static_assert(kTcK * kCoefPerStepN + kTcK <= kFwdThreads, "one coefficient prefetch per thread");
 
 __device__ __forceinline__ uint32_t cluster_rank() {
   uint32_t r;
@@ -518,8 +520,39 @@ __device__ __forceinline__ int small_int(uint32_t bits) {
   return (int)(__float_as_uint(__uint_as_float(bits) + 12582912.0f) - 0x4B400000u);
 }
 
-// DIFF: every ring of the tile runs the difference form (the tiles holding a polar cap).
-template <int NB, bool PAIR, bool DIFF>
+// Eight recursion steps of one chain from degree j0 (cs8: the coefficients of those steps), the
+// digits of the eight values it passes (0 when the chain is dead or past L) packed into w as the
+// d-digit tile stores them.  DF: the difference form, whose values d are scaled by 1 / gamma_l to
+// the scale of the normalised values u = d / gamma_l before the split.
+template <bool DF>
+__device__ __forceinline__ void fwd_steps8(double& x, double& y, double v, unsigned nmask, bool north, int E,
+                                           bool live, const double* cs8, int j0, int L,
+                                           uint32_t (&w)[kDigits][4]) {
+  uint2 q0 = make_uint2(0, 0);
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    const int j = j0 + u;
+    const StepN c = stepn_at(cs8 + u * kCoefPerStepN);
+    if (live) {
+      const double xl = (E == 0 && j < L) ? (DF ? x * c.ig : x) : 0.0;
+      const uint2 q = offset_digits(xl, exp_of(c.ig) + 2);
+      if (u & 1) {
+        w[0][u >> 1] = digit_pair(q0.y, q.y, 2);
+        w[1][u >> 1] = digit_pair(q0.y, q.y, 1);
+        w[2][u >> 1] = digit_pair(q0.y, q.y, 0);
+        w[3][u >> 1] = digit_pair(q0.x, q.x, 3);
+        w[4][u >> 1] = digit_pair(q0.x, q.x, 2);
+        w[5][u >> 1] = digit_pair(q0.x, q.x, 1);
+        w[6][u >> 1] = digit_pair(q0.x, q.x, 0);
+      } else {
+        q0 = q;
+      }
+    }
+    if (j < L - 1) stepn<DF>(x, y, v, nmask, north, c);
+  }
+}
+
+template <int NB, bool PAIR>
 __device__ __forceinline__ void tc_forward_body(const FwdArgs& a, int m, int ni, int n, int tile, int ntiles,
                                                 int l0, unsigned char* smem) {
   constexpr int NBX = PAIR ? 2 * NB : NB;
@@ -536,33 +569,59 @@ __device__ __forceinline__ void tc_forward_body(const FwdArgs& a, int m, int ni,
   longlong2* stage = reinterpret_cast<longlong2*>(smem + kFwdStageOff);
   longlong2* cl = reinterpret_cast<longlong2*>(smem + kFwdClOff);
   double* cs = reinterpret_cast<double*>(smem + kFwdCsOff);
+  double* fu = reinterpret_cast<double*>(smem + kFwdFuOff);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kFwdBarOff);
   int* eps_loc = reinterpret_cast<int*>(smem + kFwdMiscOff);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(eps_loc + 8);
   int* abort_s = eps_loc + 9;
-  int* form_s = eps_loc + 10;
   const uint32_t bar_a = tc::smem_addr(bar);
   double2* const outb = reinterpret_cast<double2*>(a.flm);
 
   const double* coef_m = a.coef + ((size_t)ni * T + mi) * (size_t)L * kCoefPerStepN;
   const double* scale = a.scale + (size_t)ni * L;
-  // mirrored rings: threads 0..127 count from the first ring of the launch, threads 128..255 from
-  // the last, so that both polar caps (the difference form) fall in the cluster's first tile
-  int tr;
-  bool tact;
+  // The launch's rings: ncn polar-cap rings at the front, ncs at the back (contiguous: sin theta
+  // is monotone on each half), the plain rings between them.  Warps 0 .. wd-1 of every tile run
+  // the difference form on the caps, 32 wd rings per tile (then on the plain rings that the plain
+  // slots of all tiles cannot hold); the other warps run the plain rings.
+  int ncn = 0, ncs = 0;
   {
-    const int half = (a.nrows + 1) / 2, q = tile * kTcRings + (tid & (kTcRings - 1));
-    const bool mirror = tid >= kTcRings;
-    tact = mirror ? q < a.nrows - half : q < half;
-    tr = mirror ? a.row0 + a.nrows - 1 - q : a.row0 + q;
+    const int half = (a.nrows + 1) / 2;
+    for (int t0 = 0; t0 < a.nrows; t0 += kFwdThreads) {
+      const int t = t0 + tid;
+      const bool cap = t < a.nrows && a.ring[a.row0 + t].diff;
+      ncn += __syncthreads_count(cap && t < half);
+      ncs += __syncthreads_count(cap && t >= half);
+    }
   }
+  const int ncap = ncn + ncs;
+  const int wd = (ncap + 32 * ntiles - 1) / (32 * ntiles);          // difference-form warps per tile
+  const int dslots = 32 * wd, pslots = kFwdThreads - dslots;
+  const int nplain = a.nrows - ncap;
+  const int nplain_p = min(nplain, ntiles * pslots);                 // plain rings in plain slots
+  const bool dform = warp < wd;
+  int tr = 0;
+  bool tact;
+  if (dform) {
+    const int s = tile * dslots + tid;
+    tact = s < ncap + (nplain - nplain_p);
+    tr = s < ncn ? a.row0 + s : s < ncap ? a.row0 + a.nrows - 1 - (s - ncn) : a.row0 + ncn + nplain_p + (s - ncap);
+  } else {
+    const int p = tile * pslots + (tid - dslots);
+    tact = p < nplain_p;
+    tr = a.row0 + ncn + p;
+  }
+  // output factor of degree l of a chunk: gamma_l scale_l 2^(rho_l - 38), rho_l = exponent of
+  // 1 / gamma_l + 2 (the column exponent is applied at the end)
+  auto out_factor = [&](int l) {
+    const double* cc = coef_m + (size_t)l * kCoefPerStepN;
+    return ldexp(cc[3] * scale[l], exp_of(cc[9]) + 2 - 38);
+  };
 
   // ---- set-up: barrier, Tensor Memory, the degrees below l0, column exponents over the cluster
   if (tid == 0) {
     tc::mbar_init(bar_a, 1);
     tc::mbar_init_fence();
     *abort_s = 0;
-    *form_s = DIFF ? 1 : 0;
   }
   if (warp == 0) tc::tmem_alloc(tc::smem_addr(tmem_slot), kFwdTmemCols);
   for (int q = tid; q < kGBytes / 16; q += kFwdThreads) reinterpret_cast<uint4*>(sG)[q] = make_uint4(0, 0, 0, 0);
@@ -578,6 +637,9 @@ __device__ __forceinline__ void tc_forward_body(const FwdArgs& a, int m, int ni,
   if (tid < kTcK * kCoefPerStepN) {
     const int j = l0 + tid / kCoefPerStepN;
     cs[tid] = (j < L) ? coef_m[(size_t)l0 * kCoefPerStepN + tid] : 0.0;
+  } else if (tid < kTcK * kCoefPerStepN + kTcK) {
+    const int l = l0 + tid - kTcK * kCoefPerStepN;
+    fu[tid - kTcK * kCoefPerStepN] = l < L ? out_factor(l) : 0.0;
   }
   double2 gv[NBX];
   {
@@ -625,8 +687,6 @@ __device__ __forceinline__ void tc_forward_body(const FwdArgs& a, int m, int ni,
     for (int q = 1; q < C; ++q) e = (c == q) ? eps[q] : e;
     return e;
   };
-  unsigned diff_tiles = 0;                   // bit q: tile q of the cluster runs the difference form
-  for (int q = 0; q < ntiles; ++q) diff_tiles |= (unsigned)ld_peer_s32(peer_addr(tc::smem_addr(form_s), (uint32_t)q)) << q;
 
   // the B operand: digit j of column c in row 8 j + c, this thread's ring in column tid
 #pragma unroll
@@ -668,20 +728,15 @@ __device__ __forceinline__ void tc_forward_body(const FwdArgs& a, int m, int ni,
       const int b = c >> 1;
       const Slot sl = slot_of<NB, PAIR>(b, sig0, a.nsig, a.nN, ni, m, n, L);
       if (sl.sig_off < 0) continue;
-      long long Xp = 0, Yp = 0, Xd = 0, Yd = 0;
+      long long Xs = 0, Ys = 0;
       const uint32_t off = cl_addr + (uint32_t)(((buf * 8 + c) * kTcK + ll) * 16);
       for (int q = 0; q < ntiles; ++q) {
         const uint32_t pa = peer_addr(off, (uint32_t)q);
-        const long long X = ld_peer_s64(pa), Y = ld_peer_s64(pa + 8);
-        if ((diff_tiles >> q) & 1u) { Xd += X; Yd += Y; } else { Xp += X; Yp += Y; }
+        Xs += ld_peer_s64(pa);
+        Ys += ld_peer_s64(pa + 8);
       }
-      // block-normalised chains hold u = d / gamma_l digits at 2^-rho_l: times gamma_l 2^rho_l;
-      // difference-form chains d digits at 2^-2
-      const double* cc = coef_m + (size_t)l * kCoefPerStepN;
-      const double vp = fma((double)Yp, 0x1p-24, (double)Xp) * cc[3];
-      const double vd = fma((double)Yd, 0x1p-24, (double)Xd);
-      const int e = col_eps(c);
-      const double val = (ldexp(vp, exp_of(cc[9]) + 2 + e - 38) + ldexp(vd, 2 + e - 38)) * scale[l];
+      // the digits hold u = d / gamma_l at 2^-rho_l: times gamma_l 2^rho_l
+      const double val = ldexp(fma((double)Ys, 0x1p-24, (double)Xs) * fu[(kk & 3) * kTcK + ll], col_eps(c));
       reinterpret_cast<double*>(outb + ((size_t)sl.sig_off * L + l) * a.flm_ld + sl.m + a.flm_c0)[c & 1] = val;
     }
   };
@@ -701,38 +756,18 @@ __device__ __forceinline__ void tc_forward_body(const FwdArgs& a, int m, int ni,
     double cpre = 0.0;
     if (comp && tid < kTcK * kCoefPerStepN && jc + kTcK + tid / kCoefPerStepN < L)
       cpre = coef_m[(size_t)(jc + kTcK) * kCoefPerStepN + tid];
+    else if (comp && tid >= kTcK * kCoefPerStepN && tid < kTcK * kCoefPerStepN + kTcK &&
+             jc + kTcK + tid - kTcK * kCoefPerStepN < L)
+      cpre = out_factor(jc + kTcK + tid - kTcK * kCoefPerStepN);
 #pragma unroll
     for (int g = 0; g < 2; ++g) {
       uint32_t w[kDigits][4];
       bool live = false;
       if (comp) {
-        uint2 q0 = make_uint2(0, 0);
         live = __any_sync(0xffffffffu, E == 0);
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const int jj = g * 8 + u, j = jc + jj;
-          const StepN c = stepn_at(csk + jj * kCoefPerStepN);
-          if (live) {
-            const double xl = (E == 0 && j < L) ? x : 0.0;
-            const int rho = DIFF ? 2 : exp_of(c.ig) + 2;
-            const uint2 q = offset_digits(xl, rho);
-            if (u & 1) {
-              w[0][u >> 1] = digit_pair(q0.y, q.y, 2);
-              w[1][u >> 1] = digit_pair(q0.y, q.y, 1);
-              w[2][u >> 1] = digit_pair(q0.y, q.y, 0);
-              w[3][u >> 1] = digit_pair(q0.x, q.x, 3);
-              w[4][u >> 1] = digit_pair(q0.x, q.x, 2);
-              w[5][u >> 1] = digit_pair(q0.x, q.x, 1);
-              w[6][u >> 1] = digit_pair(q0.x, q.x, 0);
-            } else {
-              q0 = q;
-            }
-          }
-          if (j < L - 1) {
-            stepn<DIFF>(x, y, v, nmask, north, c);
-            if (u == kNormBlock - 1) unnormalise<DIFF>(x, y, c);
-          }
-        }
+        const double* cs8 = csk + g * 8 * kCoefPerStepN;
+        if (dform) fwd_steps8<true>(x, y, v, nmask, north, E, live, cs8, jc + g * 8, L, w);
+        else fwd_steps8<false>(x, y, v, nmask, north, E, live, cs8, jc + g * 8, L, w);
         renorm(x, y, E);
       }
       // chunk k-1's MMAs read the d-digit tile: they must be done before its first store
@@ -784,6 +819,7 @@ __device__ __forceinline__ void tc_forward_body(const FwdArgs& a, int m, int ni,
       }
     }
     if (comp && tid < kTcK * kCoefPerStepN) cs[((k + 1) & 1) * kTcK * kCoefPerStepN + tid] = cpre;
+    else if (comp && tid < kTcK * kCoefPerStepN + kTcK) fu[((k + 1) & 3) * kTcK + tid - kTcK * kCoefPerStepN] = cpre;
     tc::fence_proxy_async();
     __syncthreads();
     if (*abort_s) ok = false;
@@ -833,8 +869,7 @@ __device__ __forceinline__ void tc_forward_body(const FwdArgs& a, int m, int ni,
 }
 
 // Grid: x = (rank of m) * ntiles + tile (a cluster of ntiles CTAs per order), y = n index,
-// z = batch group.  Tile q holds the launch's rings q * 128 + (tid mod 128) and, mirrored (tid >=
-// 128), nrows - 1 - that.
+// z = batch group.
 template <int NB, bool PAIR>
 __global__ void __launch_bounds__(kFwdThreads, 2) theta_forward_tc_kernel(FwdArgs a, int ntiles) {
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -859,22 +894,13 @@ __global__ void __launch_bounds__(kFwdThreads, 2) theta_forward_tc_kernel(FwdArg
     }
     return;
   }
-  // the form of the tile: the difference form if any of its rings lies in a polar cap (the caps
-  // are contiguous at both ends, so the ends of the tile's two ring ranges decide)
-  const int half = (a.nrows + 1) / 2, q0 = tile * kTcRings, q1 = min(half, q0 + kTcRings) - 1;
-  bool diff = a.ring[a.row0 + q0].diff || a.ring[a.row0 + q1].diff;
-  if (q0 < a.nrows - half) {
-    const int r1 = min(a.nrows - half, q0 + kTcRings) - 1;
-    diff = diff || a.ring[a.row0 + a.nrows - 1 - q0].diff || a.ring[a.row0 + a.nrows - 1 - r1].diff;
-  }
-  if (diff) tc_forward_body<NB, PAIR, true>(a, m, ni, n, tile, ntiles, l0, smem);
-  else tc_forward_body<NB, PAIR, false>(a, m, ni, n, tile, ntiles, l0, smem);
+  tc_forward_body<NB, PAIR>(a, m, ni, n, tile, ntiles, l0, smem);
 }
 
 template <int NB, bool PAIR>
 cudaError_t launch_fwd_tc(const FwdArgs& a, cudaStream_t st) {
   static_assert(kFwdSmemBytes <= kFwdSmemRequest, "shared memory layout");
-  const int ntiles = ((a.nrows + 1) / 2 + kTcRings - 1) / kTcRings;
+  const int ntiles = (a.nrows + kFwdRings - 1) / kFwdRings;
   if (ntiles == 0) return cudaSuccess;
   if (ntiles > kFwdMaxTiles) return cudaErrorInvalidValue;
   auto kern = theta_forward_tc_kernel<NB, PAIR>;
@@ -1212,7 +1238,7 @@ cudaError_t launch_theta_inverse_tc(const Plan& p, const InvArgs& a, cudaStream_
 // Forward theta stage on the tensor cores, for launches of at most 8 tiles of 256 rings (2048
 // rings) written straight to flm; other launches return cudaErrorNotSupported.
 cudaError_t launch_theta_forward_tc(const Plan& p, const FwdArgs& a, cudaStream_t st) {
-  if (a.part || ((a.nrows + 1) / 2 + kTcRings - 1) / kTcRings > kFwdMaxTiles) return cudaErrorNotSupported;
+  if (a.part || (a.nrows + kFwdRings - 1) / kFwdRings > kFwdMaxTiles) return cudaErrorNotSupported;
   if (paired_plan(p)) {
     if (a.nsig >= 2) return launch_fwd_tc<2, true>(a, st);
     return launch_fwd_tc<1, true>(a, st);

@@ -146,12 +146,16 @@ int s2gb_plan_create_real(s2gb_plan* out, int L, int sampling, int precision, in
  *
  * S2GB_PLAN_FMA_CONTRACTION: float64 plans whose d-functions are generated on the fly (neither
  * PRECOMPUTE nor MRECURSION) run the theta contraction -- the sum over the degree l of the inverse
- * stage (Eq. disc_ish_expanded) -- on the tensor cores by default: the float64 recursion values
- * and the coefficients are split into seven exact base-256 digits each, whose products the
- * tensor cores sum exactly in float32 (the Ozaki splitting scheme); the digit sums are combined
- * in 64-bit integers and float64.  The result agrees with a float64 sum to a few units of the
- * last place.  This flag keeps the contraction on the float64 FMA pipe instead (the kernels of
- * the recursion alone; for comparison).  Ignored by other plans.
+ * stage (Eq. disc_ish_expanded) and over the rings of the forward (Eq. disc_sh_expanded) -- on the
+ * tensor cores by default: the float64 recursion values and the coefficients are split into seven
+ * exact base-256 digits each, whose products the tensor cores sum exactly in float32 (the Ozaki
+ * splitting scheme); the digit sums are combined in 64-bit integers and float64.  The result
+ * agrees with a float64 sum to a few units of the last place.  Float32 plans with max_batch >= 16
+ * run their inverse theta stage the same way with four digits (a float32 value to 2^-30 of its
+ * bound) and exact integer level sums in place of compensated float32 sums, for every call on the
+ * plan (smaller float32 plans keep the FMA pipe, which is faster for few signals).  This flag keeps
+ * the contraction on the FMA pipe instead (float64 or float32; for comparison).  Ignored by other
+ * plans.
  */
 #define S2GB_PLAN_REAL 1u
 #define S2GB_PLAN_PRECOMPUTE 2u

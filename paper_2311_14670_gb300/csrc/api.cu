@@ -555,6 +555,8 @@ int plan_create_impl(s2gb_plan* out, int L, int spin, int N, int sampling, int p
   p.precompute = precompute;
   p.mrec = mrec;
   p.tc = precision == S2GB_FP64 && !precompute && !mrec && !fma_contraction;
+  // float32: the tensor-core inverse pays off from 16 signals per call (measured on GB300)
+  p.tc32 = precision == S2GB_FP32 && !fma_contraction && max_batch >= 16;
   int rc;
   {
     s2gb::DeviceGuard g(device);

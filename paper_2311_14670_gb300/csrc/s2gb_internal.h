@@ -68,6 +68,7 @@ struct Plan {
   int pole_s = -1;  // ring index of theta = pi handled by the pole kernels, or -1
   bool mrec = false;  // theta stages by the recursion over the order m (theta_mrec.cu)
   bool tc = false;    // float64 on-the-fly plans: the theta contraction on the tensor cores
+  bool tc32 = false;  // float32 plans of max_batch >= 16: the inverse contraction on the tensor cores
                       // (theta_tc.cu); false: on the float64 FMA pipe (theta_kernels.cu)
   // The forward's theta-direction quadrature operator (torus extension, then the FFT operator of
   // api.cu's theta_weight_operator, restricted to the R rings) is linear and the same for every
@@ -232,6 +233,7 @@ cudaError_t launch_theta_forward(const Plan& p, const FwdArgs& a, cudaStream_t s
 cudaError_t launch_theta_inverse_f32(const Plan& p, const InvArgs& a, cudaStream_t st);
 // float64 theta stages with the contraction on the tensor cores (theta_tc.cu)
 cudaError_t launch_theta_inverse_tc(const Plan& p, const InvArgs& a, cudaStream_t st);
+cudaError_t launch_theta_inverse_tc32(const Plan& p, const InvArgs& a, cudaStream_t st);
 cudaError_t launch_theta_forward_tc(const Plan& p, const FwdArgs& a, cudaStream_t st);
 // plan creation: the operator matrices from the operator's responses (theta_tc.cu)
 //   op_identity: rows r < rows of G [rows][TS] = unit vectors at torus points i0 + r

@@ -431,7 +431,7 @@ namespace {
 cudaError_t launch_theta_inverse_rings(const Plan& p, const InvArgs& a, cudaStream_t st) {
   if (p.mrec) return launch_theta_inverse_mrec(p, a, st);
   if (a.dtab) return launch_theta_inverse_pre(p, a, st);
-  if (p.precision == S2GB_FP32) return launch_theta_inverse_f32(p, a, st);
+  if (p.precision == S2GB_FP32) return p.tc32 ? launch_theta_inverse_tc32(p, a, st) : launch_theta_inverse_f32(p, a, st);
   if (p.tc) return launch_theta_inverse_tc(p, a, st);
   if (paired(p)) {
     if (a.nsig >= 2) return launch_inv_nb<2, true>(p, a, st);

@@ -44,6 +44,7 @@
 
 #include "tc_common.cuh"
 #include "theta_common.cuh"
+#include "theta_f32.cuh"
 
 // Status of the tensor-core kernels on this device: 0, or the first tc::kStatus* code recorded by a
 // kernel whose bounded wait ran out (read and cleared by s2gb_device_status).
@@ -424,6 +425,359 @@ cudaError_t launch_inv_tc(const InvArgs& a, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   dim3 grid(a.nrank * ntiles, PAIR ? (a.nN + 1) / 2 : a.nN, (a.nsig + NB - 1) / NB);
   kern<<<grid, kTcRings, kSmemRequest, st>>>(a, ntiles);
+  return launched();
+}
+
+// =============================================================================================
+// Float32 inverse theta stage with the contraction on the tensor cores.  The float32 recursion of
+// theta_f32.cuh (unnormalised d, |d| <= 1 once live) runs one chain per thread as in the float64
+// tensor-core inverse above; the contraction is the same exact digit scheme with four balanced
+// base-256 digits per operand (a float32 value to 2^-30 of its bound):
+//   * q = round(d 2^29) comes from FMAs with the magic constant 1.5 2^23, whose low mantissa bits
+//     hold the nearest integer: hi = round(d 2^21), then the exact remainder d 2^21 - hi (one more
+//     FMA) gives lo = round(256 (d 2^21 - hi)), q = 256 hi + lo (|q| <= 2^29); the coefficients
+//     h' = h scale_l become round(h' 2^(29 - eps_c)) with one exponent eps_c per column (2^eps_c
+//     bounds the column);
+//   * one MMA per d digit i accumulates the digit products (i, j), j <= 3 - i, into the TMEM
+//     columns of level s = i + j (products of levels s > 3 weigh below 2^-24 of the leading ones,
+//     under float32 rounding; with three digits the dropped level would weigh 2^-16 and cost
+//     float32 accuracy); a level receives at most 4 products of magnitude <= 2^14 per degree, so
+//     128 degrees sum exactly below 2^24 in float32;
+//   * every 128 degrees each thread combines its ring's levels per column, X = 2^24 L0 + 2^16 L1 +
+//     2^8 L2 + L3, in float32 (one rounding) and adds it to a float32 register sum (at most 16
+//     read-backs at L = 2048); the value is X 2^(eps_c - 34).
+// The level sums are exact integers, so no compensated summation is needed, and the result does
+// not depend on how the signals are batched.  Up to 16 signals share one recursion (32 columns).
+// =============================================================================================
+constexpr int kDigits32 = 4;
+constexpr int kDrain32 = 8;                // chunks of 16 degrees between read-backs: 128 degrees
+constexpr float kMagic32 = 12582912.0f;    // 1.5 * 2^23
+
+// round(256 x scale) + 0x80808080: bytes 0..3 are the balanced digits of weight 256^0..256^3,
+// offset by 128.  x scale = hi + r exactly (hi the nearest integer, |r| <= 1/2, r exact in float),
+// and the result is 256 hi + round(256 r).  Needs |x scale| < 2^22.
+__device__ __forceinline__ uint32_t offset_digits32(float x, float scale) {
+  const float y1 = fmaf(x, scale, kMagic32);
+  const float hi = y1 - kMagic32;
+  const float y2 = fmaf(fmaf(x, scale, -hi), 256.0f, kMagic32);
+  const int q = (int)((__float_as_uint(y1) - 0x4B400000u) << 8) + (int)(__float_as_uint(y2) - 0x4B400000u);
+  return (uint32_t)q + 0x80808080u;
+}
+// The same with scale 2^e, -108 <= e <= 145 (beyond float's 2^127 the value is scaled by 2^64
+// first, exactly: it is then below 2^-100).
+__device__ __forceinline__ uint32_t offset_digits32_scaled(float x, int e) {
+  return e > 120 ? offset_digits32(x * 0x1p64f, pow2f(e - 64)) : offset_digits32(x, pow2f(e));
+}
+
+template <int NB>
+struct InvTc32 {
+  static constexpr int C = 2 * NB;                          // columns (re, im of each signal)
+  static constexpr int CX = (C + 7) / 8 * 8;                // columns read back (groups of 8)
+  static constexpr int LC = C <= 16 ? 16 : 32;              // TMEM columns (and B rows) per level
+  static constexpr int kTmem = C <= 16 ? 64 : 128;          // 4 levels
+  static constexpr int kABytes = kDigits32 * kATileBytes;   // 16 KiB
+  static constexpr int kBBytes = kDigits32 * LC * kTcK * 2;
+  static constexpr int kCsOff = kABytes + kBBytes;          // recursion coefficients [2][16][6]
+  static constexpr int kSclOff = kCsOff + 2 * kTcK * kCoefPerStep * 4;   // scale_l [2 chunks][16]
+  static constexpr int kBarOff = (kSclOff + 2 * kTcK * 4 + 7) / 8 * 8;
+  static constexpr int kMiscOff = kBarOff + 8;              // eps[32], tmem slot, abort
+  static constexpr int kSmem = kMiscOff + 4 * 34;
+};
+
+template <int NB, bool DIFF>
+__device__ __forceinline__ void tc_inverse_body_f32(const InvArgs& a, int m, int ni, int tile, int l0,
+                                                    unsigned char* smem) {
+  using K = InvTc32<NB>;
+  constexpr int C = K::C, CX = K::CX, LC = K::LC;
+  const int L = a.L, T = 2 * L - 1;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int mi = m + L - 1;
+  const int sig0 = blockIdx.z * NB;
+
+  unsigned char* sA = smem;
+  unsigned char* sB = smem + K::kABytes;
+  float* cs = reinterpret_cast<float*>(smem + K::kCsOff);
+  float* scl = reinterpret_cast<float*>(smem + K::kSclOff);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + K::kBarOff);
+  int* eps_s = reinterpret_cast<int*>(smem + K::kMiscOff);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(eps_s + 32);
+  int* abort_s = eps_s + 33;
+  const uint32_t bar_a = tc::smem_addr(bar);
+
+  const float* coef_m = a.coef32 + ((size_t)ni * T + mi) * (size_t)L * kCoefPerStep;
+  const double* scale = a.scale + (size_t)ni * L;
+  auto coef_h = [&](int j, int b) {       // h_{j,b} (times scale_j later), both parts; zero when inactive
+    float2 h = make_float2(0.f, 0.f);
+    const int sig = sig0 + b;
+    if (sig < a.nsig) {
+      h = reinterpret_cast<const float2*>(a.flm)[((size_t)(sig * a.nN + ni) * L + j) * a.flm_ld + m + a.flm_c0];
+      if (a.mpos && m == 0) h.y = 0.f;
+    }
+    return h;
+  };
+
+  // ---- set-up: barrier, Tensor Memory, zero B rows, column exponents, first coefficients
+  if (tid == 0) {
+    tc::mbar_init(bar_a, 1);
+    tc::mbar_init_fence();
+    *abort_s = 0;
+  }
+  if (warp == 0) tc::tmem_alloc(tc::smem_addr(tmem_slot), K::kTmem);
+  for (int q = tid; q < K::kBBytes / 16; q += kTcRings) reinterpret_cast<uint4*>(sB)[q] = make_uint4(0, 0, 0, 0);
+  if (tid < 32) eps_s[tid] = -100000;
+  for (int q = tid; q < kTcK * kCoefPerStep; q += kTcRings) {
+    const int j = l0 + q / kCoefPerStep;
+    cs[q] = (j < L) ? coef_m[(size_t)l0 * kCoefPerStep + q] : 0.0f;
+  }
+  if (tid < kTcK) scl[tid] = l0 + tid < L ? (float)scale[l0 + tid] : 0.f;
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tmem_slot;
+  {
+    int emax[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) emax[c] = -100000;
+    // |h scale_j| < 2^(e_h + 1) 2^(e_s + 1): the exponents added on the integer pipe
+    for (int j = l0 + tid; j < L; j += kTcRings) {
+      const int es = exp_of(scale[j]) + 1;
+#pragma unroll
+      for (int b = 0; b < NB; ++b) {
+        const float2 h = coef_h(j, b);
+        if (h.x != 0.f) emax[2 * b] = max(emax[2 * b], expf_of(h.x) + es);
+        if (h.y != 0.f) emax[2 * b + 1] = max(emax[2 * b + 1], expf_of(h.y) + es);
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      const int e = __reduce_max_sync(0xffffffffu, emax[c]);
+      if ((tid & 31) == 0) atomicMax(&eps_s[c], e);
+    }
+  }
+  __syncthreads();
+  // |h'| < 2^eps_c (|round(h' 2^(29 - eps_c))| < 2^29); a column of zeros takes eps_c = 1
+  auto col_eps = [&](int c) { const int e = eps_s[c]; return (e < -1000 ? 0 : e) + 1; };
+
+  // ---- the chain of this thread's ring
+  const SeedData sd = a.seed[(size_t)ni * T + mi];
+  const int t = inv_ring(a, tile, tid);
+  float x = 0.f, y = 0.f, v = 0.f;
+  int E = 0;
+  bool north = true;
+  if (t >= 0) {
+    const RingData rd = a.ring[t];
+    seed_value_f32(sd, rd, x, E);
+    v = a.v32[t];
+    north = rd.north;
+  }
+  if (DIFF) y = x;
+  const unsigned nmask = north ? 0x80000000u : 0u;
+  // a chain that is live (|d| >= 2^-90) stays live: once the whole warp is, the bookkeeping stops
+  bool all_live = __all_sync(0xffffffffu, E == 0);
+  bool live = __any_sync(0xffffffffu, E == 0);
+
+  float X[CX];
+#pragma unroll
+  for (int c = 0; c < CX; ++c) X[c] = 0.f;
+
+  const int nchunks = (L - l0 + kTcK - 1) / kTcK;
+  int since_reset = 0;
+  bool ok = true;
+  const uint32_t sA_addr = tc::smem_addr(sA), sB_addr = tc::smem_addr(sB);
+  for (int k = 0; k < nchunks; ++k) {
+    const int jc = l0 + k * kTcK;
+    const float* csk = cs + (k & 1) * kTcK * kCoefPerStep;
+    // prefetch: the next chunk's recursion coefficients and scales, this chunk's coefficients h
+    float cpre = 0.f;
+    if (tid < kTcK * kCoefPerStep && jc + kTcK + tid / kCoefPerStep < L)
+      cpre = coef_m[(size_t)(jc + kTcK) * kCoefPerStep + tid];
+    float spre = 0.f;
+    if (tid < kTcK && jc + kTcK + tid < L) spre = (float)scale[jc + kTcK + tid];
+    constexpr int kHPer = (kTcK * NB + kTcRings - 1) / kTcRings;      // entries per thread
+    float2 hpre[kHPer];
+#pragma unroll
+    for (int r = 0; r < kHPer; ++r) {
+      const int q = tid + r * kTcRings, hj = q / NB, hb = q % NB;
+      hpre[r] = (q < kTcK * NB && jc + hj < L) ? coef_h(jc + hj, hb) : make_float2(0.f, 0.f);
+    }
+
+#pragma unroll
+    for (int g = 0; g < 2; ++g) {
+      // digits of the values of degrees jc + 8g .. +7, as pairs of float16 (0 for dead chains)
+      uint32_t w[kDigits32][4];
+      bool any = false;
+      uint32_t q0 = 0;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int jj = g * 8 + u, j = jc + jj;
+        if (live) {
+          const float xl = (E == 0 && j < L) ? x : 0.f;
+          const uint32_t q = offset_digits32(xl, 2097152.0f);          // 2^21: q ~ d 2^29
+          if (u & 1) {
+            w[0][u >> 1] = digit_pair(q0, q, 3);
+            w[1][u >> 1] = digit_pair(q0, q, 2);
+            w[2][u >> 1] = digit_pair(q0, q, 1);
+            w[3][u >> 1] = digit_pair(q0, q, 0);
+          } else {
+            q0 = q;
+          }
+        } else if (u & 1) {
+          w[0][u >> 1] = 0u;
+          w[1][u >> 1] = 0u;
+          w[2][u >> 1] = 0u;
+          w[3][u >> 1] = 0u;
+        }
+        any = any || live;
+        if (j < L - 1) {
+          const float* cp = csk + jj * kCoefPerStep;
+          const StepCoef32 c = {cp[0], cp[1], cp[2], cp[3], cp[4], cp[5]};
+          step_f32<DIFF>(x, y, v, nmask, north, c);
+        }
+        if ((u & 1) && !all_live) {     // every 2 steps: float32's range (kRescale32)
+          renorm_f32(x, y, E);
+          all_live = __all_sync(0xffffffffu, E == 0);
+          live = __any_sync(0xffffffffu, E == 0);
+        }
+      }
+      // the previous chunk's MMAs read these buffers: they must be complete before the first store
+      if (g == 0 && k > 0 && !tc::mbar_wait(bar_a, (uint32_t)((k - 1) & 1))) {
+        set_status(tc::kStatusMmaWait);
+        *abort_s = 1;
+      }
+#pragma unroll
+      for (int i = 0; i < kDigits32; ++i) {
+        const uint4 val = any ? make_uint4(w[i][0], w[i][1], w[i][2], w[i][3]) : make_uint4(0, 0, 0, 0);
+        *reinterpret_cast<uint4*>(sA + i * kATileBytes + kmajor_off(tid, g * 8)) = val;
+      }
+    }
+    // B digits of this chunk: entry (degree hj, signal hb) gives rows LC i + 2 hb and LC i + 2 hb + 1
+#pragma unroll
+    for (int r = 0; r < kHPer; ++r) {
+      const int q = tid + r * kTcRings, hj = q / NB, hb = q % NB;
+      if (q >= kTcK * NB) break;
+      const float sj = scl[(k & 1) * kTcK + hj];
+      const float2 h = make_float2(hpre[r].x * sj, hpre[r].y * sj);
+      const uint32_t qr = offset_digits32_scaled(h.x, 21 - col_eps(2 * hb));
+      const uint32_t qi = offset_digits32_scaled(h.y, 21 - col_eps(2 * hb + 1));
+#pragma unroll
+      for (int i = 0; i < kDigits32; ++i) {
+        const int p = 3 - i;
+        const float dr = (float)((int)((qr >> (8 * p)) & 0xffu) - 128);
+        const float di = (float)((int)((qi >> (8 * p)) & 0xffu) - 128);
+        *reinterpret_cast<__half*>(sB + kmajor_off(LC * i + 2 * hb, hj)) = __float2half_rn(dr);
+        *reinterpret_cast<__half*>(sB + kmajor_off(LC * i + 2 * hb + 1, hj)) = __float2half_rn(di);
+      }
+    }
+    if (tid < kTcK * kCoefPerStep) cs[((k + 1) & 1) * kTcK * kCoefPerStep + tid] = cpre;
+    if (tid < kTcK) scl[((k + 1) & 1) * kTcK + tid] = spre;
+    tc::fence_proxy_async();
+    __syncthreads();
+    if (*abort_s) { ok = false; break; }
+    if (tid == 0) {
+      tc::fence_after_sync();
+#pragma unroll
+      for (int i = 0; i < kDigits32; ++i) {
+        const uint64_t ad = tc::smem_desc(sA_addr + i * kATileBytes, 128, 256);
+        const uint64_t bd = tc::smem_desc(sB_addr, 128, 256);
+        tc::mma_f16(tmem + LC * i, ad, bd, tc::idesc_f16_f32(kTcRings, LC * (kDigits32 - i)),
+                    since_reset > 0 || i > 0);
+      }
+      tc::mma_commit(bar_a);
+    }
+    ++since_reset;
+    if (since_reset == kDrain32 || k == nchunks - 1) {
+      if (!tc::mbar_wait(bar_a, (uint32_t)(k & 1))) {
+        set_status(tc::kStatusMmaWait);
+        ok = false;
+      }
+      tc::fence_after_sync();
+      if (__all_sync(0xffffffffu, ok)) {
+        const uint32_t trow = tmem + ((uint32_t)(32 * warp) << 16);
+#pragma unroll
+        for (int h8 = 0; h8 < CX / 8; ++h8) {
+          uint32_t r[kDigits32][8];
+#pragma unroll
+          for (int s = 0; s < kDigits32; ++s) tc::tmem_ld8(trow + (uint32_t)(LC * s + 8 * h8), r[s]);
+          tc::tmem_ld_wait();
+          // the levels are exact integers in float32: 2^24 L0 + 2^16 L1 + 2^8 L2 + L3, one rounding
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            const float v3 = fmaf(__uint_as_float(r[2][e]), 256.f, __uint_as_float(r[3][e]));
+            const float v = fmaf(fmaf(__uint_as_float(r[0][e]), 256.f, __uint_as_float(r[1][e])), 65536.f, v3);
+            X[8 * h8 + e] += v;
+          }
+        }
+      }
+      tc::fence_before_sync();
+      since_reset = 0;
+      if (!__syncthreads_and(ok)) { ok = false; break; }
+    }
+  }
+
+  if (ok && t >= 0) {
+    const long long col = a.m_mod ? (m >= 0 ? m : m + a.mmod) : mi;
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      const int sig = sig0 + b;
+      if (sig >= a.nsig) continue;
+      const int er = col_eps(2 * b) - 34, ei = col_eps(2 * b + 1) - 34;
+      const float re = (X[2 * b] * pow2f(er / 2)) * pow2f(er - er / 2);
+      const float im = (X[2 * b + 1] * pow2f(ei / 2)) * pow2f(ei - ei / 2);
+      reinterpret_cast<float2*>(a.out)[(size_t)(sig * a.nN + ni) * a.s_sig + t * a.s_t + col * a.s_m] =
+          make_float2(re, im);
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after_sync();
+    tc::tmem_dealloc(tmem, K::kTmem);
+  }
+}
+
+// Grid as the float64 tensor-core inverse: x = (rank of m) * ntiles + tile, y = n index, z =
+// batch group of NB signals.
+template <int NB>
+__global__ void __launch_bounds__(kTcRings, 4) theta_inverse_tc_kernel_f32(InvArgs a, int ntiles) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const int L = a.L;
+  const int rank = a.rank0 + (int)(blockIdx.x / ntiles), tile = blockIdx.x % ntiles;
+  const int m = a.mpos ? rank : m_of_rank(rank);
+  const int ni = (int)blockIdx.y;
+  const int l0 = a.seed[(size_t)ni * (2 * L - 1) + m + L - 1].l0;
+  if (l0 >= L) {                 // no degree of this order: its ring values are 0
+    const int t = inv_ring(a, tile, (int)threadIdx.x);
+    if (t < 0) return;
+    const long long col = a.m_mod ? (m >= 0 ? m : m + a.mmod) : m + L - 1;
+    for (int b = 0; b < NB; ++b) {
+      const int sig = blockIdx.z * NB + b;
+      if (sig < a.nsig)
+        reinterpret_cast<float2*>(a.out)[(size_t)(sig * a.nN + ni) * a.s_sig + t * a.s_t + col * a.s_m] =
+            make_float2(0.f, 0.f);
+    }
+    return;
+  }
+  const int nr = a.nring - a.ring0, half = (nr + 1) / 2;
+  const int q0 = tile * (kTcRings / 2), q1 = min(half, q0 + kTcRings / 2) - 1;
+  bool diff = a.ring[a.ring0 + q0].diff || a.ring[a.ring0 + q1].diff;
+  if (q0 < nr - half) {
+    const int r1 = min(nr - half, q0 + kTcRings / 2) - 1;
+    diff = diff || a.ring[a.nring - 1 - q0].diff || a.ring[a.nring - 1 - r1].diff;
+  }
+  if (diff) tc_inverse_body_f32<NB, true>(a, m, ni, tile, l0, smem);
+  else tc_inverse_body_f32<NB, false>(a, m, ni, tile, l0, smem);
+}
+
+template <int NB>
+cudaError_t launch_inv_tc32(const InvArgs& a, cudaStream_t st) {
+  const int ntiles = ((a.nring - a.ring0 + 1) / 2 + kTcRings / 2 - 1) / (kTcRings / 2);
+  if (ntiles == 0) return cudaSuccess;
+  auto kern = theta_inverse_tc_kernel_f32<NB>;
+  constexpr int smem = (InvTc32<NB>::kSmem + 1023) / 1024 * 1024 + 1024;
+  cudaError_t e = set_dynamic_smem((const void*)kern, smem);
+  if (e != cudaSuccess) return e;
+  dim3 grid(a.nrank * ntiles, a.nN, (a.nsig + NB - 1) / NB);
+  kern<<<grid, kTcRings, smem, st>>>(a, ntiles);
   return launched();
 }
 
@@ -1224,6 +1578,14 @@ __global__ void __launch_bounds__(kTcRings, 3) theta_operator_tc_kernel(OpArgs a
 }
 
 }  // namespace
+
+cudaError_t launch_theta_inverse_tc32(const Plan& p, const InvArgs& a, cudaStream_t st) {
+  if (a.nsig >= 16) return launch_inv_tc32<16>(a, st);
+  if (a.nsig >= 8) return launch_inv_tc32<8>(a, st);
+  if (a.nsig >= 4) return launch_inv_tc32<4>(a, st);
+  if (a.nsig >= 2) return launch_inv_tc32<2>(a, st);
+  return launch_inv_tc32<1>(a, st);
+}
 
 cudaError_t launch_theta_inverse_tc(const Plan& p, const InvArgs& a, cudaStream_t st) {
   if (paired_plan(p)) {

@@ -804,7 +804,7 @@ cudaError_t launch_inv_tc32(const InvArgs& a, cudaStream_t st) {
 //     thread-block cluster (one cluster per order, up to 8 tiles), in integers: the result does
 //     not depend on the order of the additions.
 //   * Every tile gets an equal share of the polar-cap rings, which run the difference form, in
-//     its first warps (the same number in every tile), and of the other rings in the rest, so the
+//     its last warps (the same number in every tile), and of the other rings in the rest, so the
 //     CTAs of a cluster do the same work and none paces the others at the cluster barriers.  The
 //     difference form carries d itself; its values are scaled by 1 / gamma_l before the split, so
 //     that every ring's digits share the scale of the normalised values u = d / gamma_l and one
@@ -934,9 +934,11 @@ __device__ __forceinline__ void tc_forward_body(const FwdArgs& a, int m, int ni,
   const double* coef_m = a.coef + ((size_t)ni * T + mi) * (size_t)L * kCoefPerStepN;
   const double* scale = a.scale + (size_t)ni * L;
   // The launch's rings: ncn polar-cap rings at the front, ncs at the back (contiguous: sin theta
-  // is monotone on each half), the plain rings between them.  Warps 0 .. wd-1 of every tile run
+  // is monotone on each half), the plain rings between them.  The last wd warps of every tile run
   // the difference form on the caps, 32 wd rings per tile (then on the plain rings that the plain
-  // slots of all tiles cannot hold); the other warps run the plain rings.
+  // slots of all tiles cannot hold); the other warps run the plain rings.  The last warps have the
+  // least read-back work (lane quadrant 3 needs one load, taken by warp 3), which balances the
+  // difference form's extra float64 instructions.
   int ncn = 0, ncs = 0;
   {
     const int half = (a.nrows + 1) / 2;
@@ -952,15 +954,15 @@ __device__ __forceinline__ void tc_forward_body(const FwdArgs& a, int m, int ni,
   const int dslots = 32 * wd, pslots = kFwdThreads - dslots;
   const int nplain = a.nrows - ncap;
   const int nplain_p = min(nplain, ntiles * pslots);                 // plain rings in plain slots
-  const bool dform = warp < wd;
+  const bool dform = warp >= kFwdWarps - wd;
   int tr = 0;
   bool tact;
   if (dform) {
-    const int s = tile * dslots + tid;
+    const int s = tile * dslots + (tid - pslots);
     tact = s < ncap + (nplain - nplain_p);
     tr = s < ncn ? a.row0 + s : s < ncap ? a.row0 + a.nrows - 1 - (s - ncn) : a.row0 + ncn + nplain_p + (s - ncap);
   } else {
-    const int p = tile * pslots + (tid - dslots);
+    const int p = tile * pslots + tid;
     tact = p < nplain_p;
     tr = a.row0 + ncn + p;
   }

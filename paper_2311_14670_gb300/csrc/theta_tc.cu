@@ -439,10 +439,10 @@ cudaError_t launch_inv_tc(const InvArgs& a, cudaStream_t st) {
 //     h' = h scale_l become round(h' 2^(29 - eps_c)) with one exponent eps_c per column (2^eps_c
 //     bounds the column);
 //   * one MMA per d digit i accumulates the digit products (i, j), j <= 3 - i, into the TMEM
-//     columns of level s = i + j (products of levels s > 3 weigh below 2^-24 of the leading ones,
-//     under float32 rounding; with three digits the dropped level would weigh 2^-16 and cost
-//     float32 accuracy); a level receives at most 4 products of magnitude <= 2^14 per degree, so
-//     128 degrees sum exactly below 2^24 in float32;
+//     columns of level s = i + j (the dropped products of levels s > 3 amount to less than 2^-26
+//     of the product of the operands' bounds, under float32 rounding; with three digits the
+//     dropped level would cost about 2^-19, above it); a level receives at most 4 products of
+//     magnitude <= 2^14 per degree, so 128 degrees sum exactly below 2^24 in float32;
 //   * every 128 degrees each thread combines its ring's levels per column, X = 2^24 L0 + 2^16 L1 +
 //     2^8 L2 + L3, in float32 (one rounding) and adds it to a float32 register sum (at most 16
 //     read-backs at L = 2048); the value is X 2^(eps_c - 34).

@@ -75,15 +75,8 @@ def mw_theta_weights(Lp: int, dtype=np.float64) -> np.ndarray:
     k = np.arange(-(Lp - 1), Lp)
     if dtype == np.longdouble:
         th = mw_torus_thetas(Lp)                          # extended precision
-        wk = np.zeros(len(k), dtype=np.clongdouble)
-        even = (k % 2) == 0
-        wk[even] = np.longdouble(2) / (np.longdouble(1) - k[even].astype(np.longdouble) ** 2)
-        wk[k == 1] = 1j * (PI_LD / 2)
-        wk[k == -1] = -1j * (PI_LD / 2)
-        ang = -np.outer(th, k.astype(np.longdouble))
-        E = np.empty(ang.shape, dtype=np.clongdouble)
-        E.real = np.cos(ang)
-        E.imag = np.sin(ang)
+        wk = _w_hat_ld(k)
+        E = _expi_ld(-np.outer(th, k.astype(np.longdouble)))
     else:
         th = mw_torus_thetas(Lp, dtype=np.float64)       # theta_t on the torus, t < T
         wk = w_hat(k)
@@ -114,16 +107,39 @@ def mwss_phis(L: int) -> np.ndarray:
     return np.arange(2 * L).astype(np.longdouble) * PI_LD / np.longdouble(L)
 
 
-def mwss_theta_weights(Lp: int) -> np.ndarray:
+def _w_hat_ld(k: np.ndarray) -> np.ndarray:
+    """w_hat of ``w_hat`` in extended precision (clongdouble)."""
+    out = np.zeros(len(k), dtype=np.clongdouble)
+    even = (k % 2) == 0
+    out[even] = np.longdouble(2) / (np.longdouble(1) - k[even].astype(np.longdouble) ** 2)
+    out[k == 1] = 1j * (PI_LD / 2)
+    out[k == -1] = -1j * (PI_LD / 2)
+    return out
+
+
+def _expi_ld(ang: np.ndarray) -> np.ndarray:
+    """exp(i ang) for extended-precision angles, as clongdouble."""
+    E = np.empty(ang.shape, dtype=np.clongdouble)
+    E.real = np.cos(ang)
+    E.imag = np.sin(ang)
+    return E
+
+
+def mwss_theta_weights(Lp: int, dtype=np.float64) -> np.ndarray:
     """Theta quadrature weights q_t, t = 0..Lp, of the MWSS sampling theorem at bandlimit Lp:
     sum_t q_t g(theta_t) = int_0^pi g sin(theta) dtheta for every g whose torus extension is even
     about pi and has frequencies |k| <= Lp-1 (trapezoid on the 2Lp torus points, exact for the
-    product of g with the degree-(Lp-1) truncation of the weight function)."""
+    product of g with the degree-(Lp-1) truncation of the weight function).  ``dtype`` float64, or
+    np.longdouble for the extended-precision mode."""
     T = 2 * Lp
-    th = (np.arange(T).astype(np.longdouble) * PI_LD / np.longdouble(Lp)).astype(np.float64)
     k = np.arange(-(Lp - 1), Lp)
-    w = np.exp(-1j * np.outer(th, k)) @ w_hat(k)
-    q = np.empty(Lp + 1, dtype=np.complex128)
+    if dtype == np.longdouble:
+        th = np.arange(T).astype(np.longdouble) * PI_LD / np.longdouble(Lp)
+        w = _expi_ld(-np.outer(th, k.astype(np.longdouble))) @ _w_hat_ld(k)
+    else:
+        th = (np.arange(T).astype(np.longdouble) * PI_LD / np.longdouble(Lp)).astype(np.float64)
+        w = np.exp(-1j * np.outer(th, k)) @ w_hat(k)
+    q = np.empty(Lp + 1, dtype=w.dtype)
     for t in range(Lp + 1):
         zeta = 0.0 if t in (0, Lp) else 1.0
         q[t] = (w[t] + zeta * w[(T - t) % T]) / T
@@ -138,11 +154,11 @@ def dh_thetas(L: int, dtype=np.longdouble) -> np.ndarray:
     return ((2 * t + 1).astype(np.longdouble) * PI_LD / np.longdouble(4 * L)).astype(dtype)
 
 
-def dh_theta_weights(L: int) -> np.ndarray:
+def dh_theta_weights(L: int, dtype=np.float64) -> np.ndarray:
     """The theta part of the DH weights, (2/L) sin(theta_t) sum_{k<L} sin((2k+1) theta_t)/(2k+1),
     t < 2L (the paper's q(theta, phi) is this times the phi step 2 pi/(2L-1)); evaluated in
-    extended precision."""
+    extended precision and rounded to ``dtype``."""
     th = dh_thetas(L)
     k = np.arange(L).astype(np.longdouble)
     S = (np.sin(np.outer(th, 2 * k + 1)) / (2 * k + 1)).sum(axis=1)
-    return (np.longdouble(2) / L * np.sin(th) * S).astype(np.float64)
+    return (np.longdouble(2) / L * np.sin(th) * S).astype(dtype)

@@ -1,10 +1,10 @@
 """Spin-s spherical-harmonic and Wigner transforms on MW sampling -- the oracle (test infrastructure).
 
 Everything is a direct sum in float64 (no FFT); exponentials are built from exactly reduced
-integer phases.  ``exact=True`` (MW sphere and Wigner transforms) runs the same algorithm with the
-d-functions, weights, phases and every sum in numpy's extended precision (np.longdouble: 80-bit on
-x86-64, binary128 on aarch64) and rounds once to complex128 at the end (``keep=True`` returns the
-extended-precision result).  Array conventions (shared with the GPU library's boundary, written out here
+integer phases.  ``exact=True`` (sphere transforms on every sampling, MW Wigner transforms)
+runs the same algorithm with the d-functions, weights, phases and every sum in numpy's extended
+precision (np.longdouble: 80-bit on x86-64, binary128 on aarch64) and rounds once to complex128 at
+the end (``keep=True`` returns the extended-precision result).  Array conventions (shared with the GPU library's boundary, written out here
 independently):
 
 * sphere signal   f[..., t, p]           t < L rings (theta_t), p < 2L-1 (phi_p)
@@ -223,23 +223,26 @@ def sampling_thetas(L: int, sampling: str):
     return {"mw": mw_thetas, "mwss": mwss_thetas, "dh": dh_thetas}[sampling](L)
 
 
-def _phi_matrix(L: int, Tp: int, sign: int) -> np.ndarray:
+def _phi_matrix(L: int, Tp: int, sign: int, dtype=np.float64) -> np.ndarray:
     """E[p, j] = exp(sign i m_j phi_p), m_j = j - (L-1), phi_p = 2 pi p / Tp."""
     p = np.arange(Tp)[:, None]
     m = np.arange(-(L - 1), L)[None, :]
-    return _expi_pi(sign * 2 * p * m, Tp)
+    return _expi_pi(sign * 2 * p * m, Tp, dtype)
 
 
-def inverse_s(flm: np.ndarray, L: int, spin: int, sampling: str = "mw", rings=None) -> np.ndarray:
+def inverse_s(flm: np.ndarray, L: int, spin: int, sampling: str = "mw", rings=None, exact: bool = False,
+              keep: bool = False) -> np.ndarray:
     """Inverse spin-s SHT on any of the samplings: the direct sums of Eqs. disc_ish_expanded and
-    disc_ish_fft at that grid's theta_t and phi_p."""
+    disc_ish_fft at that grid's theta_t and phi_p.  ``exact``: extended precision (module
+    docstring)."""
     if sampling == "mw":
-        return inverse(flm, L, spin, rings)
+        return inverse(flm, L, spin, rings, exact, keep)
+    dt = np.longdouble if exact else np.float64
     th = sampling_thetas(L, sampling)
     if rings is not None:
         th = th[np.asarray(rings)]
-    ft = _theta_inverse(np.asarray(flm, dtype=np.complex128), L, -spin, ell_factor(L, spin), th)
-    return ft @ _phi_matrix(L, sampling_shape(L, sampling)[1], +1).T
+    ft = _theta_inverse(np.asarray(flm).astype(_cdtype(dt)), L, -spin, ell_factor(L, spin, dt), th, dt)
+    return _finish(ft @ _phi_matrix(L, sampling_shape(L, sampling)[1], +1, dt).T, keep)
 
 
 def _mwss_extend(F: np.ndarray, L: int, n: int) -> np.ndarray:
@@ -248,7 +251,7 @@ def _mwss_extend(F: np.ndarray, L: int, n: int) -> np.ndarray:
     MW's theta = pi ring (same reading)."""
     m = np.arange(-(L - 1), L)
     sigma = (-1.0) ** ((m - n) % 2)
-    G = np.zeros(F.shape[:-2] + (2 * L, F.shape[-1]), dtype=np.complex128)
+    G = np.zeros(F.shape[:-2] + (2 * L, F.shape[-1]), dtype=F.dtype)
     G[..., :L + 1, :] = F
     G[..., 0, :] = F[..., 0, :] * (1 + sigma) / 2
     G[..., L, :] = F[..., L, :] * (1 + sigma) / 2
@@ -256,51 +259,54 @@ def _mwss_extend(F: np.ndarray, L: int, n: int) -> np.ndarray:
     return G
 
 
-def _sampled_weighted_spectra(f: np.ndarray, L: int, n: int, sampling: str):
+def _sampled_weighted_spectra(f: np.ndarray, L: int, n: int, sampling: str, dtype=np.float64):
     """W[..., u, m] and theta_u such that flm = scale_l sum_u W[u, m] d^l_{m,n}(theta_u) on the MWSS
     or DH grid (f[..., t, p]): the phi DFT, then the theta quadrature of the sampling.
     DH: the explicit DH weights (Sec. 4.2.1).  MWSS: the route of Sec. 4.2.2 -- torus extension,
     Fourier coefficients |k| <= L-1 on the 2L torus points, evaluation on the MWSS grid of
     bandlimit 2L, MWSS weights at bandlimit 2L."""
     Tp = sampling_shape(L, sampling)[1]
-    F = np.asarray(f, dtype=np.complex128) @ _phi_matrix(L, Tp, -1)          # [t, m]
-    qphi = 2 * np.pi / Tp
+    F = np.asarray(f).astype(_cdtype(dtype)) @ _phi_matrix(L, Tp, -1, dtype)  # [t, m]
+    qphi = (2 * PI_LD / Tp).astype(dtype)
     if sampling == "dh":
-        return F * (dh_theta_weights(L) * qphi)[:, None], dh_thetas(L)
+        return F * (dh_theta_weights(L, dtype) * qphi)[:, None], dh_thetas(L)
     G = _mwss_extend(F, L, n)                                                # [t', m], t' < 2L
     k = np.arange(-(L - 1), L)
-    coef = _expi_pi(-np.outer(k, 2 * np.arange(2 * L)), 2 * L) / (2 * L)      # e^{-ik pi t'/L}/2L
+    coef = _expi_pi(-np.outer(k, 2 * np.arange(2 * L)), 2 * L, dtype) / dtype(2 * L)   # e^{-ik pi t'/L}/2L
     u = np.arange(2 * L + 1)
-    up = _expi_pi(np.outer(u, k), 2 * L)                                     # e^{+ik pi u/(2L)}
+    up = _expi_pi(np.outer(u, k), 2 * L, dtype)                              # e^{+ik pi u/(2L)}
     Gu = up @ (coef @ G)
-    return Gu * (mwss_theta_weights(2 * L) * qphi)[:, None], mwss_thetas(2 * L)
+    return Gu * (mwss_theta_weights(2 * L, dtype) * qphi)[:, None], mwss_thetas(2 * L)
 
 
-def _quadrature(W: np.ndarray, thetas, L: int, n: int, scale: np.ndarray, ells) -> np.ndarray:
+def _quadrature(W: np.ndarray, thetas, L: int, n: int, scale: np.ndarray, ells, dtype=np.float64) -> np.ndarray:
     """flm[..., i, m] = scale_l sum_u W[..., u, m] d^l_{m,n}(theta_u), l = ells[i] (Eq. disc_sh_expanded)."""
     ells = np.asarray(ells)
-    D = wigner_d_table(ells, n, thetas)                                      # [i, m', u]
+    D = wigner_d_table(ells, n, thetas, dtype)                               # [i, m', u]
     M = int(ells.max())
     D = D[:, M - (L - 1):M + L, :] if M >= L - 1 else np.pad(D, ((0, 0), (L - 1 - M, L - 1 - M), (0, 0)))
     out = np.einsum("...um,imu->...im", W, D) * scale[ells][:, None]
     return np.where(coeff_mask(L, n)[ells], out, 0)
 
 
-def _forward_sampled(f: np.ndarray, L: int, n: int, scale: np.ndarray, sampling: str, ells) -> np.ndarray:
+def _forward_sampled(f: np.ndarray, L: int, n: int, scale: np.ndarray, sampling: str, ells,
+                     dtype=np.float64) -> np.ndarray:
     """flm[..., i, m] = scale_l int f(theta, phi) d^l_{m,n}(theta) e^{-i m phi} sin(theta), l = ells[i],
     on the MWSS or DH grid."""
-    W, th = _sampled_weighted_spectra(f, L, n, sampling)
-    return _quadrature(W, th, L, n, scale, ells)
+    W, th = _sampled_weighted_spectra(f, L, n, sampling, dtype)
+    return _quadrature(W, th, L, n, scale, ells, dtype)
 
 
-def forward_s(f: np.ndarray, L: int, spin: int, sampling: str = "mw", ells=None) -> np.ndarray:
+def forward_s(f: np.ndarray, L: int, spin: int, sampling: str = "mw", ells=None, exact: bool = False,
+              keep: bool = False) -> np.ndarray:
     """Forward spin-s SHT on any of the samplings (MW: ``forward``; MWSS, DH: _forward_sampled
-    with d^l_{m,-s} and c_l)."""
+    with d^l_{m,-s} and c_l).  ``exact``: extended precision (module docstring)."""
     if sampling == "mw":
-        return forward(f, L, spin, ells)
+        return forward(f, L, spin, ells, None, exact, keep)
+    dt = np.longdouble if exact else np.float64
     if ells is None:
         ells = np.arange(L)
-    return _forward_sampled(f, L, -spin, ell_factor(L, spin), sampling, ells)
+    return _finish(_forward_sampled(f, L, -spin, ell_factor(L, spin, dt), sampling, ells, dt), keep)
 
 
 def adjoint_dense(fn, x_shape, y: np.ndarray) -> np.ndarray:

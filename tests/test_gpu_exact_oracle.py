@@ -1,6 +1,6 @@
 """The CUDA path against the oracle's extended-precision mode (``exact=True``: d-functions,
 weights and sums in np.longdouble) on the small sphere workload (L = 64, spin 0, MW sampling), a
-spin-2 batch and a small Wigner transform: every output element, relative max error <= 1e-12, the
+spin-2 batch, MWSS and DH plans and a small Wigner transform: every output element, relative max error <= 1e-12, the
 float64 bar.  The float64 oracle and the extended one agree to float64 rounding (pinned in
 tests/test_oracle_exact.py), so this checks the GPU against the better-conditioned reference."""
 import numpy as np
@@ -36,6 +36,20 @@ def test_sphere_inverse_and_forward_match_extended_oracle(L, spin, B):
     ref = np.stack([OT.forward(g[b], L, spin, exact=True) for b in range(B)])
     mask = OT.coeff_mask(L, -spin)
     assert rel_max(np.where(mask, got, 0), ref) <= TOL64
+
+
+@pytest.mark.parametrize("sampling", ["mwss", "dh"])
+def test_samplings_match_extended_oracle(sampling):
+    from paper_2311_14670_gb300 import Plan
+    L, spin, B = 24, 1, 2
+    p = Plan(L, spin=spin, max_batch=B, sampling=sampling)
+    flm = synth.flm_gaussian(L, spin, B, seed=31)
+    f = to_np(p.inverse(to_gpu(flm)))
+    ref = np.stack([OT.inverse_s(flm[b], L, spin, sampling, exact=True) for b in range(B)])
+    assert rel_max(f, ref) <= TOL64
+    back = to_np(p.forward(to_gpu(f)))
+    ref = np.stack([OT.forward_s(f[b], L, spin, sampling, exact=True) for b in range(B)])
+    assert rel_max(back, ref) <= TOL64
 
 
 def test_wigner_matches_extended_oracle():

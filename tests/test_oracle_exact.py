@@ -1,6 +1,6 @@
-"""Pins of the oracle's extended-precision mode (``exact=True``): the MW sphere and Wigner
-transforms with the d-functions (the recursion over m of Sec. 3.3), the MW weights (Sec. 4.2.2),
-the phases and every sum in np.longdouble.
+"""Pins of the oracle's extended-precision mode (``exact=True``): the sphere transforms on MW, MWSS
+and DH sampling and the MW Wigner transform with the d-functions (the recursion over m of
+Sec. 3.3), the quadrature weights (Sec. 4.2), the phases and every sum in np.longdouble.
 
 * Round trips land at the rounding level of the extended type (a few hundred units of its
   epsilon), three orders of magnitude below the float64 mode's: any float64 value left in a stage
@@ -81,3 +81,15 @@ def test_exact_and_float64_modes_agree(L, spin):
     rng = np.random.default_rng(L)
     f = rng.standard_normal((L, 2 * L - 1)) + 1j * rng.standard_normal((L, 2 * L - 1))
     assert _rel(T.forward(f, L, spin, exact=True), T.forward(f, L, spin)) < 1e-14
+
+
+@pytest.mark.parametrize("sampling", ["mwss", "dh"])
+@pytest.mark.parametrize("L,spin", [(8, 0), (16, 2), (12, -1)])
+def test_exact_round_trip_on_mwss_and_dh(sampling, L, spin):
+    flm = synth.flm_gaussian(L, spin, 1, seed=3 * L + spin)[0]
+    f = T.inverse_s(flm, L, spin, sampling, exact=True, keep=True)
+    back = T.forward_s(f, L, spin, sampling, exact=True, keep=True)
+    err = _rel(back, flm)
+    assert err < 8 * L * EPS_LD
+    assert _rel(T.forward_s(T.inverse_s(flm, L, spin, sampling), L, spin, sampling), flm) > 10 * err
+    assert _rel(f.astype(np.complex128), T.inverse_s(flm, L, spin, sampling)) < 1e-14
